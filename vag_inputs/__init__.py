@@ -1,0 +1,449 @@
+"""Seeded synthetic inputs for the hybrid-dimensional VAG Darcy + transport path.
+
+This module only *describes problems*: node coordinates, hexahedral cell
+connectivity, the unique faces of the mesh, which faces carry a fracture,
+permeabilities, apertures, porosities and boundary data.  It holds none of the
+scheme's arithmetic (no gradients, no transmissivities, no fluxes), so both the
+CUDA path and the CPU oracle can consume the same inputs without sharing any
+of the method.
+
+Mesh conventions (Sec. 3.1 of the paper: generalized polyhedral meshes
+conforming to the fracture network):
+
+* ``xyz``        float64 [n_nodes, 3]
+* ``cell_nodes`` int32   [n_cells, 8]   hexahedron, node ``l`` sits at the
+  lattice offset ``(l & 1, (l >> 1) & 1, (l >> 2) & 1)`` of the cell.
+* ``faces``      int32   [n_faces, 4]   every face of the mesh once, nodes in
+  cyclic order (consecutive entries share an edge).
+* ``cell_faces`` int32   [n_cells, 6]   face ids of each cell.
+* ``ff_faces``   int32   [n_ff]         ids (into ``faces``) of the fracture
+  faces, sorted; ``ff_nodes = faces[ff_faces]``.
+* ``lambda_m``   float64 [n_cells, 6]   symmetric matrix permeability tensor
+  (xx, yy, zz, xy, xz, yz).
+* ``lambda_f``, ``d_f`` float64 [n_ff]  isotropic tangential fracture
+  permeability and aperture.
+* ``dir_nodes`` int32 [n_dir] (sorted), ``dir_values`` float64 [n_dir]:
+  Dirichlet pressure; every other boundary node is a no-flow node.
+* ``phi_m`` [n_cells], ``phi_f`` [n_ff]: porosities; ``cbar`` [n_dir]: the
+  Dirichlet concentrations.
+
+All random draws come from ``numpy.random.default_rng(seed)`` in a fixed order.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+__all__ = [
+    "Problem", "hex_lattice", "axis_fracture_faces", "build_problem",
+    "config_plain16", "config_scale64", "config_mixed128", "random_dfn_problem",
+    "one_fracture_problem", "four_fracture_problem", "batch_problems",
+]
+
+
+@dataclass
+class Problem:
+    dims: Tuple[int, int, int]
+    xyz: np.ndarray
+    cell_nodes: np.ndarray
+    faces: np.ndarray
+    cell_faces: np.ndarray
+    ff_faces: np.ndarray
+    ff_nodes: np.ndarray
+    ff_frac: np.ndarray
+    lambda_m: np.ndarray
+    lambda_f: np.ndarray
+    d_f: np.ndarray
+    mu: float
+    dir_nodes: np.ndarray
+    dir_values: np.ndarray
+    phi_m: np.ndarray
+    phi_f: np.ndarray
+    cbar: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cell_nodes.shape[0])
+
+    @property
+    def n_ff(self) -> int:
+        return int(self.ff_faces.shape[0])
+
+    def c0(self) -> np.ndarray:
+        """Initial concentration in the [nodes | ffaces | cells] order: the
+        Dirichlet value on Dirichlet nodes, zero elsewhere."""
+        c = np.zeros(self.n_nodes + self.n_ff + self.n_cells)
+        c[self.dir_nodes] = self.cbar
+        return c
+
+
+# ----------------------------------------------------------------------------
+# structured hexahedral lattice (topologically Cartesian)
+# ----------------------------------------------------------------------------
+
+def _nid(dims, i, j, k):
+    nx, ny, nz = dims
+    return i + (nx + 1) * (j + (ny + 1) * k)
+
+
+def hex_lattice(dims):
+    """Connectivity of an nx*ny*nz hexahedral lattice.
+
+    Returns (cell_nodes, faces, cell_faces, face_axis, face_ijk) where face ids
+    are grouped as x-normal, y-normal, z-normal lattice faces.
+    """
+    nx, ny, nz = dims
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    i = i.ravel(); j = j.ravel(); k = k.ravel()
+    cell_nodes = np.stack([
+        _nid(dims, i + (l & 1), j + ((l >> 1) & 1), k + ((l >> 2) & 1)) for l in range(8)
+    ], axis=1).astype(np.int32)
+
+    # x-normal faces at (i, j, k), i in 0..nx, j < ny, k < nz
+    kx, jx, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx + 1), indexing="ij")
+    ix = ix.ravel(); jx = jx.ravel(); kx = kx.ravel()
+    fx = np.stack([_nid(dims, ix, jx, kx), _nid(dims, ix, jx + 1, kx),
+                   _nid(dims, ix, jx + 1, kx + 1), _nid(dims, ix, jx, kx + 1)], axis=1)
+    ky, jy, iy = np.meshgrid(np.arange(nz), np.arange(ny + 1), np.arange(nx), indexing="ij")
+    iy = iy.ravel(); jy = jy.ravel(); ky = ky.ravel()
+    fy = np.stack([_nid(dims, iy, jy, ky), _nid(dims, iy + 1, jy, ky),
+                   _nid(dims, iy + 1, jy, ky + 1), _nid(dims, iy, jy, ky + 1)], axis=1)
+    kz, jz, iz = np.meshgrid(np.arange(nz + 1), np.arange(ny), np.arange(nx), indexing="ij")
+    iz = iz.ravel(); jz = jz.ravel(); kz = kz.ravel()
+    fz = np.stack([_nid(dims, iz, jz, kz), _nid(dims, iz + 1, jz, kz),
+                   _nid(dims, iz + 1, jz + 1, kz), _nid(dims, iz, jz + 1, kz)], axis=1)
+    faces = np.concatenate([fx, fy, fz]).astype(np.int32)
+    nfx = fx.shape[0]; nfy = fy.shape[0]
+
+    def xf(ii, jj, kk):
+        return ii + (nx + 1) * (jj + ny * kk)
+
+    def yf(ii, jj, kk):
+        return nfx + ii + nx * (jj + (ny + 1) * kk)
+
+    def zf(ii, jj, kk):
+        return nfx + nfy + ii + nx * (jj + ny * kk)
+
+    cell_faces = np.stack([xf(i, j, k), xf(i + 1, j, k), yf(i, j, k), yf(i, j + 1, k),
+                           zf(i, j, k), zf(i, j, k + 1)], axis=1).astype(np.int32)
+    face_axis = np.concatenate([np.zeros(nfx), np.ones(nfy), 2 * np.ones(fz.shape[0])]).astype(np.int8)
+    face_ijk = np.concatenate([np.stack([ix, jx, kx], 1), np.stack([iy, jy, ky], 1),
+                               np.stack([iz, jz, kz], 1)]).astype(np.int64)
+    return cell_nodes, faces, cell_faces, face_axis, face_ijk
+
+
+def axis_fracture_faces(dims, axis, plane, lo_a, hi_a, lo_b, hi_b):
+    """Face ids of an axis-aligned rectangle lying on lattice node plane
+    ``plane`` normal to ``axis``; (lo_a, hi_a) x (lo_b, hi_b) are cell-index
+    ranges in the two other axes, in increasing axis order."""
+    nx, ny, nz = dims
+    nfx = (nx + 1) * ny * nz
+    nfy = nx * (ny + 1) * nz
+    a = np.arange(lo_a, hi_a)
+    b = np.arange(lo_b, hi_b)
+    A, B = np.meshgrid(a, b, indexing="ij")
+    A = A.ravel(); B = B.ravel()
+    if axis == 0:
+        ids = plane + (nx + 1) * (A + ny * B)
+    elif axis == 1:
+        ids = nfx + A + nx * (plane + (ny + 1) * B)
+    else:
+        ids = nfx + nfy + A + nx * (B + ny * plane)
+    return ids.astype(np.int64)
+
+
+def _lattice_xyz(dims):
+    nx, ny, nz = dims
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    return np.stack([i.ravel() / nx, j.ravel() / ny, k.ravel() / nz], axis=1).astype(np.float64)
+
+
+def _jitter(dims, xyz, faces, ff_faces, face_axis, amp, rng):
+    """Perturb interior nodes uniformly by +-amp*h per coordinate, keeping each
+    fracture face planar: a node on a fracture plane keeps that plane's normal
+    coordinate."""
+    nx, ny, nz = dims
+    h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+    d = rng.uniform(-amp, amp, size=xyz.shape) * h[None, :]
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    boundary = ((i == 0) | (i == nx) | (j == 0) | (j == ny) | (k == 0) | (k == nz)).ravel()
+    d[boundary] = 0.0
+    for ax in range(3):
+        sel = ff_faces[face_axis[ff_faces] == ax]
+        if sel.size:
+            frozen = np.unique(faces[sel].ravel())
+            d[frozen, ax] = 0.0
+    return xyz + d
+
+
+def _lognormal_aniso(n_cells, rng, log10_std=1.0, aniso=10.0):
+    """Cellwise tensor k_K (I + (aniso-1) a a^T), log10 k_K ~ N(0, std), one
+    seeded unit axis a for the whole field."""
+    logk = rng.normal(0.0, log10_std, size=n_cells)
+    a = rng.normal(size=3)
+    a /= np.linalg.norm(a)
+    k = 10.0 ** logk
+    t = aniso - 1.0
+    lam = np.empty((n_cells, 6))
+    lam[:, 0] = k * (1 + t * a[0] * a[0])
+    lam[:, 1] = k * (1 + t * a[1] * a[1])
+    lam[:, 2] = k * (1 + t * a[2] * a[2])
+    lam[:, 3] = k * t * a[0] * a[1]
+    lam[:, 4] = k * t * a[0] * a[2]
+    lam[:, 5] = k * t * a[1] * a[2]
+    return lam
+
+
+def build_problem(dims, fractures: Sequence[Tuple], *, jitter=0.0, seed=0,
+                  lam_m="identity", ratio=1e4, d_f=1e-2, phi_m=0.2, phi_f=0.4,
+                  xyz=None, frac_lambda: Optional[Sequence[float]] = None,
+                  frac_df: Optional[Sequence[float]] = None,
+                  dirichlet="x", meta=None) -> Problem:
+    """Assemble a Problem on a hexahedral lattice.
+
+    ``fractures``: list of (axis, plane, lo_a, hi_a, lo_b, hi_b) rectangles, or
+    lists of raw face ids (for meshes whose fracture is not axis-aligned).
+    Overlapping rectangles on one plane merge; each face is one fracture face.
+    ``dirichlet="x"``: p = 1 - x on the x = 0 and x = 1 faces (inflow c = 1 on
+    x = 0), no-flow elsewhere.
+    """
+    rng = np.random.default_rng(seed)
+    cell_nodes, faces, cell_faces, face_axis, _ = hex_lattice(dims)
+    ids, owner = [], []
+    for f_idx, fr in enumerate(fractures):
+        if isinstance(fr, np.ndarray):
+            fid = fr.astype(np.int64)
+        else:
+            fid = axis_fracture_faces(dims, *fr)
+        ids.append(fid)
+        owner.append(np.full(fid.shape, f_idx))
+    if ids:
+        allid = np.concatenate(ids)
+        allown = np.concatenate(owner)
+        ff_faces, first = np.unique(allid, return_index=True)
+        ff_frac = allown[first].astype(np.int32)
+    else:
+        ff_faces = np.zeros(0, np.int64)
+        ff_frac = np.zeros(0, np.int32)
+    ff_faces = ff_faces.astype(np.int32)
+    if xyz is None:
+        xyz = _lattice_xyz(dims)
+        if jitter > 0:
+            xyz = _jitter(dims, xyz, faces, ff_faces, face_axis, jitter, rng)
+    n_cells = cell_nodes.shape[0]
+    if isinstance(lam_m, np.ndarray):
+        lam = lam_m
+        med = 1.0
+    elif lam_m == "identity":
+        lam = np.zeros((n_cells, 6)); lam[:, :3] = 1.0
+        med = 1.0
+    elif lam_m == "lognormal":
+        lam = _lognormal_aniso(n_cells, rng)
+        med = 1.0   # median of k_K: log10 mean 0
+    else:
+        raise ValueError(lam_m)
+    nff = ff_faces.shape[0]
+    if frac_lambda is not None:
+        lam_f = np.asarray(frac_lambda, np.float64)[ff_frac]
+    else:
+        lam_f = np.full(nff, ratio * med)
+    if frac_df is not None:
+        dff = np.asarray(frac_df, np.float64)[ff_frac]
+    else:
+        dff = np.full(nff, d_f)
+    if dirichlet == "x":
+        nx, ny, nz = dims
+        k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+        i = i.ravel()
+        left = np.nonzero(i == 0)[0]; right = np.nonzero(i == nx)[0]
+        dir_nodes = np.concatenate([left, right])
+        order = np.argsort(dir_nodes)
+        dir_nodes = dir_nodes[order].astype(np.int32)
+        dir_values = (1.0 - xyz[dir_nodes, 0])
+        cbar = np.where(np.isin(dir_nodes, left), 1.0, 0.0)
+    else:
+        dir_nodes, dir_values, cbar = dirichlet
+        dir_nodes = np.asarray(dir_nodes, np.int32)
+    return Problem(
+        dims=tuple(dims), xyz=np.ascontiguousarray(xyz, np.float64),
+        cell_nodes=cell_nodes, faces=faces, cell_faces=cell_faces,
+        ff_faces=ff_faces, ff_nodes=np.ascontiguousarray(faces[ff_faces]).astype(np.int32),
+        ff_frac=ff_frac, lambda_m=np.ascontiguousarray(lam, np.float64),
+        lambda_f=lam_f, d_f=dff, mu=1.0,
+        dir_nodes=dir_nodes, dir_values=np.asarray(dir_values, np.float64),
+        phi_m=np.full(n_cells, float(phi_m)), phi_f=np.full(nff, float(phi_f)),
+        cbar=np.asarray(cbar, np.float64), meta=dict(meta or {}))
+
+
+# ----------------------------------------------------------------------------
+# the workloads
+# ----------------------------------------------------------------------------
+
+def config_plain16(n=16) -> Problem:
+    """Unit cube, n^3 hex cells, one fracture on the node plane x = 0.5,
+    Lambda_m = I, d_f = 1e-2, Lambda_f = 1e4 (K_f d_f = 1e2), p = 1 - x on
+    x = 0/1, porosities 0.2 / 0.4, inflow c = 1 on x = 0."""
+    dims = (n, n, n)
+    return build_problem(dims, [(0, n // 2, 0, n, 0, n)], ratio=1e4,
+                         meta={"name": f"plain{n}", "seed": None})
+
+
+def config_scale64(n=64, seed=1234) -> Problem:
+    """n^3 jittered (+-20% h) hex mesh with four fractures x=.5, y=.5, z=.5 and
+    x=.25 restricted to y<.5; lognormal (log10 std 1) matrix permeability with
+    10:1 anisotropy along a seeded axis; fracture/matrix ratio 1e4."""
+    h = n // 2
+    fr = [(0, h, 0, n, 0, n), (1, h, 0, n, 0, n), (2, h, 0, n, 0, n), (0, n // 4, 0, h, 0, n)]
+    return build_problem((n, n, n), fr, jitter=0.2, seed=seed, lam_m="lognormal",
+                         ratio=1e4, meta={"name": f"scale{n}", "seed": seed})
+
+
+def random_rectangles(n, n_frac, rng):
+    """Seeded axis-aligned rectangles snapped to lattice lines: normal axis
+    uniform in {x, y, z}, interior node plane uniform, side lengths U(0.1, 0.6),
+    placed uniformly so that the rectangle fits in the unit square."""
+    out = []
+    for _ in range(n_frac):
+        axis = int(rng.integers(0, 3))
+        plane = int(rng.integers(1, n))
+        la = max(1, int(round(rng.uniform(0.1, 0.6) * n)))
+        lb = max(1, int(round(rng.uniform(0.1, 0.6) * n)))
+        a0 = int(rng.integers(0, n - la + 1))
+        b0 = int(rng.integers(0, n - lb + 1))
+        out.append((axis, plane, a0, a0 + la, b0, b0 + lb))
+    return out
+
+
+def random_dfn_problem(n, n_frac, ratio, seed, jitter=0.2) -> Problem:
+    rng = np.random.default_rng(seed)
+    fr = random_rectangles(n, n_frac, rng)
+    sub = int(rng.integers(0, 2**31 - 1))
+    return build_problem((n, n, n), fr, jitter=jitter, seed=sub, lam_m="lognormal",
+                         ratio=ratio, meta={"name": f"dfn{n}_{n_frac}", "seed": seed,
+                                            "ratio": ratio})
+
+
+def config_mixed128(n=128, ratio=1e4, seed=4321) -> Problem:
+    """128^3 jittered mesh with a DFN of 50 seeded axis-aligned rectangles."""
+    return random_dfn_problem(n, 50, ratio, seed)
+
+
+def batch_problems(count, seed=99, n_lo=16, n_hi=48):
+    """Independent realisations: n ~ U{n_lo..n_hi}, 1-20 rectangles,
+    fracture/matrix ratio log-uniform in [1e2, 1e6], lognormal matrix K."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        nf = int(rng.integers(1, 21))
+        ratio = float(10.0 ** rng.uniform(2.0, 6.0))
+        s = int(rng.integers(0, 2**31 - 1))
+        out.append(random_dfn_problem(n, nf, ratio, s))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# meshes of the two analytical test cases (Sec. 5.1 and 5.2), extruded in z
+# ----------------------------------------------------------------------------
+
+def _line_intersections(xa0, xa1, yb0, yb1):
+    """Nodes of a topologically Cartesian grid whose i-lines run from
+    (xa0[i], 0) to (xa1[i], 1) and whose j-lines run from (0, yb0[j]) to
+    (1, yb1[j]).  Returns X, Y of shape [nj, ni]."""
+    XA0 = xa0[None, :]; XA1 = xa1[None, :]
+    YB0 = yb0[:, None]; YB1 = yb1[:, None]
+    # point on i-line: x = XA0 + s (XA1 - XA0), y = s
+    # point on j-line: y = YB0 + x (YB1 - YB0)
+    # s = YB0 + (XA0 + s dX) dY  ->  s (1 - dX dY) = YB0 + XA0 dY
+    dX = XA1 - XA0; dY = YB1 - YB0
+    s = (YB0 + XA0 * dY) / (1.0 - dX * dY)
+    return XA0 + s * dX, s
+
+
+def _extrude(X, Y, dz):
+    nj, ni = X.shape
+    xyz = np.zeros((2, nj, ni, 3))
+    xyz[:, :, :, 0] = X[None]
+    xyz[:, :, :, 1] = Y[None]
+    xyz[1, :, :, 2] = dz
+    return xyz.reshape(-1, 3)
+
+
+def one_fracture_problem(nx, tan_theta=0.5, lam_f=20.0, d_f=0.01):
+    """Sec. 5.1: unit square, fracture from (0, 1/4) to (1, 1/4 + tan(theta)),
+    Lambda_m = 1, phi_m = phi_f = 1, p = 1 - x on x = 0 and x = 1, y walls and
+    z walls no-flow; c = 1 enters on the whole x = 0 side.  The grid's j-lines
+    follow the fracture (it lies on the j = nx/2 line), the i-lines are
+    x = i / nx, one cell layer of thickness 1/nx in z."""
+    ny = nx
+    jf = nx // 2
+    xa = np.arange(nx + 1) / nx
+    yl = 0.25; yr = 0.25 + tan_theta
+    jj = np.arange(ny + 1)
+    yb0 = np.where(jj <= jf, yl * jj / jf, yl + (1 - yl) * (jj - jf) / (ny - jf))
+    yb1 = np.where(jj <= jf, yr * jj / jf, yr + (1 - yr) * (jj - jf) / (ny - jf))
+    X, Y = _line_intersections(xa, xa, yb0, yb1)
+    dims = (nx, ny, 1)
+    xyz = _extrude(X, Y, 1.0 / nx)
+    ff = axis_fracture_faces(dims, 1, jf, 0, nx, 0, 1)
+    nnodes = xyz.shape[0]
+    i = np.arange(nnodes) % (nx + 1)
+    left = np.nonzero(i == 0)[0]; right = np.nonzero(i == nx)[0]
+    dn = np.sort(np.concatenate([left, right]))
+    dv = 1.0 - xyz[dn, 0]
+    cb = np.where(np.isin(dn, left), 1.0, 0.0)
+    return build_problem(dims, [ff], xyz=xyz, frac_lambda=[lam_f], frac_df=[d_f],
+                         phi_m=1.0, phi_f=1.0, dirichlet=(dn, dv, cb),
+                         meta={"name": f"onefrac{nx}", "tan_theta": tan_theta,
+                               "lam_f": lam_f, "d_f": d_f, "jf": jf})
+
+
+def four_fracture_problem(nx, tan1=5.0 / 8.0, tan2=0.25, lam_f1=200.0, lam_f3=400.0, d_f=0.01):
+    """Sec. 5.2: fractures along the line (0, 1/4)-(1, 1/4 + tan1) (Gamma_1,
+    Gamma_2) and the line (3/4, 0)-(3/4 - tan2, 1) (Gamma_3, Gamma_4), crossing
+    at x_0.  Grid lines follow both fracture lines; p = 1 - x on x = 0, x = 1
+    and at the two fracture tips on y = 0 and y = 1; other walls no-flow.
+    Dirichlet concentration 1 at the tip of Gamma_1 on x = 0 and at the tip of
+    Gamma_4 on y = 1, zero on every other Dirichlet node."""
+    ny = nx
+    jf = int(round(0.5625 * ny))
+    i_f = int(round(0.625 * nx))
+    ii = np.arange(nx + 1)
+    xb, xt = 0.75, 0.75 - tan2
+    xa0 = np.where(ii <= i_f, xb * ii / i_f, xb + (1 - xb) * (ii - i_f) / (nx - i_f))
+    xa1 = np.where(ii <= i_f, xt * ii / i_f, xt + (1 - xt) * (ii - i_f) / (nx - i_f))
+    jj = np.arange(ny + 1)
+    yl, yr = 0.25, 0.25 + tan1
+    yb0 = np.where(jj <= jf, yl * jj / jf, yl + (1 - yl) * (jj - jf) / (ny - jf))
+    yb1 = np.where(jj <= jf, yr * jj / jf, yr + (1 - yr) * (jj - jf) / (ny - jf))
+    X, Y = _line_intersections(xa0, xa1, yb0, yb1)
+    dims = (nx, ny, 1)
+    xyz = _extrude(X, Y, 1.0 / nx)
+    f1 = axis_fracture_faces(dims, 1, jf, 0, i_f, 0, 1)
+    f2 = axis_fracture_faces(dims, 1, jf, i_f, nx, 0, 1)
+    f3 = axis_fracture_faces(dims, 0, i_f, 0, jf, 0, 1)
+    f4 = axis_fracture_faces(dims, 0, i_f, jf, ny, 0, 1)
+    nnodes = xyz.shape[0]
+    i = np.arange(nnodes) % (nx + 1)
+    j = (np.arange(nnodes) // (nx + 1)) % (ny + 1)
+    left = np.nonzero(i == 0)[0]; right = np.nonzero(i == nx)[0]
+    tip_bot = np.nonzero((i == i_f) & (j == 0))[0]
+    tip_top = np.nonzero((i == i_f) & (j == ny))[0]
+    dn = np.unique(np.concatenate([left, right, tip_bot, tip_top]))
+    dv = 1.0 - xyz[dn, 0]
+    tip1 = left[(j[left] == jf)]
+    cb = np.where(np.isin(dn, tip1) | np.isin(dn, tip_top), 1.0, 0.0)
+    return build_problem(dims, [f1, f2, f3, f4], xyz=xyz,
+                         frac_lambda=[lam_f1, lam_f1, lam_f3, lam_f3],
+                         frac_df=[d_f] * 4, phi_m=1.0, phi_f=1.0,
+                         dirichlet=(dn, dv, cb),
+                         meta={"name": f"fourfrac{nx}", "tan1": tan1, "tan2": tan2,
+                               "lam_f1": lam_f1, "lam_f3": lam_f3, "d_f": d_f,
+                               "jf": jf, "if": i_f})
