@@ -1,0 +1,243 @@
+/*
+ * vag.h -- C ABI of the GB300 implementation of the hybrid-dimensional Vertex
+ * Approximate Gradient (VAG) Darcy solve and explicit upwind transport
+ * (Xing, Masson, Lopez: "Parallel Vertex Approximate Gradient discretization
+ * of hybrid dimensional Darcy flow and transport in discrete fracture
+ * networks").
+ *
+ * One process drives one GPU.  Every array argument is a plain pointer plus
+ * the sizes given in the structs; a `mem` argument says whether the pointers
+ * are host (VAG_MEM_HOST) or device (VAG_MEM_DEVICE) addresses.  The caller
+ * owns every array it passes; the library copies inputs in and writes outputs
+ * out and keeps no caller pointer after a call returns.  Opaque handles are
+ * owned by the library and released by the matching *_destroy call.
+ *
+ * Errors: every entry point returns a vag_status; VAG_OK is 0.  On an error
+ * the outputs are left untouched (except VAG_ENOTCONVERGED, which writes the
+ * last iterate and a filled info struct) and vag_last_error() describes the
+ * cause.  No C++ exception crosses this boundary.  Device kernels never trap:
+ * failed checks and exhausted waits set a status word that the host reads.
+ *
+ * Index base 0, indices int32.  Every global vector of unknowns or
+ * concentrations is ordered [nodes | fracture faces | cells].
+ *
+ * Threading: a vag_ctx and the systems created from it are used by one host
+ * thread at a time.  The server (vag_server_*) is internally synchronised.
+ */
+#ifndef VAG_H
+#define VAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int vag_status;
+enum {
+  VAG_OK = 0,
+  VAG_EINVAL = 1,          /* bad argument (null pointer, size, value)      */
+  VAG_ENOMEM = 2,          /* device allocation failed                      */
+  VAG_EBUDGET = 3,         /* the context's memory budget would be exceeded */
+  VAG_ENOTCONVERGED = 4,   /* Krylov solve hit maxit above rtol             */
+  VAG_EBREAKDOWN = 5,      /* p^T A p <= 0 (matrix not SPD) or NaN          */
+  VAG_ETIMEOUT = 6,        /* a bounded wait expired                        */
+  VAG_ECUDA = 7,           /* a CUDA runtime call failed                    */
+  VAG_EMESH = 8            /* the mesh is not conforming / not supported    */
+};
+
+enum { VAG_MEM_HOST = 0, VAG_MEM_DEVICE = 1 };
+enum { VAG_FP64 = 0, VAG_MIXED = 1 };
+enum { VAG_PC_JACOBI = 0, VAG_PC_CHEBYSHEV = 1, VAG_PC_AMG = 2 };
+
+typedef struct vag_ctx vag_ctx;
+typedef struct vag_system vag_system;
+
+/*
+ * Mesh (Sec. 3.1, generalized polyhedral mesh conforming to the fracture
+ * network; this library takes its hexahedral case).
+ *   xyz        [3*n_nodes]  node coordinates, x y z interleaved.
+ *   cell_nodes [8*n_cells]  node l of a cell sits at lattice offset
+ *              (l&1, (l>>1)&1, (l>>2)&1): faces are {0,2,6,4} (-x),
+ *              {1,3,7,5} (+x), {0,1,5,4} (-y), {2,3,7,6} (+y), {0,1,3,2} (-z),
+ *              {4,5,7,6} (+z); faces need not be planar.
+ *   ff_nodes   [4*n_ff]     the fracture faces F_Gamma, each a face of the
+ *              mesh given by its four nodes in cyclic order.  A fracture face
+ *              that is not a face of some cell is a VAG_EMESH error.
+ * Cell centres x_K and face centres x_sigma are the isobarycentres of their
+ * nodes (beta_{sigma,s} = 1/4).
+ */
+typedef struct {
+  int32_t n_nodes;
+  const double *xyz;
+  int32_t n_cells;
+  const int32_t *cell_nodes;
+  int32_t n_ff;
+  const int32_t *ff_nodes;
+} vag_mesh;
+
+/*
+ * Physical data of Eq. (modeleCont) and Eq. (varformVAG):
+ *   lambda_m [6*n_cells] cellwise-constant SPD tensor Lambda_m as
+ *            (xx, yy, zz, xy, xz, yz);
+ *   lambda_f [n_ff]      isotropic tangential fracture permeability;
+ *   d_f      [n_ff]      fracture aperture (width);
+ *   mu                   viscosity (> 0).
+ */
+typedef struct {
+  const double *lambda_m;
+  const double *lambda_f;
+  const double *d_f;
+  double mu;
+} vag_props;
+
+/*
+ * Dirichlet nodes V_D with pressure u_s = values[i] (Sec. 3.1; the paper's
+ * V_ext).  Every other boundary node is a no-flow node.  Nodes must be
+ * distinct and at least one node must be given.
+ */
+typedef struct {
+  int32_t n_dir;
+  const int32_t *nodes;
+  const double *values;
+} vag_dirichlet;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the device
+ * memory all systems of this context may hold (0 = no cap).  The context owns
+ * a non-blocking stream unless vag_ctx_set_stream() supplies one. */
+vag_status vag_ctx_create(int device, size_t mem_budget_bytes, vag_ctx **out);
+void vag_ctx_destroy(vag_ctx *ctx);
+/* Use the caller's cudaStream_t (passed as void*); NULL restores the
+ * context's own stream.  Every later call of this context runs on it. */
+vag_status vag_ctx_set_stream(vag_ctx *ctx, void *cuda_stream);
+/* Human-readable description of the last error on this context. */
+const char *vag_last_error(const vag_ctx *ctx);
+/* Device bytes currently held by the context's systems. */
+size_t vag_ctx_bytes_in_use(const vag_ctx *ctx);
+
+/* --------------------------------------------------------------- assembly */
+
+/*
+ * Build the VAG system of Sec. 3.1 and Sec. 4.2 on the device:
+ *  - symbolic phase (once per mesh): fracture faces matched to cell faces,
+ *    node->cell and node->fracture-face adjacency, the Krylov unknowns
+ *    (V \ V_D) u F_Gamma and the CSR pattern of the cell-eliminated system;
+ *  - numeric phase: the local matrices a_{K,nu}^{nu'} of Eq. (VAGFluxMatrix)
+ *    on the 24 tetrahedra T_{K,sigma,e} of every cell, the fracture matrices
+ *    a_{sigma,s}^{s'} of Eq. (VAGFluxFracture), and the Schur complement of
+ *    Eq. (eqschur) (cell unknowns eliminated, A_cc diagonal) gathered row by
+ *    row into CSR with the Dirichlet columns moved to the right-hand side.
+ * Krylov rows are the non-Dirichlet nodes in increasing node id followed by
+ * the fracture faces in input order.  All arithmetic is FP64.
+ * mem: location of every pointer in mesh, props and bc.
+ */
+vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *props,
+                        const vag_dirichlet *bc, int mem, vag_system **out);
+/* Re-run the numeric phase with new properties on the same mesh. */
+vag_status vag_update_props(vag_system *sys, const vag_props *props, int mem);
+void vag_system_destroy(vag_system *sys);
+
+typedef struct {
+  int32_t n_nodes, n_cells, n_ff, n_dir;
+  int32_t n_rows;          /* Krylov unknowns: non-Dirichlet nodes + fracture faces */
+  int64_t nnz;             /* nonzeros of the eliminated system                   */
+  int32_t n_frac_cells;    /* cells with at least one fracture face               */
+  int32_t n_cv;            /* control volumes = n_nodes + n_ff + n_cells          */
+  int64_t nnz_transport;   /* off-diagonal entries of the upwind transport map    */
+  size_t device_bytes;     /* device memory held by this system                   */
+} vag_system_info;
+vag_status vag_system_get_info(const vag_system *sys, vag_system_info *info);
+
+/* ------------------------------------------------------------------ solve */
+
+typedef struct {
+  int precision;     /* VAG_FP64, or VAG_MIXED: FP32 inner Krylov inside FP64
+                        iterative refinement (residual and update in FP64)   */
+  int precond;       /* VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG          */
+  double rtol;       /* stop at ||b - A x||_2 <= rtol ||b||_2 (> 0)           */
+  int32_t maxit;     /* Krylov iteration cap (total over refinements)          */
+  int mem;           /* location of u_out                                     */
+} vag_solve_opts;
+
+typedef struct {
+  int32_t iterations;    /* Krylov iterations (inner iterations for MIXED)     */
+  int32_t outer;         /* refinement steps (MIXED), else 1                   */
+  double rel_residual;   /* final ||b - A x|| / ||b|| recomputed in FP64       */
+  double ms_setup;       /* preconditioner setup, device time                   */
+  double ms_solve;       /* Krylov loop + cell recovery, device time            */
+  vag_status status;
+} vag_solve_info;
+
+/*
+ * Solve the eliminated system by preconditioned conjugate gradients (the
+ * matrix is symmetric positive definite: Galerkin form, Dirichlet rows
+ * removed), then recover the cell unknowns by Eq. (eqschurcell) and keep the
+ * full solution on the device for vag_transport.  u_out (optional, may be
+ * NULL): [n_nodes + n_ff + n_cells] in the [nodes | ffaces | cells] order, the
+ * Dirichlet values echoed at Dirichlet nodes.
+ */
+vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
+                     vag_solve_info *info);
+
+/* y = A x on the Krylov rows of the eliminated system (FP64).  x, y: [n_rows]. */
+vag_status vag_spmv(vag_system *sys, const double *x, double *y, int mem);
+
+/* -------------------------------------------------------------- transport */
+
+typedef struct {
+  const double *phi_m;   /* [n_cells] matrix porosity                          */
+  const double *phi_f;   /* [n_ff] fracture porosity                           */
+  const double *cbar;    /* [n_dir] Dirichlet concentration, aligned with bc   */
+  double omega;          /* control-volume fraction alpha = omega/|V_K| (Sec.
+                            3.2.1); 0 <= omega < 1, typically 0.5             */
+  double cfl;            /* > 0: dt = cfl * the CFL bound of Eq. (eq_CFL)     */
+  double dt;             /* used when cfl <= 0                                */
+  int32_t n_steps;       /* explicit Euler steps to take (>= 0)               */
+  int mem;               /* location of phi_m, phi_f, cbar and c_inout        */
+} vag_transport_opts;
+
+typedef struct {
+  double dt_max;         /* the CFL bound min(dt_M, dt_F, dt_V)               */
+  double dt;             /* the step used                                     */
+  int32_t steps;
+  double ms;             /* device time of the steps                          */
+} vag_transport_info;
+
+/*
+ * Explicit first-order upwind transport (Sec. 3.2, Eq. darcyfluxH) driven by
+ * the fluxes of the last vag_solve (or of vag_set_fluxes).  Porous volumes
+ * follow Sec. 3.2.1 with alpha_{K,s} = omega/8 on nodes of K outside
+ * V_D u V_Gamma and alpha_{sigma,s} = omega/4 on nodes of sigma outside V_D.
+ * c_inout: [n_nodes + n_ff + n_cells]; on entry c^0, on exit c^{n_steps}.  The
+ * Dirichlet entries are set to cbar before the first step (c^0_s = cbar_s).
+ */
+vag_status vag_transport(vag_system *sys, const vag_transport_opts *opts, double *c_inout,
+                         vag_transport_info *info);
+
+/* ----------------------------------------------------- inspection / tests */
+
+/* Copy out the eliminated system: rowptr [n_rows+1], col [nnz] (row indices),
+ * val [nnz], rhs [n_rows], row_dof [n_rows] (global DOF of each row: node id,
+ * or n_nodes + fracture-face index).  Any pointer may be NULL. */
+vag_status vag_export_system(const vag_system *sys, int32_t *rowptr, int32_t *col, double *val,
+                             double *rhs, int32_t *row_dof, int mem);
+/* Fluxes of Eq. (VAGFluxMatrix) / Eq. (VAGFluxFracture) in the library's
+ * layout: F_cell_nodes [8*n_cells] (F_{K,s}, s in cell_nodes order),
+ * F_cell_faces [6*n_cells] (F_{K,sigma} on the cell's six faces in the face
+ * order of vag_mesh, 0 where the face is not a fracture face), F_frac
+ * [4*n_ff] (F_{sigma,s}, s in ff_nodes order). */
+vag_status vag_export_fluxes(const vag_system *sys, double *F_cell_nodes, double *F_cell_faces,
+                             double *F_frac, int mem);
+/* Replace the fluxes (same layout) used by the next vag_transport. */
+vag_status vag_set_fluxes(vag_system *sys, const double *F_cell_nodes, const double *F_cell_faces,
+                          const double *F_frac, int mem);
+/* Porous volumes phi_mu [n_cv] of the last vag_transport (0 at Dirichlet nodes). */
+vag_status vag_export_porous_volumes(const vag_system *sys, double *phi, int mem);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VAG_H */

@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) implementation of the hybrid-dimensional VAG Darcy solve and
+explicit upwind transport (Xing, Masson, Lopez, arXiv 1602.03641).
+
+The compute path is ``libvag.so`` (CUDA, built in-tree by ``build.build()``)
+behind the C ABI of ``include/vag.h``; ``vag`` is its ctypes binding.
+"""
+from .vag import (  # noqa: F401
+    Context, System, VagError, assemble_problem, lib, declared_symbols,
+    VAG_OK, VAG_EINVAL, VAG_ENOMEM, VAG_EBUDGET, VAG_ENOTCONVERGED, VAG_EBREAKDOWN, VAG_ETIMEOUT,
+    VAG_ECUDA, VAG_EMESH, VAG_MEM_HOST, VAG_MEM_DEVICE, VAG_FP64, VAG_MIXED,
+    VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG,
+)

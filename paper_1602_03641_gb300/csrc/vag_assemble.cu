@@ -1,0 +1,331 @@
+// Numeric phase of vag_assemble (FP64):
+//  k_cell_local  one thread per cell: the local VAG matrix
+//                a_{K,nu}^{nu'} = int_K Lambda_m/mu grad eta_nu . grad eta_nu'
+//                of Eq. (VAGFluxMatrix), integrated exactly on the 24
+//                tetrahedra T_{K,sigma,e} = conv(x_K, x_sigma, e) (Sec. 3.1).
+//                The face-centre vertex of a non-fracture face is the
+//                interpolation I_sigma (beta = 1/4 on the face nodes); on a
+//                fracture face it is the unknown v_sigma.
+//  k_ff_local    one thread per fracture face: a_{sigma,s}^{s'} of
+//                Eq. (VAGFluxFracture) on the triangles (x_sigma, e).
+//  k_gather_rows one thread per Krylov row: the Schur complement of
+//                Eq. (eqschur), A = A_[vf][vf] - A_[vf]c A_cc^{-1} A_c[vf],
+//                summed over the row's cells and fracture faces in a fixed
+//                order (deterministic, no atomics); Dirichlet columns go to
+//                the right-hand side.
+#include "vag_internal.cuh"
+#include "vag_hex.cuh"
+
+namespace vag {
+namespace {
+
+struct V3 {
+  double x, y, z;
+};
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 ldv(const double *__restrict__ xyz, int n) {
+  return {xyz[3 * (size_t)n], xyz[3 * (size_t)n + 1], xyz[3 * (size_t)n + 2]};
+}
+
+// packed index in a 6x6 symmetric matrix over (K, sigma, t0, t1, t2, t3)
+__host__ __device__ constexpr int p6(int i, int j) {
+  return i <= j ? i * 6 - (i * (i - 1)) / 2 + (j - i) : j * 6 - (j * (j - 1)) / 2 + (i - j);
+}
+// packed index in a 4x4 symmetric matrix
+__host__ __device__ constexpr int p4(int i, int j) {
+  return i <= j ? i * 4 - (i * (i - 1)) / 2 + (j - i) : j * 4 - (j * (j - 1)) / 2 + (i - j);
+}
+
+// P1 stiffness S_ij = |T| grad l_i . L grad l_j on the tetrahedron (p0..p3).
+// With e_k = p_k - p0, the area vectors n1 = e2 x e3, n2 = e3 x e1,
+// n3 = e1 x e2 satisfy grad l_k = n_k / det (det = e1 . n1) and
+// n0 = -(n1 + n2 + n3); hence S_ij = n_i . L n_j / (6 |det|).
+__device__ __forceinline__ void tet_stiffness(V3 p0, V3 p1, V3 p2, V3 p3, const double (&L)[6],
+                                              double (&S)[10], double &vol) {
+  const V3 e1 = p1 - p0, e2 = p2 - p0, e3 = p3 - p0;
+  V3 n[4];
+  n[1] = cross(e2, e3);
+  n[2] = cross(e3, e1);
+  n[3] = cross(e1, e2);
+  n[0] = {-(n[1].x + n[2].x + n[3].x), -(n[1].y + n[2].y + n[3].y), -(n[1].z + n[2].z + n[3].z)};
+  const double ad = fabs(dot(e1, n[1]));
+  vol = ad * (1.0 / 6.0);
+  const double inv = 1.0 / (6.0 * ad);
+  V3 Ln[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    Ln[j].x = L[0] * n[j].x + L[3] * n[j].y + L[4] * n[j].z;
+    Ln[j].y = L[3] * n[j].x + L[1] * n[j].y + L[5] * n[j].z;
+    Ln[j].z = L[4] * n[j].x + L[5] * n[j].y + L[2] * n[j].z;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = i; j < 4; ++j) S[p4(i, j)] = dot(n[i], Ln[j]) * inv;
+}
+
+__global__ void __launch_bounds__(128) k_cell_local(int nc, const int *__restrict__ cn, const double *__restrict__ xyz,
+                                                    const double *__restrict__ lam, double inv_mu,
+                                                    const int *__restrict__ cell_ff, const int *__restrict__ fc_index,
+                                                    int n_fc, double *__restrict__ Mc, double *__restrict__ Mfc,
+                                                    double *__restrict__ cvol, int *status) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nc) return;
+  double L[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) L[k] = lam[6 * (size_t)K + k] * inv_mu;
+  int nd[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) nd[l] = cn[8 * (size_t)K + l];
+  V3 xK = {0, 0, 0};
+#pragma unroll
+  for (int l = 0; l < 8; ++l) xK = xK + ldv(xyz, nd[l]);
+  xK = {xK.x * 0.125, xK.y * 0.125, xK.z * 0.125};
+  const int fi = fc_index[K];
+
+  double M[hex::kPacked];
+#pragma unroll
+  for (int k = 0; k < hex::kPacked; ++k) M[k] = 0.0;
+  double vol = 0.0;
+  double minvol = 1e300;
+
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) {
+    V3 q[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) q[t] = ldv(xyz, nd[hex::face(lf, t)]);
+    const V3 xs = {0.25 * (q[0].x + q[1].x + q[2].x + q[3].x), 0.25 * (q[0].y + q[1].y + q[2].y + q[3].y),
+                   0.25 * (q[0].z + q[1].z + q[2].z + q[3].z)};
+    double F[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) F[k] = 0.0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      double S[10], tv;
+      tet_stiffness(xK, xs, q[e], q[(e + 1) & 3], L, S, tv);
+      vol += tv;
+      minvol = fmin(minvol, tv);
+      const int map[4] = {0, 1, 2 + e, 2 + ((e + 1) & 3)};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j) F[p6(map[i], map[j])] += S[p4(i, j)];
+    }
+    const bool isff = cell_ff[6 * (size_t)K + lf] >= 0;
+    M[hex::pidx(0, 0)] += F[p6(0, 0)];
+    if (!isff) {
+      // x_sigma = I_sigma: the sigma row/column is spread with weight 1/4
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int a = 1 + hex::face(lf, t);
+        M[hex::pidx(0, a)] += F[p6(0, 2 + t)] + 0.25 * F[p6(0, 1)];
+#pragma unroll
+        for (int u = t; u < 4; ++u) {
+          const int b = 1 + hex::face(lf, u);
+          M[hex::pidx(a, b)] += F[p6(2 + t, 2 + u)] + 0.25 * (F[p6(1, 2 + u)] + F[p6(1, 2 + t)]) +
+                                0.0625 * F[p6(1, 1)];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int a = 1 + hex::face(lf, t);
+        M[hex::pidx(0, a)] += F[p6(0, 2 + t)];
+#pragma unroll
+        for (int u = t; u < 4; ++u) {
+          const int b = 1 + hex::face(lf, u);
+          M[hex::pidx(a, b)] += F[p6(2 + t, 2 + u)];
+        }
+      }
+      if (fi >= 0) {
+        Mfc[(size_t)(lf * 6 + 0) * n_fc + fi] = F[p6(1, 1)];
+        Mfc[(size_t)(lf * 6 + 1) * n_fc + fi] = F[p6(0, 1)];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) Mfc[(size_t)(lf * 6 + 2 + t) * n_fc + fi] = F[p6(1, 2 + t)];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < hex::kPacked; ++k) Mc[(size_t)k * nc + K] = M[k];
+  cvol[K] = vol;
+  if (!(minvol > 0.0)) atomicOr(status, ST_BAD_GEOMETRY);
+}
+
+// Fracture-face matrix on (sigma, n0..n3) from the P1 tangential stiffness of
+// the triangles (x_sigma, n_e, n_{e+1}): with the edge vectors E_i opposite
+// vertex i (E0 + E1 + E2 = 0), S_ij = coef (E_i . E_j) / (4 |T|).
+__global__ void k_ff_local(int nf, const int *__restrict__ ffn, const double *__restrict__ xyz,
+                           const double *__restrict__ lamf, const double *__restrict__ df, double inv_mu,
+                           double *__restrict__ Mff, double *__restrict__ area, int *status) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  V3 q[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) q[t] = ldv(xyz, ffn[4 * (size_t)f + t]);
+  const V3 xs = {0.25 * (q[0].x + q[1].x + q[2].x + q[3].x), 0.25 * (q[0].y + q[1].y + q[2].y + q[3].y),
+                 0.25 * (q[0].z + q[1].z + q[2].z + q[3].z)};
+  const double coef = df[f] * lamf[f] * inv_mu;
+  double M[25];
+#pragma unroll
+  for (int k = 0; k < 25; ++k) M[k] = 0.0;
+  double ar = 0.0, minar = 1e300;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const V3 a = q[e], b = q[(e + 1) & 3];
+    const V3 E[3] = {b - a, xs - b, a - xs};
+    const V3 nrm = cross(a - xs, b - xs);
+    const double A = 0.5 * sqrt(dot(nrm, nrm));
+    ar += A;
+    minar = fmin(minar, A);
+    const double c = coef / (4.0 * A);
+    const int map[3] = {0, 1 + e, 1 + ((e + 1) & 3)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) M[map[i] * 5 + map[j]] += c * dot(E[i], E[j]);
+  }
+#pragma unroll
+  for (int k = 0; k < 25; ++k) Mff[(size_t)k * nf + f] = M[k];
+  area[f] = ar;
+  if (!(minar > 0.0)) atomicOr(status, ST_BAD_GEOMETRY);
+}
+
+struct GatherView {
+  int nv, nc, nf, n_fc;
+  const int *cn, *ffn, *node_dir, *cell_ff, *ff_cells, *ff_lface, *fc_index;
+  const int *n2c_ptr, *n2c, *n2f_ptr, *n2f, *row_of_dof, *dof_of_row;
+  const int *rowptr, *col, *diag_pos;
+  const double *Mc, *Mfc, *Mff, *dir_vals;
+  double *val, *rhs, *dinv;
+};
+
+struct RowAcc {
+  const GatherView &g;
+  int beg, end;
+  double b;
+  int *status;
+  __device__ RowAcc(const GatherView &gv, int bg, int en, int *st) : g(gv), beg(bg), end(en), b(0.0), status(st) {}
+  __device__ void add(int dof, double v) {
+    if (dof < g.nv) {
+      const int d = g.node_dir[dof];
+      if (d >= 0) { b -= v * g.dir_vals[d]; return; }
+    }
+    const int c = g.row_of_dof[dof];
+    int lo = beg, hi = end;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (g.col[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    if (c < 0 || lo >= end || g.col[lo] != c) { atomicOr(status, ST_NO_SLOT); return; }
+    g.val[lo] += v;
+  }
+};
+
+__device__ __forceinline__ double mc(const GatherView &g, int i, int j, int K) {
+  return g.Mc[(size_t)hex::pidx(i, j) * g.nc + K];
+}
+__device__ __forceinline__ double mfc(const GatherView &g, int lf, int k, int fi) {
+  return g.Mfc[(size_t)(lf * 6 + k) * g.n_fc + fi];
+}
+
+__global__ void k_gather_rows(GatherView g, int n_rows, int *status) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const int beg = g.rowptr[r], end = g.rowptr[r + 1];
+  for (int k = beg; k < end; ++k) g.val[k] = 0.0;
+  RowAcc acc(g, beg, end, status);
+  const int dof = g.dof_of_row[r];
+  if (dof < g.nv) {
+    // node row s: Schur rows of the cells around s, then fracture rows
+    for (int e = g.n2c_ptr[dof]; e < g.n2c_ptr[dof + 1]; ++e) {
+      const int K = g.n2c[e] >> 3, a = g.n2c[e] & 7;
+      const double fac = mc(g, 0, 1 + a, K) / mc(g, 0, 0, K);     // M_aK / M_KK
+      for (int bn = 0; bn < 8; ++bn)
+        acc.add(g.cn[8 * (size_t)K + bn], mc(g, 1 + a, 1 + bn, K) - fac * mc(g, 0, 1 + bn, K));
+      const int fi = g.fc_index[K];
+      if (fi >= 0) {
+        for (int lf = 0; lf < 6; ++lf) {
+          const int f = g.cell_ff[6 * (size_t)K + lf];
+          if (f < 0) continue;
+          const int t = hex::pos_on_face(lf, a);
+          const double Mas = t >= 0 ? mfc(g, lf, 2 + t, fi) : 0.0;
+          acc.add(g.nv + f, Mas - fac * mfc(g, lf, 1, fi));
+        }
+      }
+    }
+    for (int e = g.n2f_ptr[dof]; e < g.n2f_ptr[dof + 1]; ++e) {
+      const int f = g.n2f[e] >> 2, t = g.n2f[e] & 3;
+      acc.add(g.nv + f, g.Mff[(size_t)((1 + t) * 5) * g.nf + f]);
+      for (int u = 0; u < 4; ++u) acc.add(g.ffn[4 * (size_t)f + u], g.Mff[(size_t)((1 + t) * 5 + 1 + u) * g.nf + f]);
+    }
+  } else {
+    const int f = dof - g.nv;
+    for (int c = 0; c < 2; ++c) {
+      const int K = g.ff_cells[2 * f + c];
+      if (K < 0) continue;
+      const int lf = g.ff_lface[2 * f + c];
+      const int fi = g.fc_index[K];
+      const double fac = mfc(g, lf, 1, fi) / mc(g, 0, 0, K);      // M_sigmaK / M_KK
+      for (int bn = 0; bn < 8; ++bn) {
+        const int t = hex::pos_on_face(lf, bn);
+        const double Msb = t >= 0 ? mfc(g, lf, 2 + t, fi) : 0.0;
+        acc.add(g.cn[8 * (size_t)K + bn], Msb - fac * mc(g, 0, 1 + bn, K));
+      }
+      for (int lf2 = 0; lf2 < 6; ++lf2) {
+        const int f2 = g.cell_ff[6 * (size_t)K + lf2];
+        if (f2 < 0) continue;
+        const double Mss = lf2 == lf ? mfc(g, lf, 0, fi) : 0.0;
+        acc.add(g.nv + f2, Mss - fac * mfc(g, lf2, 1, fi));
+      }
+    }
+    acc.add(g.nv + f, g.Mff[(size_t)0 * g.nf + f]);
+    for (int u = 0; u < 4; ++u) acc.add(g.ffn[4 * (size_t)f + u], g.Mff[(size_t)(1 + u) * g.nf + f]);
+  }
+  g.rhs[r] = acc.b;
+  const double d = g.val[g.diag_pos[r]];   // the symbolic phase guarantees a diagonal slot
+  if (!(d > 0.0)) atomicOr(status, ST_NONPOSITIVE);
+  g.dinv[r] = 1.0 / d;
+}
+
+}  // namespace
+
+void numeric_phase(System *s) {
+  cudaStream_t st = s->ctx->stream;
+  if (!s->Mc) {
+    s->Mc = sys_alloc<double>(s, (size_t)hex::kPacked * s->nc);
+    s->Mfc = sys_alloc<double>(s, (size_t)36 * (s->n_fc > 0 ? s->n_fc : 1));
+    s->Mff = sys_alloc<double>(s, (size_t)25 * (s->nf > 0 ? s->nf : 1));
+    s->cvol = sys_alloc<double>(s, s->nc);
+    s->ffarea = sys_alloc<double>(s, s->nf > 0 ? s->nf : 1);
+    s->val = sys_alloc<double>(s, (size_t)s->nnz);
+    s->rhs = sys_alloc<double>(s, s->n_rows);
+    s->dinv = sys_alloc<double>(s, s->n_rows);
+  }
+  VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
+  const double inv_mu = 1.0 / s->mu;
+  k_cell_local<<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, s->cell_nodes, s->xyz, s->lam, inv_mu, s->cell_ff,
+                                                      s->fc_index, s->n_fc, s->Mc, s->Mfc, s->cvol, s->status);
+  VAG_CHECK_LAUNCH();
+  if (s->nf) {
+    k_ff_local<<<grid_for(s->nf, 128), 128, 0, st>>>(s->nf, s->ff_nodes, s->xyz, s->lamf, s->df, inv_mu, s->Mff,
+                                                      s->ffarea, s->status);
+    VAG_CHECK_LAUNCH();
+  }
+  GatherView g{s->nv, s->nc, s->nf, s->n_fc, s->cell_nodes, s->ff_nodes, s->node_dir, s->cell_ff,
+               s->ff_cells, s->ff_lface, s->fc_index, s->n2c_ptr, s->n2c, s->n2f_ptr, s->n2f,
+               s->row_of_dof, s->dof_of_row, s->rowptr, s->col, s->diag_pos, s->Mc, s->Mfc, s->Mff,
+               s->dir_vals, s->val, s->rhs, s->dinv};
+  k_gather_rows<<<grid_for(s->n_rows, 128), 128, 0, st>>>(g, s->n_rows, s->status);
+  VAG_CHECK_LAUNCH();
+  const int stv = read_status(s);
+  if (stv & ST_BAD_GEOMETRY) fail(VAG_EMESH, "degenerate sub-tetrahedron or fracture triangle");
+  if (stv & ST_NONPOSITIVE) fail(VAG_EINVAL, "non-positive diagonal in the eliminated system");
+  if (stv & ST_NO_SLOT) fail(VAG_EMESH, "internal: a Schur contribution has no CSR slot");
+}
+
+}  // namespace vag

@@ -1,0 +1,355 @@
+// extern "C" entry points of libvag (declared in include/vag.h): argument
+// checks, host/device staging, and the mapping of internal errors to status
+// codes.  No exception crosses this boundary.
+#include <cstring>
+#include <memory>
+
+#include "vag_internal.cuh"
+
+using namespace vag;
+
+namespace {
+
+template <class F>
+vag_status guarded(Ctx *c, F &&f) {
+  try {
+    f();
+    if (c) c->last_error.clear();
+    return VAG_OK;
+  } catch (const Error &e) {
+    if (c) c->last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    if (c) c->last_error = "host allocation failed";
+    return VAG_ENOMEM;
+  } catch (...) {
+    if (c) c->last_error = "unexpected internal error";
+    return VAG_ECUDA;
+  }
+}
+
+void check_mem(int mem) {
+  if (mem != VAG_MEM_HOST && mem != VAG_MEM_DEVICE) fail(VAG_EINVAL, "mem must be VAG_MEM_HOST or VAG_MEM_DEVICE");
+}
+
+cudaMemcpyKind to_dev(int mem) { return mem == VAG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind from_dev(int mem) { return mem == VAG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+template <class T>
+T *upload(System *s, const T *src, size_t n, int mem, const char *what) {
+  if (n && !src) fail(VAG_EINVAL, std::string(what) + " is NULL");
+  T *d = sys_alloc<T>(s, n);
+  if (n) VAG_CUDA(cudaMemcpyAsync(d, src, sizeof(T) * n, to_dev(mem), s->ctx->stream));
+  return d;
+}
+
+template <class T>
+void copy_in(System *s, T *dst, const T *src, size_t n, int mem, const char *what) {
+  if (n && !src) fail(VAG_EINVAL, std::string(what) + " is NULL");
+  if (n) VAG_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * n, to_dev(mem), s->ctx->stream));
+}
+
+template <class T>
+void copy_out(const System *s, T *dst, const T *src, size_t n, int mem) {
+  if (dst && n) VAG_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * n, from_dev(mem), s->ctx->stream));
+}
+
+void use_device(Ctx *c) { VAG_CUDA(cudaSetDevice(c->device)); }
+
+}  // namespace
+
+extern "C" {
+
+vag_status vag_ctx_create(int device, size_t mem_budget_bytes, vag_ctx **out) {
+  if (!out) return VAG_EINVAL;
+  *out = nullptr;
+  std::unique_ptr<vag_ctx> c(new (std::nothrow) vag_ctx());
+  if (!c) return VAG_ENOMEM;
+  vag_status st = guarded(&c->c, [&] {
+    int n = 0;
+    VAG_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) fail(VAG_EINVAL, "no such CUDA device");
+    c->c.device = device;
+    c->c.budget = mem_budget_bytes;
+    VAG_CUDA(cudaSetDevice(device));
+    VAG_CUDA(cudaStreamCreateWithFlags(&c->c.own_stream, cudaStreamNonBlocking));
+    c->c.stream = c->c.own_stream;
+  });
+  if (st != VAG_OK) return st;
+  *out = c.release();
+  return VAG_OK;
+}
+
+void vag_ctx_destroy(vag_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->c.own_stream) {
+    cudaStreamSynchronize(ctx->c.own_stream);
+    cudaStreamDestroy(ctx->c.own_stream);
+  }
+  delete ctx;
+}
+
+vag_status vag_ctx_set_stream(vag_ctx *ctx, void *stream) {
+  if (!ctx) return VAG_EINVAL;
+  return guarded(&ctx->c, [&] {
+    if (stream == nullptr) {
+      ctx->c.stream = ctx->c.own_stream;
+      return;
+    }
+    // the legacy default stream cannot be captured into CUDA graphs
+    if (stream == (void *)cudaStreamLegacy || stream == (void *)0)
+      fail(VAG_EINVAL, "pass a created stream, not the legacy default stream");
+    ctx->c.stream = (cudaStream_t)stream;
+  });
+}
+
+const char *vag_last_error(const vag_ctx *ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
+
+size_t vag_ctx_bytes_in_use(const vag_ctx *ctx) { return ctx ? ctx->c.in_use : 0; }
+
+vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *props, const vag_dirichlet *bc,
+                        int mem, vag_system **out) {
+  if (!ctx) return VAG_EINVAL;
+  if (out) *out = nullptr;
+  std::unique_ptr<vag_system> sys;
+  vag_status st = guarded(&ctx->c, [&] {
+    if (!mesh || !props || !bc || !out) fail(VAG_EINVAL, "null argument");
+    check_mem(mem);
+    if (mesh->n_nodes <= 0 || mesh->n_cells <= 0 || mesh->n_ff < 0) fail(VAG_EINVAL, "bad mesh sizes");
+    if (bc->n_dir <= 0) fail(VAG_EINVAL, "at least one Dirichlet node is required");
+    if (!(props->mu > 0.0)) fail(VAG_EINVAL, "mu must be positive");
+    if ((int64_t)mesh->n_nodes + mesh->n_ff + mesh->n_cells > 0x7fffffffLL) fail(VAG_EINVAL, "mesh too large");
+    use_device(&ctx->c);
+    sys.reset(new vag_system());
+    System *s = &sys->s;
+    s->ctx = &ctx->c;
+    s->nv = mesh->n_nodes;
+    s->nc = mesh->n_cells;
+    s->nf = mesh->n_ff;
+    s->nd = bc->n_dir;
+    s->n_cv = s->nv + s->nf + s->nc;
+    s->mu = props->mu;
+    VAG_CUDA(cudaEventCreate(&s->ev0));
+    VAG_CUDA(cudaEventCreate(&s->ev1));
+    s->status = sys_alloc<int>(s, 4);
+    s->xyz = upload(s, mesh->xyz, 3 * (size_t)s->nv, mem, "xyz");
+    s->cell_nodes = upload(s, mesh->cell_nodes, 8 * (size_t)s->nc, mem, "cell_nodes");
+    s->ff_nodes = upload(s, mesh->ff_nodes, 4 * (size_t)s->nf, mem, "ff_nodes");
+    s->dir_nodes = upload(s, bc->nodes, (size_t)s->nd, mem, "dirichlet nodes");
+    s->dir_vals = upload(s, bc->values, (size_t)s->nd, mem, "dirichlet values");
+    s->lam = upload(s, props->lambda_m, 6 * (size_t)s->nc, mem, "lambda_m");
+    s->lamf = upload(s, props->lambda_f, (size_t)s->nf, mem, "lambda_f");
+    s->df = upload(s, props->d_f, (size_t)s->nf, mem, "d_f");
+    symbolic_phase(s);
+    numeric_phase(s);
+  });
+  if (st != VAG_OK) {
+    if (sys) {
+      sys_free_all(&sys->s);
+      if (sys->s.ev0) cudaEventDestroy(sys->s.ev0);
+      if (sys->s.ev1) cudaEventDestroy(sys->s.ev1);
+    }
+    return st;
+  }
+  *out = sys.release();
+  return VAG_OK;
+}
+
+vag_status vag_update_props(vag_system *sys, const vag_props *props, int mem) {
+  if (!sys) return VAG_EINVAL;
+  System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    if (!props) fail(VAG_EINVAL, "null props");
+    check_mem(mem);
+    if (!(props->mu > 0.0)) fail(VAG_EINVAL, "mu must be positive");
+    use_device(s->ctx);
+    copy_in(s, s->lam, props->lambda_m, 6 * (size_t)s->nc, mem, "lambda_m");
+    copy_in(s, s->lamf, props->lambda_f, (size_t)s->nf, mem, "lambda_f");
+    copy_in(s, s->df, props->d_f, (size_t)s->nf, mem, "d_f");
+    s->mu = props->mu;
+    numeric_phase(s);
+    s->solved = false;
+    s->have_flux = false;
+  });
+}
+
+void vag_system_destroy(vag_system *sys) {
+  if (!sys) return;
+  System *s = &sys->s;
+  if (s->ctx && s->ctx->stream) cudaStreamSynchronize(s->ctx->stream);
+  if (s->pcg_graph) cudaGraphExecDestroy(s->pcg_graph);
+  if (s->ks_host) cudaFreeHost(s->ks_host);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
+  sys_free_all(s);
+  delete sys;
+}
+
+vag_status vag_system_get_info(const vag_system *sys, vag_system_info *info) {
+  if (!sys || !info) return VAG_EINVAL;
+  const System *s = &sys->s;
+  info->n_nodes = s->nv;
+  info->n_cells = s->nc;
+  info->n_ff = s->nf;
+  info->n_dir = s->nd;
+  info->n_rows = s->n_rows;
+  info->nnz = s->nnz;
+  info->n_frac_cells = s->n_fc;
+  info->n_cv = s->n_cv;
+  info->nnz_transport = s->nnz_t;
+  info->device_bytes = s->bytes;
+  return VAG_OK;
+}
+
+vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out, vag_solve_info *info) {
+  if (!sys) return VAG_EINVAL;
+  System *s = &sys->s;
+  vag_solve_info local{};
+  vag_solve_info *inf = info ? info : &local;
+  vag_status st = guarded(s->ctx, [&] {
+    if (!opts) fail(VAG_EINVAL, "null options");
+    check_mem(opts->mem);
+    if (!(opts->rtol > 0.0) || opts->maxit <= 0) fail(VAG_EINVAL, "rtol must be > 0 and maxit > 0");
+    if (opts->precision != VAG_FP64) fail(VAG_EINVAL, "precision not available in this build");
+    if (opts->precond != VAG_PC_JACOBI) fail(VAG_EINVAL, "preconditioner not available in this build");
+    use_device(s->ctx);
+    pcg_solve(s, opts, inf);
+    copy_out(s, u_out, s->u, (size_t)s->n_cv, opts->mem);
+    VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+    if (inf->status == VAG_EBREAKDOWN) fail(VAG_EBREAKDOWN, "CG breakdown: p^T A p <= 0 or NaN");
+    if (inf->status == VAG_ENOTCONVERGED)
+      fail(VAG_ENOTCONVERGED, "CG reached maxit above rtol (last iterate written)");
+  });
+  return st;
+}
+
+vag_status vag_spmv(vag_system *sys, const double *x, double *y, int mem) {
+  if (!sys) return VAG_EINVAL;
+  System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    if (!x || !y) fail(VAG_EINVAL, "null vector");
+    check_mem(mem);
+    use_device(s->ctx);
+    cudaStream_t st = s->ctx->stream;
+    if (mem == VAG_MEM_DEVICE) {
+      spmv_f64(s, x, y);
+    } else {
+      double *dx, *dy;
+      const size_t n = s->n_rows;
+      VAG_CUDA(cudaMallocAsync(&dx, sizeof(double) * n, st));
+      VAG_CUDA(cudaMallocAsync(&dy, sizeof(double) * n, st));
+      VAG_CUDA(cudaMemcpyAsync(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+      spmv_f64(s, dx, dy);
+      VAG_CUDA(cudaMemcpyAsync(y, dy, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+      VAG_CUDA(cudaFreeAsync(dx, st));
+      VAG_CUDA(cudaFreeAsync(dy, st));
+    }
+    VAG_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+vag_status vag_transport(vag_system *sys, const vag_transport_opts *o, double *c_inout, vag_transport_info *info) {
+  if (!sys) return VAG_EINVAL;
+  System *s = &sys->s;
+  vag_transport_info local{};
+  vag_transport_info *inf = info ? info : &local;
+  return guarded(s->ctx, [&] {
+    if (!o || !c_inout) fail(VAG_EINVAL, "null argument");
+    check_mem(o->mem);
+    if (!s->have_flux) fail(VAG_EINVAL, "no fluxes: call vag_solve or vag_set_fluxes first");
+    if (o->n_steps < 0) fail(VAG_EINVAL, "n_steps < 0");
+    if (!(o->omega >= 0.0 && o->omega < 1.0)) fail(VAG_EINVAL, "omega must be in [0, 1)");
+    if (!(o->cfl > 0.0) && !(o->dt > 0.0)) fail(VAG_EINVAL, "give cfl > 0 or dt > 0");
+    use_device(s->ctx);
+    cudaStream_t st = s->ctx->stream;
+    const size_t n = s->n_cv;
+    // stage porosities, cbar and c
+    if (!o->phi_m || (s->nf && !o->phi_f) || !o->cbar) fail(VAG_EINVAL, "null porosity or cbar");
+    double *stage;
+    const size_t tot = (size_t)s->nc + s->nf + s->nd + (o->mem == VAG_MEM_HOST ? n : 0);
+    VAG_CUDA(cudaMallocAsync(&stage, sizeof(double) * (tot ? tot : 1), st));
+    double *pm = stage, *pf = stage + s->nc, *cb = pf + s->nf;
+    VAG_CUDA(cudaMemcpyAsync(pm, o->phi_m, sizeof(double) * s->nc, to_dev(o->mem), st));
+    if (s->nf) VAG_CUDA(cudaMemcpyAsync(pf, o->phi_f, sizeof(double) * s->nf, to_dev(o->mem), st));
+    VAG_CUDA(cudaMemcpyAsync(cb, o->cbar, sizeof(double) * s->nd, to_dev(o->mem), st));
+    double *cdev = c_inout;
+    if (o->mem == VAG_MEM_HOST) {
+      cdev = cb + s->nd;
+      VAG_CUDA(cudaMemcpyAsync(cdev, c_inout, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    }
+    try {
+      transport_run(s, o, cdev, inf, pm, pf, cb);
+    } catch (...) {
+      cudaFreeAsync(stage, st);
+      throw;
+    }
+    if (o->mem == VAG_MEM_HOST)
+      VAG_CUDA(cudaMemcpyAsync(c_inout, cdev, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    VAG_CUDA(cudaFreeAsync(stage, st));
+    VAG_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+vag_status vag_export_system(const vag_system *sys, int32_t *rowptr, int32_t *col, double *val, double *rhs,
+                             int32_t *row_dof, int mem) {
+  if (!sys) return VAG_EINVAL;
+  const System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    check_mem(mem);
+    use_device(s->ctx);
+    copy_out(s, rowptr, s->rowptr, (size_t)s->n_rows + 1, mem);
+    copy_out(s, col, s->col, (size_t)s->nnz, mem);
+    copy_out(s, val, s->val, (size_t)s->nnz, mem);
+    copy_out(s, rhs, s->rhs, (size_t)s->n_rows, mem);
+    copy_out(s, row_dof, s->dof_of_row, (size_t)s->n_rows, mem);
+    VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  });
+}
+
+vag_status vag_export_fluxes(const vag_system *sys, double *Fcn, double *Fcf, double *Fff, int mem) {
+  if (!sys) return VAG_EINVAL;
+  const System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    check_mem(mem);
+    if (!s->have_flux) fail(VAG_EINVAL, "no fluxes yet");
+    use_device(s->ctx);
+    copy_out(s, Fcn, s->Fcn, 8 * (size_t)s->nc, mem);
+    copy_out(s, Fcf, s->Fcf, 6 * (size_t)s->nc, mem);
+    copy_out(s, Fff, s->Fff, 4 * (size_t)s->nf, mem);
+    VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  });
+}
+
+vag_status vag_set_fluxes(vag_system *sys, const double *Fcn, const double *Fcf, const double *Fff, int mem) {
+  if (!sys) return VAG_EINVAL;
+  System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    check_mem(mem);
+    if (!Fcn || !Fcf || (s->nf && !Fff)) fail(VAG_EINVAL, "null flux array");
+    use_device(s->ctx);
+    if (!s->Fcn) {
+      s->Fcn = sys_alloc<double>(s, 8 * (size_t)s->nc);
+      s->Fcf = sys_alloc<double>(s, 6 * (size_t)s->nc);
+      s->Fff = sys_alloc<double>(s, 4 * (size_t)(s->nf > 0 ? s->nf : 1));
+    }
+    copy_in(s, s->Fcn, Fcn, 8 * (size_t)s->nc, mem, "F_cell_nodes");
+    copy_in(s, s->Fcf, Fcf, 6 * (size_t)s->nc, mem, "F_cell_faces");
+    copy_in(s, s->Fff, Fff, 4 * (size_t)s->nf, mem, "F_frac");
+    VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+    s->have_flux = true;
+  });
+}
+
+vag_status vag_export_porous_volumes(const vag_system *sys, double *phi, int mem) {
+  if (!sys) return VAG_EINVAL;
+  const System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    check_mem(mem);
+    if (!s->phi) fail(VAG_EINVAL, "no porous volumes yet: call vag_transport first");
+    use_device(s->ctx);
+    copy_out(s, phi, s->phi, (size_t)s->n_cv, mem);
+    VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  });
+}
+
+}  // extern "C"

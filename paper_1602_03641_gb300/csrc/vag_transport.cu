@@ -1,0 +1,364 @@
+// Cell recovery, Darcy fluxes and the explicit upwind transport of Sec. 3.2.
+//
+//  k_recover     Eq. (eqschurcell): u_K = -(sum_nu M_K,nu u_nu) / M_KK.
+//  k_cell_flux   Eq. (VAGFluxMatrix): F_{K,nu} = sum_nu' a_{K,nu}^{nu'} (u_K - u_nu').
+//  k_ff_flux     Eq. (VAGFluxFracture): F_{sigma,s} = sum_s' a_{sigma,s}^{s'} (u_sigma - u_s').
+//  k_porous      porous volumes phi_K, phi_sigma, phi_s of Sec. 3.2.1.
+//  k_map_count / k_map_fill
+//                one explicit Euler step with the upwind fluxes of
+//                Eq. (darcyfluxH) is the linear map
+//                  c^{n+1}_mu = d_mu c^n_mu + sum_{nu upstream of mu} w_{mu,nu} c^n_nu,
+//                  d_mu = 1 - dt/phi_mu * (outflow of mu),  w >= 0,
+//                because every edge with F != 0 has one upstream end: its
+//                flux enters the downstream control volume with the upstream
+//                concentration and leaves the upstream one with it.  The map
+//                is built once per (fluxes, dt) as a CSR of the inflow edges;
+//                Dirichlet rows keep c = cbar (d = 1, no inflow).
+//  k_cfl         Eq. (eq_CFL): min over non-Dirichlet CVs of phi / outflow.
+//  k_step        c' = d c + W c (one thread per control volume).
+#include "vag_internal.cuh"
+#include "vag_reduce.cuh"
+#include "vag_hex.cuh"
+
+namespace vag {
+namespace {
+
+constexpr int TB = 256;
+
+__device__ __forceinline__ double mcK(const double *Mc, int nc, int i, int j, int K) {
+  return Mc[(size_t)hex::pidx(i, j) * nc + K];
+}
+__device__ __forceinline__ double mfcK(const double *Mfc, int n_fc, int lf, int k, int fi) {
+  return Mfc[(size_t)(lf * 6 + k) * n_fc + fi];
+}
+
+__global__ void k_recover(int nc, int nv, const int *__restrict__ cn, const int *__restrict__ cell_ff,
+                          const int *__restrict__ fc_index, int n_fc, const double *__restrict__ Mc,
+                          const double *__restrict__ Mfc, double *__restrict__ u, int nf) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nc) return;
+  double s = 0.0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) s = fma(mcK(Mc, nc, 0, 1 + b, K), u[cn[8 * (size_t)K + b]], s);
+  const int fi = fc_index[K];
+  if (fi >= 0) {
+    for (int lf = 0; lf < 6; ++lf) {
+      const int f = cell_ff[6 * (size_t)K + lf];
+      if (f >= 0) s = fma(mfcK(Mfc, n_fc, lf, 1, fi), u[nv + f], s);
+    }
+  }
+  u[(size_t)nv + nf + K] = -s / mcK(Mc, nc, 0, 0, K);
+}
+
+__global__ void k_cell_flux(int nc, int nv, int nf, const int *__restrict__ cn, const int *__restrict__ cell_ff,
+                            const int *__restrict__ fc_index, int n_fc, const double *__restrict__ Mc,
+                            const double *__restrict__ Mfc, const double *__restrict__ u, double *__restrict__ Fcn,
+                            double *__restrict__ Fcf) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nc) return;
+  const double uK = u[(size_t)nv + nf + K];
+  double du[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) du[b] = uK - u[cn[8 * (size_t)K + b]];
+  const int fi = fc_index[K];
+  double dus[6];
+  int ffid[6];
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) {
+    ffid[lf] = fi >= 0 ? cell_ff[6 * (size_t)K + lf] : -1;
+    dus[lf] = ffid[lf] >= 0 ? uK - u[nv + ffid[lf]] : 0.0;
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    double F = 0.0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) F = fma(mcK(Mc, nc, 1 + a, 1 + b, K), du[b], F);
+    if (fi >= 0) {
+#pragma unroll
+      for (int lf = 0; lf < 6; ++lf) {
+        const int t = hex::pos_on_face(lf, a);
+        if (t >= 0 && ffid[lf] >= 0) F = fma(mfcK(Mfc, n_fc, lf, 2 + t, fi), dus[lf], F);
+      }
+    }
+    Fcn[8 * (size_t)K + a] = F;
+  }
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) {
+    double F = 0.0;
+    if (ffid[lf] >= 0) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) F = fma(mfcK(Mfc, n_fc, lf, 2 + t, fi), du[hex::face(lf, t)], F);
+      F = fma(mfcK(Mfc, n_fc, lf, 0, fi), dus[lf], F);
+    }
+    Fcf[6 * (size_t)K + lf] = F;
+  }
+}
+
+__global__ void k_ff_flux(int nf, int nv, const int *__restrict__ ffn, const double *__restrict__ Mff,
+                          const double *__restrict__ u, double *__restrict__ Fff) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const double us = u[nv + f];
+  double du[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) du[t] = us - u[ffn[4 * (size_t)f + t]];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    double F = 0.0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F = fma(Mff[(size_t)((1 + t) * 5 + 1 + v) * nf + f], du[v], F);
+    Fff[4 * (size_t)f + t] = F;
+  }
+}
+
+struct TView {
+  int nv, nf, nc;
+  const int *cn, *ffn, *cell_ff, *ff_cells, *ff_lface, *node_dir, *node_isfrac;
+  const int *n2c_ptr, *n2c, *n2f_ptr, *n2f;
+  const double *cvol, *ffarea, *df, *phi_m, *phi_f;
+  const double *Fcn, *Fcf, *Fff;
+  double omega;
+};
+
+__global__ void k_porous(TView t, double *__restrict__ phi, int *status) {
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = t.nv + t.nf + t.nc;
+  if (mu >= n) return;
+  double p = 0.0;
+  if (mu < t.nv) {
+    const int s = mu;
+    if (t.node_dir[s] >= 0) { phi[mu] = 0.0; return; }
+    if (t.node_isfrac[s]) {
+      for (int e = t.n2f_ptr[s]; e < t.n2f_ptr[s + 1]; ++e) {
+        const int f = t.n2f[e] >> 2;
+        p += (t.omega * 0.25) * t.df[f] * t.ffarea[f] * t.phi_f[f];
+      }
+    } else {
+      for (int e = t.n2c_ptr[s]; e < t.n2c_ptr[s + 1]; ++e) {
+        const int K = t.n2c[e] >> 3;
+        p += (t.omega * 0.125) * t.cvol[K] * t.phi_m[K];
+      }
+    }
+  } else if (mu < t.nv + t.nf) {
+    const int f = mu - t.nv;
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cnt += t.node_dir[t.ffn[4 * (size_t)f + q]] < 0;
+    p = (1.0 - t.omega * 0.25 * cnt) * t.df[f] * t.ffarea[f] * t.phi_f[f];
+  } else {
+    const int K = mu - t.nv - t.nf;
+    int cnt = 0;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int s = t.cn[8 * (size_t)K + l];
+      cnt += (t.node_dir[s] < 0) && !t.node_isfrac[s];
+    }
+    p = (1.0 - t.omega * 0.125 * cnt) * t.cvol[K] * t.phi_m[K];
+  }
+  if (!(p > 0.0)) atomicOr(status, ST_NONPOSITIVE);
+  phi[mu] = p;
+}
+
+// Visit the edges of control volume mu: fn(F_in_view, neighbour) where
+// F_in_view > 0 means the flux enters mu from the neighbour (the neighbour is
+// upstream) and F_in_view < 0 means it leaves mu.
+template <class Fn>
+__device__ __forceinline__ void for_edges(const TView &t, int mu, Fn &&fn) {
+  if (mu < t.nv) {
+    const int s = mu;
+    for (int e = t.n2c_ptr[s]; e < t.n2c_ptr[s + 1]; ++e) {   // F_{K,s} > 0: K -> s
+      const int K = t.n2c[e] >> 3, a = t.n2c[e] & 7;
+      fn(t.Fcn[8 * (size_t)K + a], t.nv + t.nf + K);
+    }
+    for (int e = t.n2f_ptr[s]; e < t.n2f_ptr[s + 1]; ++e) {   // F_{sigma,s} > 0: sigma -> s
+      const int f = t.n2f[e] >> 2, q = t.n2f[e] & 3;
+      fn(t.Fff[4 * (size_t)f + q], t.nv + f);
+    }
+  } else if (mu < t.nv + t.nf) {
+    const int f = mu - t.nv;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) fn(-t.Fff[4 * (size_t)f + q], t.ffn[4 * (size_t)f + q]);
+    for (int c = 0; c < 2; ++c) {                                // F_{K,sigma} > 0: K -> sigma
+      const int K = t.ff_cells[2 * f + c];
+      if (K < 0) continue;
+      fn(t.Fcf[6 * (size_t)K + t.ff_lface[2 * f + c]], t.nv + t.nf + K);
+    }
+  } else {
+    const int K = mu - t.nv - t.nf;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) fn(-t.Fcn[8 * (size_t)K + a], t.cn[8 * (size_t)K + a]);
+#pragma unroll
+    for (int lf = 0; lf < 6; ++lf) {
+      const int f = t.cell_ff[6 * (size_t)K + lf];
+      if (f >= 0) fn(-t.Fcf[6 * (size_t)K + lf], t.nv + f);
+    }
+  }
+}
+
+__device__ __forceinline__ bool is_dir(const TView &t, int mu) { return mu < t.nv && t.node_dir[mu] >= 0; }
+
+// Per CV: number of inflow edges and the CFL ratio phi / outflow.
+__global__ void __launch_bounds__(TB) k_map_count(TView t, const double *__restrict__ phi, int *__restrict__ cnt,
+                                                  double *partials, unsigned *counter, double *dts) {
+  const int n = t.nv + t.nf + t.nc;
+  double best = INFINITY;
+  for (int mu = blockIdx.x * TB + threadIdx.x; mu < n; mu += gridDim.x * TB) {
+    if (is_dir(t, mu)) { cnt[mu] = 0; continue; }
+    int c = 0;
+    double out = 0.0;
+    for_edges(t, mu, [&](double Fin, int) {
+      if (Fin > 0.0) ++c;
+      else out -= Fin;
+    });
+    cnt[mu] = c;
+    if (out > 0.0) best = fmin(best, phi[mu] / out);
+  }
+  // min-reduction (order-independent); reuse the sum helper on -1/x is not
+  // exact, so reduce explicitly with shared memory
+  __shared__ double sh[TB / 32];
+  __shared__ bool last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = sh[0];
+    for (int w = 1; w < TB / 32; ++w) m = fmin(m, sh[w]);
+    partials[blockIdx.x] = m;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double m = INFINITY;
+    for (int b = 0; b < (int)gridDim.x; ++b) m = fmin(m, __ldcg(&partials[b]));
+    dts[0] = m;
+    *counter = 0u;
+  }
+}
+
+// dts[1] = cfl * dts[0] (cfl > 0) or the given dt.
+__global__ void k_pick_dt(double *dts, double cfl, double dt) { dts[1] = cfl > 0 ? cfl * dts[0] : dt; }
+
+__global__ void k_map_fill(TView t, const double *__restrict__ phi, const int *__restrict__ rowptr,
+                           const double *__restrict__ dts, double *__restrict__ diag, int *__restrict__ col,
+                           double *__restrict__ w) {
+  const int n = t.nv + t.nf + t.nc;
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mu >= n) return;
+  if (is_dir(t, mu)) { diag[mu] = 1.0; return; }
+  const double h = dts[1] / phi[mu];
+  int k = rowptr[mu];
+  double out = 0.0;
+  for_edges(t, mu, [&](double Fin, int nb) {
+    if (Fin > 0.0) {
+      col[k] = nb;
+      w[k] = h * Fin;
+      ++k;
+    } else {
+      out -= Fin;
+    }
+  });
+  diag[mu] = 1.0 - h * out;
+}
+
+__global__ void __launch_bounds__(TB) k_step(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                             const double *__restrict__ w, const double *__restrict__ diag,
+                                             const double *__restrict__ c, double *__restrict__ cn) {
+  const int mu = blockIdx.x * TB + threadIdx.x;
+  if (mu >= n) return;
+  double v = diag[mu] * c[mu];
+  const int b = rowptr[mu], e = rowptr[mu + 1];
+  for (int k = b; k < e; ++k) v = fma(w[k], __ldg(&c[col[k]]), v);
+  cn[mu] = v;
+}
+
+__global__ void k_set_dir(int nd, const int *__restrict__ dn, const double *__restrict__ cbar, double *__restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nd) c[dn[i]] = cbar[i];
+}
+
+}  // namespace
+
+void recover_cells_and_fluxes(System *s) {
+  cudaStream_t st = s->ctx->stream;
+  if (!s->Fcn) {
+    s->Fcn = sys_alloc<double>(s, 8 * (size_t)s->nc);
+    s->Fcf = sys_alloc<double>(s, 6 * (size_t)s->nc);
+    s->Fff = sys_alloc<double>(s, 4 * (size_t)(s->nf > 0 ? s->nf : 1));
+  }
+  k_recover<<<grid_for(s->nc, TB), TB, 0, st>>>(s->nc, s->nv, s->cell_nodes, s->cell_ff, s->fc_index, s->n_fc,
+                                                s->Mc, s->Mfc, s->u, s->nf);
+  k_cell_flux<<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, s->nv, s->nf, s->cell_nodes, s->cell_ff, s->fc_index,
+                                                    s->n_fc, s->Mc, s->Mfc, s->u, s->Fcn, s->Fcf);
+  if (s->nf) k_ff_flux<<<grid_for(s->nf, TB), TB, 0, st>>>(s->nf, s->nv, s->ff_nodes, s->Mff, s->u, s->Fff);
+  VAG_CHECK_LAUNCH();
+  s->have_flux = true;
+}
+
+// phi_m [nc], phi_f [nf], cbar [nd] already on the device.
+void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_transport_info *info,
+                   const double *phi_m, const double *phi_f, const double *cbar) {
+  cudaStream_t st = s->ctx->stream;
+  const int n = s->n_cv;
+  if (!s->phi) {
+    s->phi = sys_alloc<double>(s, n);
+    s->tdiag = sys_alloc<double>(s, n);
+    s->trowptr = sys_alloc<int>(s, (size_t)n + 1);
+    s->cbuf = sys_alloc<double>(s, 2 * (size_t)n);
+    s->dts = sys_alloc<double>(s, 4);
+  }
+  if (!s->partials) {
+    s->partials = sys_alloc<double>(s, 4 * (size_t)kMaxRedBlocks);
+    s->counter = sys_alloc<unsigned>(s, 4);
+    VAG_CUDA(cudaMemsetAsync(s->counter, 0, 4 * sizeof(unsigned), st));
+  }
+  TView t{s->nv, s->nf, s->nc, s->cell_nodes, s->ff_nodes, s->cell_ff, s->ff_cells, s->ff_lface,
+          s->node_dir, s->node_isfrac, s->n2c_ptr, s->n2c, s->n2f_ptr, s->n2f, s->cvol, s->ffarea, s->df,
+          phi_m, phi_f, s->Fcn, s->Fcf, s->Fff, o->omega};
+  VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
+  k_porous<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->status);
+  int *cnt;
+  VAG_CUDA(cudaMallocAsync(&cnt, sizeof(int) * ((size_t)n + 1), st));
+  int g = (int)std::min<int64_t>(grid_for(n, TB), std::min(num_sms() * 4, kMaxRedBlocks));
+  k_map_count<<<g, TB, 0, st>>>(t, s->phi, cnt, s->partials, s->counter, s->dts);
+  k_pick_dt<<<1, 1, 0, st>>>(s->dts, o->cfl, o->dt);
+  VAG_CHECK_LAUNCH();
+  const int64_t nnz_t = scan_exclusive(cnt, s->trowptr, n, st);
+  VAG_CUDA(cudaFreeAsync(cnt, st));
+  if (read_status(s) & ST_NONPOSITIVE) fail(VAG_EINVAL, "a control volume has a non-positive porous volume");
+  if (nnz_t > s->t_cap) {
+    // grow the inflow-edge arrays (kept across calls)
+    s->tcol = sys_alloc<int>(s, (size_t)nnz_t);
+    s->tval = sys_alloc<double>(s, (size_t)nnz_t);
+    s->t_cap = nnz_t;
+  }
+  s->nnz_t = nnz_t;
+  k_map_fill<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->trowptr, s->dts, s->tdiag, s->tcol, s->tval);
+  // c^0 with the Dirichlet values
+  double *c0 = s->cbuf, *c1 = s->cbuf + n;
+  VAG_CUDA(cudaMemcpyAsync(c0, c_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  k_set_dir<<<grid_for(s->nd, TB), TB, 0, st>>>(s->nd, s->dir_nodes, cbar, c0);
+  VAG_CHECK_LAUNCH();
+  VAG_CUDA(cudaEventRecord(s->ev0, st));
+  const int gs = grid_for(n, TB);
+  for (int k = 0; k < o->n_steps; ++k) {
+    k_step<<<gs, TB, 0, st>>>(n, s->trowptr, s->tcol, s->tval, s->tdiag, c0, c1);
+    std::swap(c0, c1);
+  }
+  VAG_CHECK_LAUNCH();
+  VAG_CUDA(cudaEventRecord(s->ev1, st));
+  VAG_CUDA(cudaMemcpyAsync(c_dev, c0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  double dts[2];
+  VAG_CUDA(cudaMemcpyAsync(dts, s->dts, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  VAG_CUDA(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+  info->dt_max = dts[0];
+  info->dt = dts[1];
+  info->steps = o->n_steps;
+  info->ms = ms;
+}
+
+}  // namespace vag

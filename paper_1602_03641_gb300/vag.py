@@ -1,0 +1,301 @@
+"""ctypes binding of libvag (include/vag.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name on the loaded
+library object (``lib()``), plus thin helpers (``Context``, ``System``) that
+turn numpy arrays (host) or torch CUDA tensors (device) into the plain
+pointers and sizes the ABI takes.  All arithmetic runs in the CUDA library;
+if ``libvag.so`` is missing or cannot be loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvag.so")
+
+VAG_OK, VAG_EINVAL, VAG_ENOMEM, VAG_EBUDGET, VAG_ENOTCONVERGED = 0, 1, 2, 3, 4
+VAG_EBREAKDOWN, VAG_ETIMEOUT, VAG_ECUDA, VAG_EMESH = 5, 6, 7, 8
+VAG_MEM_HOST, VAG_MEM_DEVICE = 0, 1
+VAG_FP64, VAG_MIXED = 0, 1
+VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG = 0, 1, 2
+
+STATUS_NAMES = {0: "VAG_OK", 1: "VAG_EINVAL", 2: "VAG_ENOMEM", 3: "VAG_EBUDGET", 4: "VAG_ENOTCONVERGED",
+                5: "VAG_EBREAKDOWN", 6: "VAG_ETIMEOUT", 7: "VAG_ECUDA", 8: "VAG_EMESH"}
+
+
+class vag_mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("xyz", C.c_void_p), ("n_cells", C.c_int32),
+                ("cell_nodes", C.c_void_p), ("n_ff", C.c_int32), ("ff_nodes", C.c_void_p)]
+
+
+class vag_props(C.Structure):
+    _fields_ = [("lambda_m", C.c_void_p), ("lambda_f", C.c_void_p), ("d_f", C.c_void_p), ("mu", C.c_double)]
+
+
+class vag_dirichlet(C.Structure):
+    _fields_ = [("n_dir", C.c_int32), ("nodes", C.c_void_p), ("values", C.c_void_p)]
+
+
+class vag_system_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_cells", C.c_int32), ("n_ff", C.c_int32), ("n_dir", C.c_int32),
+                ("n_rows", C.c_int32), ("nnz", C.c_int64), ("n_frac_cells", C.c_int32), ("n_cv", C.c_int32),
+                ("nnz_transport", C.c_int64), ("device_bytes", C.c_size_t)]
+
+
+class vag_solve_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int32),
+                ("mem", C.c_int)]
+
+
+class vag_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("outer", C.c_int32), ("rel_residual", C.c_double),
+                ("ms_setup", C.c_double), ("ms_solve", C.c_double), ("status", C.c_int)]
+
+
+class vag_transport_opts(C.Structure):
+    _fields_ = [("phi_m", C.c_void_p), ("phi_f", C.c_void_p), ("cbar", C.c_void_p), ("omega", C.c_double),
+                ("cfl", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int32), ("mem", C.c_int)]
+
+
+class vag_transport_info(C.Structure):
+    _fields_ = [("dt_max", C.c_double), ("dt", C.c_double), ("steps", C.c_int32), ("ms", C.c_double)]
+
+
+P = C.c_void_p
+_SIGS = {
+    "vag_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(P)]),
+    "vag_ctx_destroy": (None, [P]),
+    "vag_ctx_set_stream": (C.c_int, [P, P]),
+    "vag_last_error": (C.c_char_p, [P]),
+    "vag_ctx_bytes_in_use": (C.c_size_t, [P]),
+    "vag_assemble": (C.c_int, [P, C.POINTER(vag_mesh), C.POINTER(vag_props), C.POINTER(vag_dirichlet),
+                               C.c_int, C.POINTER(P)]),
+    "vag_update_props": (C.c_int, [P, C.POINTER(vag_props), C.c_int]),
+    "vag_system_destroy": (None, [P]),
+    "vag_system_get_info": (C.c_int, [P, C.POINTER(vag_system_info)]),
+    "vag_solve": (C.c_int, [P, C.POINTER(vag_solve_opts), P, C.POINTER(vag_solve_info)]),
+    "vag_spmv": (C.c_int, [P, P, P, C.c_int]),
+    "vag_transport": (C.c_int, [P, C.POINTER(vag_transport_opts), P, C.POINTER(vag_transport_info)]),
+    "vag_export_system": (C.c_int, [P, P, P, P, P, P, C.c_int]),
+    "vag_export_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
+    "vag_set_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
+    "vag_export_porous_volumes": (C.c_int, [P, P, C.c_int]),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load libvag.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1602_03641_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+class VagError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ----------------------------------------------------------------- marshal --
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=None):
+    """Data pointer of a numpy array (host) or torch tensor (device)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    a = x
+    if not (a.flags["C_CONTIGUOUS"]):
+        raise ValueError("array must be C-contiguous")
+    if dtype is not None and a.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {a.dtype}")
+    return a.ctypes.data
+
+
+def _mem_of(*xs):
+    kinds = set()
+    for x in xs:
+        if x is None:
+            continue
+        kinds.add(VAG_MEM_DEVICE if (_is_torch(x) and x.is_cuda) else VAG_MEM_HOST)
+    if len(kinds) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return kinds.pop() if kinds else VAG_MEM_HOST
+
+
+class Context:
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self._L = lib()
+        h = P()
+        st = self._L.vag_ctx_create(device, budget_bytes, C.byref(h))
+        if st != VAG_OK:
+            raise VagError(st, "vag_ctx_create failed")
+        self.h = h
+
+    def check(self, st):
+        if st != VAG_OK:
+            raise VagError(st, self._L.vag_last_error(self.h).decode())
+
+    def set_stream(self, stream_ptr: Optional[int]):
+        self.check(self._L.vag_ctx_set_stream(self.h, P(stream_ptr) if stream_ptr else None))
+
+    def bytes_in_use(self):
+        return int(self._L.vag_ctx_bytes_in_use(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.vag_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def assemble(self, xyz, cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values):
+        """Arrays: numpy (host) or CUDA tensors (device), float64 / int32."""
+        mem = _mem_of(xyz, cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, dir_nodes, dir_values)
+        m = vag_mesh(int(len(xyz) // 3 if xyz.ndim == 1 else xyz.shape[0]), _ptr(xyz, np.float64),
+                     int(cell_nodes.numel() // 8 if _is_torch(cell_nodes) else cell_nodes.size // 8),
+                     _ptr(cell_nodes, np.int32),
+                     int(ff_nodes.numel() // 4 if _is_torch(ff_nodes) else ff_nodes.size // 4),
+                     _ptr(ff_nodes, np.int32))
+        p = vag_props(_ptr(lambda_m, np.float64), _ptr(lambda_f, np.float64), _ptr(d_f, np.float64), float(mu))
+        nd = int(dir_nodes.numel() if _is_torch(dir_nodes) else dir_nodes.size)
+        b = vag_dirichlet(nd, _ptr(dir_nodes, np.int32), _ptr(dir_values, np.float64))
+        h = P()
+        self.check(self._L.vag_assemble(self.h, C.byref(m), C.byref(p), C.byref(b), mem, C.byref(h)))
+        return System(self, h)
+
+
+class System:
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self.h = h
+        self._L = ctx._L
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.vag_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> vag_system_info:
+        i = vag_system_info()
+        self.ctx.check(self._L.vag_system_get_info(self.h, C.byref(i)))
+        return i
+
+    def update_props(self, lambda_m, lambda_f, d_f, mu):
+        mem = _mem_of(lambda_m, lambda_f, d_f)
+        p = vag_props(_ptr(lambda_m, np.float64), _ptr(lambda_f, np.float64), _ptr(d_f, np.float64), float(mu))
+        self.ctx.check(self._L.vag_update_props(self.h, C.byref(p), mem))
+
+    def solve(self, out=None, precision=VAG_FP64, precond=VAG_PC_JACOBI, rtol=1e-12, maxit=20000,
+              raise_on_error=True):
+        """Returns (u, info); u over [nodes | ffaces | cells]."""
+        n = self.info().n_cv
+        if out is None:
+            out = np.empty(n)
+        mem = _mem_of(out)
+        o = vag_solve_opts(precision, precond, float(rtol), int(maxit), mem)
+        inf = vag_solve_info()
+        st = self._L.vag_solve(self.h, C.byref(o), _ptr(out, np.float64), C.byref(inf))
+        if raise_on_error:
+            self.ctx.check(st)
+        inf.ret = st
+        return out, inf
+
+    def spmv(self, x, y=None):
+        if y is None:
+            y = np.empty_like(x)
+        mem = _mem_of(x, y)
+        self.ctx.check(self._L.vag_spmv(self.h, _ptr(x, np.float64), _ptr(y, np.float64), mem))
+        return y
+
+    def transport(self, c, phi_m, phi_f, cbar, n_steps, cfl=0.9, dt=0.0, omega=0.5):
+        """c is updated in place (numpy or CUDA tensor, [n_cv])."""
+        mem = _mem_of(c, phi_m, phi_f, cbar)
+        o = vag_transport_opts(_ptr(phi_m, np.float64), _ptr(phi_f, np.float64), _ptr(cbar, np.float64),
+                               float(omega), float(cfl), float(dt), int(n_steps), mem)
+        inf = vag_transport_info()
+        self.ctx.check(self._L.vag_transport(self.h, C.byref(o), _ptr(c, np.float64), C.byref(inf)))
+        return inf
+
+    def export_system(self):
+        i = self.info()
+        rowptr = np.empty(i.n_rows + 1, np.int32)
+        col = np.empty(i.nnz, np.int32)
+        val = np.empty(i.nnz)
+        rhs = np.empty(i.n_rows)
+        row_dof = np.empty(i.n_rows, np.int32)
+        self.ctx.check(self._L.vag_export_system(self.h, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(rhs),
+                                                 _ptr(row_dof), VAG_MEM_HOST))
+        return dict(rowptr=rowptr, col=col, val=val, rhs=rhs, row_dof=row_dof)
+
+    def export_fluxes(self):
+        i = self.info()
+        Fcn = np.empty(8 * i.n_cells)
+        Fcf = np.empty(6 * i.n_cells)
+        Fff = np.empty(max(4 * i.n_ff, 1))
+        self.ctx.check(self._L.vag_export_fluxes(self.h, _ptr(Fcn), _ptr(Fcf), _ptr(Fff), VAG_MEM_HOST))
+        return Fcn.reshape(-1, 8), Fcf.reshape(-1, 6), Fff[:4 * i.n_ff].reshape(-1, 4)
+
+    def set_fluxes(self, Fcn, Fcf, Fff):
+        Fcn = np.ascontiguousarray(Fcn, np.float64)
+        Fcf = np.ascontiguousarray(Fcf, np.float64)
+        Fff = np.ascontiguousarray(Fff, np.float64)
+        self.ctx.check(self._L.vag_set_fluxes(self.h, _ptr(Fcn), _ptr(Fcf), _ptr(Fff) if Fff.size else None,
+                                              VAG_MEM_HOST))
+
+    def export_porous_volumes(self):
+        phi = np.empty(self.info().n_cv)
+        self.ctx.check(self._L.vag_export_porous_volumes(self.h, _ptr(phi), VAG_MEM_HOST))
+        return phi
+
+
+def assemble_problem(ctx: Context, pb, device=False):
+    """Marshal a ``vag_inputs.Problem``-like object (attributes xyz,
+    cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values)."""
+    arrs = [np.ascontiguousarray(pb.xyz, np.float64).ravel(), np.ascontiguousarray(pb.cell_nodes, np.int32).ravel(),
+            np.ascontiguousarray(pb.ff_nodes, np.int32).ravel(), np.ascontiguousarray(pb.lambda_m, np.float64).ravel(),
+            np.ascontiguousarray(pb.lambda_f, np.float64), np.ascontiguousarray(pb.d_f, np.float64)]
+    dn = np.ascontiguousarray(pb.dir_nodes, np.int32)
+    dv = np.ascontiguousarray(pb.dir_values, np.float64)
+    if device:
+        import torch
+        arrs = [torch.from_numpy(a).cuda() for a in arrs]
+        dn = torch.from_numpy(dn).cuda()
+        dv = torch.from_numpy(dv).cuda()
+    xyz, cn, ffn, lam, lamf, df = arrs
+    return ctx.assemble(xyz, cn, ffn, lam, lamf, df, pb.mu, dn, dv)
