@@ -1,0 +1,439 @@
+#!/usr/bin/env python3
+"""Throughput of the VAG Darcy + transport path on GB300 (one JSON line).
+
+One step = one realisation of the 64^3 workload pushed through the C ABI:
+  vag_assemble  (symbolic phase, local VAG matrices on 24 sub-tetrahedra per
+                 cell, fracture matrices, Schur row gather into CSR)
+  vag_solve     (preconditioned CG to ||r|| <= 1e-10 ||b||, cell recovery,
+                 fluxes)
+  vag_transport (porous volumes, CFL step at CFL 0.9, upwind map, 200 explicit
+                 steps)
+  vag_system_destroy.
+Workload: 64^3 hexahedra, interior nodes jittered by +-20% h (fracture-normal
+coordinates frozen), fractures on x=.5, y=.5, z=.5 and x=.25 (y<.5),
+lognormal matrix permeability (log10 std 1) with 10:1 anisotropy along a
+seeded axis, fracture/matrix ratio 1e4, p = 1 - x on x = 0, 1.
+
+`value` times steps whose inputs already sit in HBM (torch CUDA tensors);
+`e2e` times the same steps from pinned host buffers with the copies in and the
+pressure and concentration copies out inside the timed region.  L2 is flushed
+(256 MiB write) before every timed step.  Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import os
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS_EDGE = 64
+TRANSPORT_STEPS = 200
+RTOL = 1e-10
+METRIC = "Darcy solves/s (assemble + solve to 1e-10 + 200 transport steps)"
+UNIT = "solves/s"
+WORKLOAD = ("scale64: 64^3 jittered hex (262144 cells, 274625 nodes), 4 fractures (14336 fracture faces), "
+            "lognormal anisotropic Lambda_m, Lambda_f/Lambda_m = 1e4, FP64 CG to 1e-10, 200 upwind steps at CFL 0.9")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "chebyshev", "amg"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=N_CELLS_EDGE, help="mesh edge (profiling cases only)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers --
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs (rows of
+    the GPU with our UUID, else of the CUDA ordinal)."""
+    Q = ("uuid,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, uuid, ordinal):
+        self.uuid = (uuid or "").lower()
+        self.ordinal = str(ordinal)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = [[x.strip() for x in line.split(",")] for line in out.strip().splitlines()]
+        rows = [r for r in rows if len(r) >= 10]
+        mine = [r for r in rows if self.uuid and self.uuid in r[0].lower()]
+        if not mine:
+            mine = [r for r in rows if r[1] == self.ordinal]
+        sm, mx, reasons = [], [], set()
+        for f in mine:
+            try:
+                sm.append(float(f[2]))
+                mx.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[6:10]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, only if the
+    kernel's source is unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel_key)
+    if not d:
+        return None
+    if d.get("source_hash") != source_hash(d.get("sources", [])):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# -------------------------------------------------------------- CPU oracle --
+
+def oracle_sample():
+    """The oracle end to end on the 32^3 instance of the workload recipe,
+    each phase scaled to 64^3 by exact work counts (cells; nonzeros x CG
+    iterations; control volumes x steps).  Returns (seconds per full-size
+    solve, seconds of CPU work spent)."""
+    import vag_inputs as vi
+    from oracle import vag_oracle as vo
+    with open(os.path.join(ROOT, "oracle", "cpu_baseline_counts.json")) as f:
+        cnt = json.load(f)
+    full, smp = cnt["scale64"], cnt["scale32"]
+    pb = vi.config_scale64(32)
+    t0 = time.perf_counter()
+    m = vo.Mesh(pb)
+    cms = vo._all_cell_matrices(pb, m)
+    fm = vo.fracture_local_matrices(pb, m)
+    A = vo.assemble_full(pb, m, cms, fm)
+    S, b, R = vo.schur_system(pb, A)
+    t1 = time.perf_counter()
+    x, it = vo.pcg_jacobi(S, b, rtol=RTOL, maxit=100000)
+    t2 = time.perf_counter()
+    u = np.zeros(A.shape[0]); u[pb.dir_nodes] = pb.dir_values; u[R] = x
+    u = vo.recover_cells(pb, A, u)
+    Fc = [vo.cell_fluxes(cm, u) for cm in cms]
+    Ff = vo.fracture_fluxes(fm, u)
+    tr = vo.Transport(pb, cms, fm, Fc, Ff, omega=0.5, mesh=m)
+    dt = 0.9 * tr.cfl_dt()
+    t3 = time.perf_counter()
+    c = pb.c0()
+    for _ in range(TRANSPORT_STEPS):
+        c = tr.step(c, dt)
+    t4 = time.perf_counter()
+    s_cells = full["n_cells"] / smp["n_cells"]
+    s_pcg = (full["nnz"] * full["oracle_pcg_iterations"]) / (smp["nnz"] * max(it, 1))
+    s_cv = full["n_cv"] / smp["n_cv"]
+    scaled = (t1 - t0) * s_cells + (t2 - t1) * s_pcg + (t3 - t2) * s_cells + (t4 - t3) * s_cv
+    return scaled, t4 - t0
+
+
+def cpu_baseline_block(n_samples=2):
+    tot, spent = 0.0, 0.0
+    for _ in range(n_samples):
+        s, w = oracle_sample()
+        tot += s
+        spent += w
+    return {"value": n_samples / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{n_samples} complete oracle runs (numpy/scipy FP64, one thread) of the same recipe at "
+                       f"32^3, each phase scaled to 64^3 by exact work counts (cells; nnz x the oracle's own "
+                       f"Jacobi-CG iteration count at 64^3; control volumes x 200 steps); "
+                       f"{spent:.1f} s of CPU work")}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample()
+    times, spent = [], 0.0
+    for _ in range(args.steps):
+        s, w = oracle_sample()
+        times.append(s)
+        spent += w
+    value = args.steps / sum(times)
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": (f"per step: one complete oracle run of the recipe at 32^3 scaled to 64^3 by exact work "
+                      f"counts; {spent:.1f} s of CPU work over {args.steps} steps")}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "solver": "Jacobi-CG (oracle)"},
+        "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                     "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------- GPU arm --
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_1602_03641_gb300 as pkg
+    import vag_inputs as vi
+
+    precond = {"jacobi": pkg.VAG_PC_JACOBI, "chebyshev": pkg.VAG_PC_CHEBYSHEV, "amg": pkg.VAG_PC_AMG}[args.precond]
+    pb = vi.config_scale64(args.n)
+    host = {
+        "xyz": pb.xyz.ravel(), "cn": pb.cell_nodes.ravel(), "ffn": pb.ff_nodes.ravel(),
+        "lam": pb.lambda_m.ravel(), "lamf": pb.lambda_f, "df": pb.d_f,
+        "dn": pb.dir_nodes, "dv": pb.dir_values, "phm": pb.phi_m, "phf": pb.phi_f, "cb": pb.cbar, "c0": pb.c0(),
+    }
+    host = {k: np.ascontiguousarray(v) for k, v in host.items()}
+    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    # pinned host copies for the end-to-end leg
+    pin = {}
+    for k, v in host.items():
+        t = torch.empty(v.shape, dtype=torch.from_numpy(v).dtype, pin_memory=True)
+        t.copy_(torch.from_numpy(v))
+        pin[k] = t.numpy()
+    n_cv = pb.n_nodes + pb.n_ff + pb.n_cells
+    u_pin = torch.empty(n_cv, dtype=torch.float64, pin_memory=True).numpy()
+    c_pin = torch.empty(n_cv, dtype=torch.float64, pin_memory=True).numpy()
+
+    ctx = pkg.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.set_stream(stream.cuda_stream)
+    u_dev = torch.empty(n_cv, dtype=torch.float64, device=dev)
+    c_dev = torch.empty(n_cv, dtype=torch.float64, device=dev)
+    flush_buf = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
+
+    def step_device():
+        s = ctx.assemble(d["xyz"], d["cn"], d["ffn"], d["lam"], d["lamf"], d["df"], pb.mu, d["dn"], d["dv"])
+        _, info = s.solve(out=u_dev, precond=precond, rtol=RTOL, maxit=100000)
+        with torch.cuda.stream(stream):
+            c_dev.copy_(d["c0"])
+        tinf = s.transport(c_dev, d["phm"], d["phf"], d["cb"], n_steps=TRANSPORT_STEPS, cfl=0.9)
+        s.close()
+        return info, tinf
+
+    def step_device_prec(precision, rtol):
+        s = ctx.assemble(d["xyz"], d["cn"], d["ffn"], d["lam"], d["lamf"], d["df"], pb.mu, d["dn"], d["dv"])
+        _, info = s.solve(out=u_dev, precision=precision, precond=precond, rtol=rtol, maxit=100000)
+        with torch.cuda.stream(stream):
+            c_dev.copy_(d["c0"])
+        tinf = s.transport(c_dev, d["phm"], d["phf"], d["cb"], n_steps=TRANSPORT_STEPS, cfl=0.9)
+        s.close()
+        return info, tinf
+
+    def step_host():
+        s = ctx.assemble(pin["xyz"], pin["cn"], pin["ffn"], pin["lam"], pin["lamf"], pin["df"], pb.mu,
+                         pin["dn"], pin["dv"])
+        _, info = s.solve(out=u_pin, precond=precond, rtol=RTOL, maxit=100000)
+        c_pin[:] = pin["c0"]
+        tinf = s.transport(c_pin, pin["phm"], pin["phf"], pin["cb"], n_steps=TRANSPORT_STEPS, cfl=0.9)
+        s.close()
+        return info, tinf
+
+    def flush():
+        with torch.cuda.stream(stream):
+            flush_buf.zero_()
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        infos = []
+        for i in range(k):
+            flush()
+            evs[i][0].record(stream)
+            infos.append(fn())
+            evs[i][1].record(stream)
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in evs], infos
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+    gpu_uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    sampler = ClockSampler(str(gpu_uuid) if gpu_uuid is not None else None, local)
+    lc0 = pkg.launch_count()
+    ms, infos = timed(step_device, args.steps)
+    lc1 = pkg.launch_count()
+    barrier()
+    clocks = sampler.stop()
+    tot = sum(ms)
+    if world > 1:
+        t = torch.tensor([tot], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    value = world * args.steps / (tot / 1e3)
+
+    # end to end from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        step_host()
+        barrier()
+        ms_h, _ = timed(step_host, args.steps)
+        tot_h = sum(ms_h)
+        if world > 1:
+            t = torch.tensor([tot_h], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_h = float(t.item())
+        h2d = sum(pin[k].nbytes for k in ["xyz", "cn", "ffn", "lam", "lamf", "df", "dn", "dv", "phm", "phf", "cb",
+                                         "c0"])
+        e2e = {"value": world * args.steps / (tot_h / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(u_pin.nbytes + c_pin.nbytes), "ms_per_step": tot_h / args.steps}
+
+    # mixed precision (FP32 inner CG in FP64 refinement) vs FP64 CG, both to a
+    # 1e-8 relative residual, same step otherwise
+    cmp = {}
+    for name, prec in (("fp64", pkg.VAG_FP64), ("mixed", pkg.VAG_MIXED)):
+        step_device_prec(prec, 1e-8)
+        ms_c, inf_c = timed(lambda: step_device_prec(prec, 1e-8), max(3, args.steps // 2))
+        cmp[name] = {"solves_per_s": len(ms_c) / (sum(ms_c) / 1e3), "ms_per_step": sum(ms_c) / len(ms_c),
+                     "solve_ms": inf_c[-1][0].ms_solve, "iterations": inf_c[-1][0].iterations,
+                     "refinements": inf_c[-1][0].outer, "rel_residual": inf_c[-1][0].rel_residual}
+    cmp["mixed_over_fp64"] = cmp["mixed"]["solves_per_s"] / cmp["fp64"]["solves_per_s"]
+
+    # kernel rooflines: SpMV of the eliminated system and one transport step,
+    # CUDA events on the stream the library launches on
+    peak, peak_kind = measured_peaks()
+    s = ctx.assemble(d["xyz"], d["cn"], d["ffn"], d["lam"], d["lamf"], d["df"], pb.mu, d["dn"], d["dv"])
+    inf = s.info()
+    x = torch.rand(inf.n_rows, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    L = pkg.lib()
+    for _ in range(20):
+        L.vag_spmv(s.h, x.data_ptr(), y.data_ptr(), pkg.VAG_MEM_DEVICE)
+    R = 400
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    for _ in range(R):
+        L.vag_spmv(s.h, x.data_ptr(), y.data_ptr(), pkg.VAG_MEM_DEVICE)
+    e1.record(stream)
+    stream.synchronize()
+    spmv_ms = e0.elapsed_time(e1) / R
+    spmv_bytes = inf.nnz * 12 + (inf.n_rows + 1) * 4 + inf.n_rows * 16
+    s.solve(out=u_dev, precond=precond, rtol=RTOL, maxit=100000)
+    tms = {}
+    for nst in (20, 420):
+        with torch.cuda.stream(stream):
+            c_dev.copy_(d["c0"])
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        tinf = s.transport(c_dev, d["phm"], d["phf"], d["cb"], n_steps=nst, cfl=0.9)
+        eb.record(stream)
+        stream.synchronize()
+        tms[nst] = ea.elapsed_time(eb)
+    inf = s.info()
+    tstep_ms = (tms[420] - tms[20]) / 400
+    tstep_bytes = inf.n_cv * (8 + 8 + 8 + 4) + inf.nnz_transport * 12
+    s.close()
+
+    iters = [i[0].iterations for i in infos]
+    spmv_share = (statistics.mean(iters) + 1) * spmv_ms / (tot / args.steps)
+    trans_share = TRANSPORT_STEPS * tstep_ms / (tot / args.steps)
+    kern = {
+        "spmv_csr_f64": {"ms": spmv_ms, "bytes": spmv_bytes, "gbs": spmv_bytes / spmv_ms / 1e6,
+                         "share_of_step": spmv_share},
+        "transport_step": {"ms": tstep_ms, "bytes": tstep_bytes, "gbs": tstep_bytes / tstep_ms / 1e6,
+                           "share_of_step": trans_share},
+    }
+    dom = "spmv_csr_f64" if spmv_share >= trans_share else "transport_step"
+    ach = kern[dom]["gbs"]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind, "traffic": ncu_traffic(dom),
+            "bytes_per_launch": kern[dom]["bytes"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.n == N_CELLS_EDGE else f"scale{args.n} (profiling case)",
+                       "precond": args.precond, "rtol": RTOL,
+                       "transport_steps": TRANSPORT_STEPS, "n_rows": inf.n_rows, "nnz": inf.nnz,
+                       "n_cv": inf.n_cv, "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "cg_iterations": iters[-1], "rel_residual": infos[-1][0].rel_residual,
+            "phases_ms": {"solve": infos[-1][0].ms_solve, "transport_steps": infos[-1][1].ms},
+            "spmv_gbs": kern["spmv_csr_f64"]["gbs"], "kernels": kern,
+            "roofline": roof, "gpu_launches": int(lc1 - lc0), "clocks": clocks, "e2e": e2e,
+            "mixed_vs_fp64_at_1e-8": cmp,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_block()
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

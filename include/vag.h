@@ -109,6 +109,9 @@ typedef struct {
  * memory all systems of this context may hold (0 = no cap).  The context owns
  * a non-blocking stream unless vag_ctx_set_stream() supplies one. */
 vag_status vag_ctx_create(int device, size_t mem_budget_bytes, vag_ctx **out);
+/* Release the context.  Systems created from it stay valid; the context's
+ * resources are freed with the last of them.  No new system may be created
+ * from a destroyed context. */
 void vag_ctx_destroy(vag_ctx *ctx);
 /* Use the caller's cudaStream_t (passed as void*); NULL restores the
  * context's own stream.  Every later call of this context runs on it. */
@@ -117,6 +120,9 @@ vag_status vag_ctx_set_stream(vag_ctx *ctx, void *cuda_stream);
 const char *vag_last_error(const vag_ctx *ctx);
 /* Device bytes currently held by the context's systems. */
 size_t vag_ctx_bytes_in_use(const vag_ctx *ctx);
+/* Number of CUDA kernels this library has launched in this process (kernels
+ * inside a replayed CUDA graph count once per replay).  For instrumentation. */
+unsigned long long vag_launch_count(void);
 
 /* --------------------------------------------------------------- assembly */
 
@@ -136,6 +142,27 @@ size_t vag_ctx_bytes_in_use(const vag_ctx *ctx);
  */
 vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *props,
                         const vag_dirichlet *bc, int mem, vag_system **out);
+/*
+ * Batch of independent realisations in one system handle: the n_sys meshes
+ * are assembled as their disjoint union (node, cell and fracture-face ids of
+ * system i are offset by the sizes of systems 0..i-1), so one symbolic phase,
+ * one numeric phase, one Krylov loop and one transport loop serve the whole
+ * batch.  Each system keeps its own CG scalars and convergence test and its
+ * own CFL step, and its arithmetic is independent of the other systems: a
+ * system gives bitwise the same results alone or in any batch.  meshes,
+ * props, bcs: arrays of n_sys structs (per-system ids, 0-based); every system
+ * must have the same mu.  Vectors of the batch (u_out, c_inout, phi_m, ...)
+ * are the union's: [all nodes | all fracture faces | all cells], each block
+ * ordered by system; vag_system_get_batch gives the offsets.
+ */
+vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshes, const vag_props *props,
+                              const vag_dirichlet *bcs, int mem, vag_system **out);
+/* Layout of a batch: n_sys, and (arrays of n_sys+1, any may be NULL) the first
+ * node, fracture face, cell and Krylov row of each system.  A single system is
+ * a batch of one. */
+vag_status vag_system_get_batch(const vag_system *sys, int32_t *n_sys, int32_t *node_start, int32_t *ff_start,
+                                int32_t *cell_start, int32_t *row_start);
+
 /* Re-run the numeric phase with new properties on the same mesh. */
 vag_status vag_update_props(vag_system *sys, const vag_props *props, int mem);
 void vag_system_destroy(vag_system *sys);
@@ -182,7 +209,13 @@ typedef struct {
 vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
                      vag_solve_info *info);
 
-/* y = A x on the Krylov rows of the eliminated system (FP64).  x, y: [n_rows]. */
+/* Per-system results of the last vag_solve of a batch: infos [n_sys]
+ * (ms_setup and ms_solve are 0; vag_solve reports the batch's times). */
+vag_status vag_solve_get_infos(const vag_system *sys, vag_solve_info *infos);
+
+/* y = A x on the Krylov rows of the eliminated system (FP64).  x, y: [n_rows].
+ * With VAG_MEM_DEVICE the call is stream-ordered on the context stream and
+ * returns without waiting; with VAG_MEM_HOST it returns after y is written. */
 vag_status vag_spmv(vag_system *sys, const double *x, double *y, int mem);
 
 /* -------------------------------------------------------------- transport */
@@ -200,8 +233,9 @@ typedef struct {
 } vag_transport_opts;
 
 typedef struct {
-  double dt_max;         /* the CFL bound min(dt_M, dt_F, dt_V)               */
-  double dt;             /* the step used                                     */
+  double dt_max;         /* the CFL bound min(dt_M, dt_F, dt_V) (a batch: the
+                            smallest over its systems)                        */
+  double dt;             /* the step used (a batch: the smallest)             */
   int32_t steps;
   double ms;             /* device time of the steps                          */
 } vag_transport_info;
@@ -216,6 +250,10 @@ typedef struct {
  */
 vag_status vag_transport(vag_system *sys, const vag_transport_opts *opts, double *c_inout,
                          vag_transport_info *info);
+
+/* Per-system CFL bound and step of the last vag_transport: [n_sys] each (a
+ * system with no outflow anywhere has bound +inf and step 0 under cfl > 0). */
+vag_status vag_transport_get_dts(const vag_system *sys, double *dt_max, double *dt);
 
 /* ----------------------------------------------------- inspection / tests */
 

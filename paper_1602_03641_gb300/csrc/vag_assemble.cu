@@ -309,19 +309,21 @@ void numeric_phase(System *s) {
   VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   const double inv_mu = 1.0 / s->mu;
   k_cell_local<<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, s->cell_nodes, s->xyz, s->lam, inv_mu, s->cell_ff,
-                                                      s->fc_index, s->n_fc, s->Mc, s->Mfc, s->cvol, s->status);
+                                                      s->fc_index, s->n_fc, s->Mc, s->Mfc, s->cvol, s->status); note_launches(1);
   VAG_CHECK_LAUNCH();
   if (s->nf) {
     k_ff_local<<<grid_for(s->nf, 128), 128, 0, st>>>(s->nf, s->ff_nodes, s->xyz, s->lamf, s->df, inv_mu, s->Mff,
-                                                      s->ffarea, s->status);
+                                                      s->ffarea, s->status); note_launches(1);
     VAG_CHECK_LAUNCH();
   }
   GatherView g{s->nv, s->nc, s->nf, s->n_fc, s->cell_nodes, s->ff_nodes, s->node_dir, s->cell_ff,
                s->ff_cells, s->ff_lface, s->fc_index, s->n2c_ptr, s->n2c, s->n2f_ptr, s->n2f,
                s->row_of_dof, s->dof_of_row, s->rowptr, s->col, s->diag_pos, s->Mc, s->Mfc, s->Mff,
                s->dir_vals, s->val, s->rhs, s->dinv};
-  k_gather_rows<<<grid_for(s->n_rows, 128), 128, 0, st>>>(g, s->n_rows, s->status);
+  k_gather_rows<<<grid_for(s->n_rows, 128), 128, 0, st>>>(g, s->n_rows, s->status); note_launches(1);
   VAG_CHECK_LAUNCH();
+  if (s->sval) sell_values(s);
+  s->mx.stale = true;
   const int stv = read_status(s);
   if (stv & ST_BAD_GEOMETRY) fail(VAG_EMESH, "degenerate sub-tetrahedron or fracture triangle");
   if (stv & ST_NONPOSITIVE) fail(VAG_EINVAL, "non-positive diagonal in the eliminated system");

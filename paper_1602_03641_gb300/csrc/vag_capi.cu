@@ -56,6 +56,54 @@ void copy_out(const System *s, T *dst, const T *src, size_t n, int mem) {
 
 void use_device(Ctx *c) { VAG_CUDA(cudaSetDevice(c->device)); }
 
+// Segment starts of a batch (host vectors already filled) copied to the device.
+void upload_segments(System *s) {
+  Segments &g = s->seg;
+  const int n1 = g.n_sys + 1;
+  g.d_node_start = upload(s, g.node_start.data(), n1, VAG_MEM_HOST, "node_start");
+  g.d_ff_start = upload(s, g.ff_start.data(), n1, VAG_MEM_HOST, "ff_start");
+  g.d_cell_start = upload(s, g.cell_start.data(), n1, VAG_MEM_HOST, "cell_start");
+  g.d_row_start = sys_alloc<int>(s, n1);
+  VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+}
+
+__global__ void k_add_offset(int *a, int64_t n, int off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += off;
+}
+
+void free_ctx(vag_ctx *ctx) {
+  if (ctx->c.own_stream) {
+    cudaStreamSynchronize(ctx->c.own_stream);
+    cudaStreamDestroy(ctx->c.own_stream);
+  }
+  delete ctx;
+}
+
+// A system counts against its context; a context whose destruction was
+// requested while systems were alive is freed with its last system.
+void destroy_system(vag_system *sys) {
+  if (!sys) return;
+  System *s = &sys->s;
+  Ctx *c = s->ctx;
+  if (c && c->stream) cudaStreamSynchronize(c->stream);
+  if (s->pcg_graph) cudaGraphExecDestroy(s->pcg_graph);
+  if (s->mx.graph) cudaGraphExecDestroy(s->mx.graph);
+  if (s->pcg_graph_amg) cudaGraphExecDestroy(s->pcg_graph_amg);
+  amg_free(s);
+  if (s->ks_host) cudaFreeHost(s->ks_host);
+  if (s->n_done_host) cudaFreeHost(s->n_done_host);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
+  sys_free_all(s);
+  const bool counted = s->counted;
+  delete sys;
+  if (c && counted) {
+    c->live_systems -= 1;
+    if (c->destroy_requested && c->live_systems == 0) free_ctx(c->owner);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -71,6 +119,7 @@ vag_status vag_ctx_create(int device, size_t mem_budget_bytes, vag_ctx **out) {
     if (device < 0 || device >= n) fail(VAG_EINVAL, "no such CUDA device");
     c->c.device = device;
     c->c.budget = mem_budget_bytes;
+    c->c.owner = c.get();
     VAG_CUDA(cudaSetDevice(device));
     VAG_CUDA(cudaStreamCreateWithFlags(&c->c.own_stream, cudaStreamNonBlocking));
     c->c.stream = c->c.own_stream;
@@ -81,12 +130,9 @@ vag_status vag_ctx_create(int device, size_t mem_budget_bytes, vag_ctx **out) {
 }
 
 void vag_ctx_destroy(vag_ctx *ctx) {
-  if (!ctx) return;
-  if (ctx->c.own_stream) {
-    cudaStreamSynchronize(ctx->c.own_stream);
-    cudaStreamDestroy(ctx->c.own_stream);
-  }
-  delete ctx;
+  if (!ctx || ctx->c.destroy_requested) return;
+  ctx->c.destroy_requested = true;
+  if (ctx->c.live_systems == 0) free_ctx(ctx);
 }
 
 vag_status vag_ctx_set_stream(vag_ctx *ctx, void *stream) {
@@ -107,6 +153,8 @@ const char *vag_last_error(const vag_ctx *ctx) { return ctx ? ctx->c.last_error.
 
 size_t vag_ctx_bytes_in_use(const vag_ctx *ctx) { return ctx ? ctx->c.in_use : 0; }
 
+unsigned long long vag_launch_count(void) { return launches_so_far(); }
+
 vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *props, const vag_dirichlet *bc,
                         int mem, vag_system **out) {
   if (!ctx) return VAG_EINVAL;
@@ -122,7 +170,10 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
     use_device(&ctx->c);
     sys.reset(new vag_system());
     System *s = &sys->s;
+    if (ctx->c.destroy_requested) fail(VAG_EINVAL, "context already destroyed");
     s->ctx = &ctx->c;
+    s->counted = true;
+    ctx->c.live_systems += 1;
     s->nv = mesh->n_nodes;
     s->nc = mesh->n_cells;
     s->nf = mesh->n_ff;
@@ -140,18 +191,148 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
     s->lam = upload(s, props->lambda_m, 6 * (size_t)s->nc, mem, "lambda_m");
     s->lamf = upload(s, props->lambda_f, (size_t)s->nf, mem, "lambda_f");
     s->df = upload(s, props->d_f, (size_t)s->nf, mem, "d_f");
+    Segments &g = s->seg;
+    g.n_sys = 1;
+    g.node_start = {0, s->nv};
+    g.ff_start = {0, s->nf};
+    g.cell_start = {0, s->nc};
+    g.dir_start = {0, s->nd};
+    upload_segments(s);
     symbolic_phase(s);
+    build_tiles(s);
+    build_sell(s);
     numeric_phase(s);
   });
   if (st != VAG_OK) {
-    if (sys) {
-      sys_free_all(&sys->s);
-      if (sys->s.ev0) cudaEventDestroy(sys->s.ev0);
-      if (sys->s.ev1) cudaEventDestroy(sys->s.ev1);
-    }
+    destroy_system(sys.release());
     return st;
   }
   *out = sys.release();
+  return VAG_OK;
+}
+
+vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshes, const vag_props *props,
+                              const vag_dirichlet *bcs, int mem, vag_system **out) {
+  if (!ctx) return VAG_EINVAL;
+  if (out) *out = nullptr;
+  std::unique_ptr<vag_system> sys;
+  vag_status st = guarded(&ctx->c, [&] {
+    if (!meshes || !props || !bcs || !out || n_sys <= 0) fail(VAG_EINVAL, "null argument or n_sys <= 0");
+    check_mem(mem);
+    int64_t nv = 0, nc = 0, nf = 0, nd = 0;
+    for (int i = 0; i < n_sys; ++i) {
+      const vag_mesh &m = meshes[i];
+      if (m.n_nodes <= 0 || m.n_cells <= 0 || m.n_ff < 0) fail(VAG_EINVAL, "bad mesh sizes in system " + std::to_string(i));
+      if (bcs[i].n_dir <= 0) fail(VAG_EINVAL, "system " + std::to_string(i) + " has no Dirichlet node");
+      if (!(props[i].mu > 0.0)) fail(VAG_EINVAL, "mu must be positive");
+      if (props[i].mu != props[0].mu) fail(VAG_EINVAL, "all systems of a batch must share mu");
+      nv += m.n_nodes; nc += m.n_cells; nf += m.n_ff; nd += bcs[i].n_dir;
+    }
+    if (nv + nf + nc > 0x7fffffffLL || 8 * nc > 0x7fffffffLL) fail(VAG_EINVAL, "batch too large");
+    use_device(&ctx->c);
+    sys.reset(new vag_system());
+    System *s = &sys->s;
+    if (ctx->c.destroy_requested) fail(VAG_EINVAL, "context already destroyed");
+    s->ctx = &ctx->c;
+    s->counted = true;
+    ctx->c.live_systems += 1;
+    s->nv = (int)nv; s->nc = (int)nc; s->nf = (int)nf; s->nd = (int)nd;
+    s->n_cv = s->nv + s->nf + s->nc;
+    s->mu = props[0].mu;
+    VAG_CUDA(cudaEventCreate(&s->ev0));
+    VAG_CUDA(cudaEventCreate(&s->ev1));
+    s->status = sys_alloc<int>(s, 4);
+    Segments &g = s->seg;
+    g.n_sys = n_sys;
+    g.node_start.assign(n_sys + 1, 0); g.ff_start.assign(n_sys + 1, 0);
+    g.cell_start.assign(n_sys + 1, 0); g.dir_start.assign(n_sys + 1, 0);
+    for (int i = 0; i < n_sys; ++i) {
+      g.node_start[i + 1] = g.node_start[i] + meshes[i].n_nodes;
+      g.ff_start[i + 1] = g.ff_start[i] + meshes[i].n_ff;
+      g.cell_start[i + 1] = g.cell_start[i] + meshes[i].n_cells;
+      g.dir_start[i + 1] = g.dir_start[i] + bcs[i].n_dir;
+    }
+    s->xyz = sys_alloc<double>(s, 3 * (size_t)nv);
+    s->cell_nodes = sys_alloc<int>(s, 8 * (size_t)nc);
+    s->ff_nodes = sys_alloc<int>(s, 4 * (size_t)nf);
+    s->dir_nodes = sys_alloc<int>(s, (size_t)nd);
+    s->dir_vals = sys_alloc<double>(s, (size_t)nd);
+    s->lam = sys_alloc<double>(s, 6 * (size_t)nc);
+    s->lamf = sys_alloc<double>(s, (size_t)nf);
+    s->df = sys_alloc<double>(s, (size_t)nf);
+    cudaStream_t str = ctx->c.stream;
+    for (int i = 0; i < n_sys; ++i) {
+      const vag_mesh &m = meshes[i];
+      const int v0 = g.node_start[i], c0 = g.cell_start[i], f0 = g.ff_start[i], d0 = g.dir_start[i];
+      copy_in(s, s->xyz + 3 * (size_t)v0, m.xyz, 3 * (size_t)m.n_nodes, mem, "xyz");
+      copy_in(s, s->cell_nodes + 8 * (size_t)c0, m.cell_nodes, 8 * (size_t)m.n_cells, mem, "cell_nodes");
+      copy_in(s, s->ff_nodes + 4 * (size_t)f0, m.ff_nodes, 4 * (size_t)m.n_ff, mem, "ff_nodes");
+      copy_in(s, s->dir_nodes + d0, bcs[i].nodes, (size_t)bcs[i].n_dir, mem, "dirichlet nodes");
+      copy_in(s, s->dir_vals + d0, bcs[i].values, (size_t)bcs[i].n_dir, mem, "dirichlet values");
+      copy_in(s, s->lam + 6 * (size_t)c0, props[i].lambda_m, 6 * (size_t)m.n_cells, mem, "lambda_m");
+      copy_in(s, s->lamf + f0, props[i].lambda_f, (size_t)m.n_ff, mem, "lambda_f");
+      copy_in(s, s->df + f0, props[i].d_f, (size_t)m.n_ff, mem, "d_f");
+      if (v0) {   // node ids of system i become union ids
+        k_add_offset<<<grid_for(8 * (int64_t)m.n_cells, 256), 256, 0, str>>>(s->cell_nodes + 8 * (size_t)c0,
+                                                                            8 * (int64_t)m.n_cells, v0);
+        if (m.n_ff)
+          k_add_offset<<<grid_for(4 * (int64_t)m.n_ff, 256), 256, 0, str>>>(s->ff_nodes + 4 * (size_t)f0,
+                                                                           4 * (int64_t)m.n_ff, v0);
+        k_add_offset<<<grid_for(bcs[i].n_dir, 256), 256, 0, str>>>(s->dir_nodes + d0, bcs[i].n_dir, v0);
+        note_launches(m.n_ff ? 3 : 2);
+        VAG_CHECK_LAUNCH();
+      }
+    }
+    upload_segments(s);
+    symbolic_phase(s);
+    build_tiles(s);
+    build_sell(s);
+    numeric_phase(s);
+  });
+  if (st != VAG_OK) {
+    destroy_system(sys.release());
+    return st;
+  }
+  *out = sys.release();
+  return VAG_OK;
+}
+
+vag_status vag_system_get_batch(const vag_system *sys, int32_t *n_sys, int32_t *node_start, int32_t *ff_start,
+                                int32_t *cell_start, int32_t *row_start) {
+  if (!sys) return VAG_EINVAL;
+  const Segments &g = sys->s.seg;
+  if (n_sys) *n_sys = g.n_sys;
+  for (int i = 0; i <= g.n_sys; ++i) {
+    if (node_start) node_start[i] = g.node_start[i];
+    if (ff_start) ff_start[i] = g.ff_start[i];
+    if (cell_start) cell_start[i] = g.cell_start[i];
+    if (row_start) row_start[i] = g.row_start[i];
+  }
+  return VAG_OK;
+}
+
+vag_status vag_solve_get_infos(const vag_system *sys, vag_solve_info *infos) {
+  if (!sys || !infos) return VAG_EINVAL;
+  const System *s = &sys->s;
+  if (!s->solved) {
+    if (s->ctx) s->ctx->last_error = "no solve yet";
+    return VAG_EINVAL;
+  }
+  solve_infos(s, infos);
+  return VAG_OK;
+}
+
+vag_status vag_transport_get_dts(const vag_system *sys, double *dt_max, double *dt) {
+  if (!sys) return VAG_EINVAL;
+  const System *s = &sys->s;
+  if (s->dts_host.size() < 2 * (size_t)s->seg.n_sys) {
+    if (s->ctx) s->ctx->last_error = "no transport yet";
+    return VAG_EINVAL;
+  }
+  for (int g = 0; g < s->seg.n_sys; ++g) {
+    if (dt_max) dt_max[g] = s->dts_host[2 * g];
+    if (dt) dt[g] = s->dts_host[2 * g + 1];
+  }
   return VAG_OK;
 }
 
@@ -173,17 +354,7 @@ vag_status vag_update_props(vag_system *sys, const vag_props *props, int mem) {
   });
 }
 
-void vag_system_destroy(vag_system *sys) {
-  if (!sys) return;
-  System *s = &sys->s;
-  if (s->ctx && s->ctx->stream) cudaStreamSynchronize(s->ctx->stream);
-  if (s->pcg_graph) cudaGraphExecDestroy(s->pcg_graph);
-  if (s->ks_host) cudaFreeHost(s->ks_host);
-  if (s->ev0) cudaEventDestroy(s->ev0);
-  if (s->ev1) cudaEventDestroy(s->ev1);
-  sys_free_all(s);
-  delete sys;
-}
+void vag_system_destroy(vag_system *sys) { destroy_system(sys); }
 
 vag_status vag_system_get_info(const vag_system *sys, vag_system_info *info) {
   if (!sys || !info) return VAG_EINVAL;
@@ -210,10 +381,14 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     if (!opts) fail(VAG_EINVAL, "null options");
     check_mem(opts->mem);
     if (!(opts->rtol > 0.0) || opts->maxit <= 0) fail(VAG_EINVAL, "rtol must be > 0 and maxit > 0");
-    if (opts->precision != VAG_FP64) fail(VAG_EINVAL, "precision not available in this build");
-    if (opts->precond != VAG_PC_JACOBI) fail(VAG_EINVAL, "preconditioner not available in this build");
+    if (opts->precision != VAG_FP64 && opts->precision != VAG_MIXED) fail(VAG_EINVAL, "unknown precision");
+    if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_AMG)
+      fail(VAG_EINVAL, "preconditioner not available in this build");
+    if (opts->precision == VAG_MIXED && opts->precond != VAG_PC_JACOBI)
+      fail(VAG_EINVAL, "the mixed-precision path takes the Jacobi preconditioner in this build");
     use_device(s->ctx);
-    pcg_solve(s, opts, inf);
+    if (opts->precision == VAG_MIXED) mixed_solve(s, opts, inf);
+    else pcg_solve(s, opts, inf);
     copy_out(s, u_out, s->u, (size_t)s->n_cv, opts->mem);
     VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
     if (inf->status == VAG_EBREAKDOWN) fail(VAG_EBREAKDOWN, "CG breakdown: p^T A p <= 0 or NaN");
@@ -232,7 +407,8 @@ vag_status vag_spmv(vag_system *sys, const double *x, double *y, int mem) {
     use_device(s->ctx);
     cudaStream_t st = s->ctx->stream;
     if (mem == VAG_MEM_DEVICE) {
-      spmv_f64(s, x, y);
+      spmv_f64(s, x, y);   // stream-ordered: no host synchronisation
+      return;
     } else {
       double *dx, *dy;
       const size_t n = s->n_rows;

@@ -1,7 +1,17 @@
 // Shared device utilities: budget-checked allocation, exclusive scan, status.
+#include <atomic>
+
 #include "vag_internal.cuh"
 
 namespace vag {
+
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local bool t_capturing = false;
+void set_capturing(bool on) { t_capturing = on; }
+void note_launches(unsigned long long n) {
+  if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void *sys_alloc_bytes(System *s, size_t bytes) {
   Ctx *c = s->ctx;
@@ -130,10 +140,12 @@ void scan_rec(const int *in, int *out, int n, cudaStream_t st) {
   int *sums_scan = sums + ntiles;
   scan_tiles<<<ntiles, kScanThreads, 0, st>>>(in, out, sums, n);
   VAG_CHECK_LAUNCH();
+  note_launches(2);   // scan_tiles + write_total
   if (ntiles > 1) {
     scan_rec(sums, sums_scan, ntiles, st);
     add_tile_offsets<<<ntiles, kScanThreads, 0, st>>>(out, sums_scan, n);
     VAG_CHECK_LAUNCH();
+    note_launches(1);
   } else {
     VAG_CUDA(cudaMemsetAsync(sums_scan, 0, sizeof(int), st));
   }

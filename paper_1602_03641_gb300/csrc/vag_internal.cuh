@@ -11,6 +11,8 @@
 
 #include "vag.h"
 
+struct vag_ctx;
+
 namespace vag {
 
 // --------------------------------------------------------------- errors ----
@@ -53,6 +55,9 @@ struct Ctx {
   int device = 0;
   size_t budget = 0;
   size_t in_use = 0;
+  int live_systems = 0;        // systems created from this context and not yet destroyed
+  bool destroy_requested = false;
+  struct ::vag_ctx *owner = nullptr;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   std::string last_error;
@@ -64,14 +69,68 @@ struct Alloc {
   size_t bytes;
 };
 
-// Krylov scalars kept on the device.
+// Krylov scalars kept on the device, one set per system of a batch.
 struct KrylovScalars {
   double rz, pq, alpha, beta, rr, bb, tol2, res2;
   int iter, maxit, done, breakdown;
+  int inner_total;             // mixed precision: inner iterations summed over refinements
+  int stalled;                 // true residual stopped falling (rounding floor)
+};
+
+// One level of the aggregation AMG hierarchy (level 0 aliases the system).
+struct AmgLevel {
+  int n = 0;
+  int64_t nnz = 0;
+  int *rowptr = nullptr, *col = nullptr;
+  double *val = nullptr, *dinv = nullptr;
+  std::vector<int> sys_start;      // host, n_sys+1: first row of each system
+  int *d_sys_start = nullptr;
+  int *agg = nullptr;              // [n] aggregate (row of the next level) or -1
+  int nc = 0;
+  int *mptr = nullptr, *mem = nullptr;   // members of each aggregate, sorted
+  double *x = nullptr, *b = nullptr, *t = nullptr;   // V-cycle work vectors
+};
+struct Amg {
+  std::vector<AmgLevel> levels;
+  std::vector<void *> allocs;
+  size_t bytes = 0;
+  double *inv = nullptr;           // dense inverses of the coarsest blocks
+  long long *inv_off = nullptr;
+  bool built = false;
+};
+
+// State of the mixed-precision solve (FP32 inner CG inside FP64 refinement).
+struct Mixed {
+  float *sval32 = nullptr;     // FP32 sliced-ELL values of S A S, S = D^{-1/2}
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  double *sc = nullptr;        // S
+  KrylovScalars *ks_in = nullptr;
+  int *n_done_in = nullptr;
+  bool stale = true;           // values older than the last numeric phase
+  cudaGraphExec_t graph = nullptr;
+};
+
+// A batch of independent systems is assembled as the disjoint union of their
+// meshes; each system's Krylov rows are contiguous.  Reductions run per row
+// tile (one thread block each); the last tile of a system to finish sums the
+// system's tile partials in tile order, so a system's arithmetic does not
+// depend on the other systems of the batch.
+struct Segments {
+  int n_sys = 1;
+  std::vector<int> node_start, ff_start, cell_start, dir_start, row_start;   // host, n_sys+1
+  int *d_node_start = nullptr, *d_ff_start = nullptr, *d_cell_start = nullptr, *d_row_start = nullptr;
+  int n_tiles = 0;
+  std::vector<int> tile_start_h;     // first tile of each system, n_sys+1
+  int *tile_sys = nullptr;           // [n_tiles]
+  int *tile_row0 = nullptr;          // [n_tiles+1] (row range of tile t: [row0[t], row1[t]))
+  int *tile_row1 = nullptr;
+  int *sys_tile0 = nullptr;          // [n_sys+1] first tile of each system
+  int *cv_sys = nullptr;             // [n_cv] system of each control volume
 };
 
 struct System {
   Ctx *ctx = nullptr;
+  bool counted = false;        // counted in ctx->live_systems
   std::vector<Alloc> allocs;
   size_t bytes = 0;
 
@@ -116,19 +175,34 @@ struct System {
   double *cvol = nullptr;      // [nc]
   double *ffarea = nullptr;    // [nf]
   double *val = nullptr;       // [nnz]
+  // sliced-ELL copy (32-row slices, column-major inside a slice)
+  int n_slices = 0;
+  int64_t sell_nnz = 0;
+  int *slice_ptr = nullptr;    // [n_slices+1] element offsets
+  int *scol = nullptr;         // [sell_nnz]
+  double *sval = nullptr;      // [sell_nnz]
   double *rhs = nullptr;       // [n_rows]
   double *dinv = nullptr;      // [n_rows]
 
   // solve (device)
   double *u = nullptr;         // [n_cv] full solution (nodes | ffaces | cells)
   double *kx = nullptr, *kr = nullptr, *kp = nullptr, *kq = nullptr;   // [n_rows]
-  double *partials = nullptr;  // [2 * kMaxRedBlocks]
-  unsigned int *counter = nullptr;
-  KrylovScalars *ks = nullptr;
-  KrylovScalars *ks_host = nullptr;   // pinned mirror for polling
+  double *partials = nullptr;  // [2 * n_tiles] (Krylov) / [kMaxRedBlocks] (transport)
+  unsigned int *counter = nullptr;     // [n_sys + 1] arrival counters
+  KrylovScalars *ks = nullptr;         // [n_sys]
+  KrylovScalars *ks_host = nullptr;    // pinned mirror [n_sys]
+  int *n_done = nullptr;               // systems converged (device)
+  int *n_done_host = nullptr;          // pinned mirror
+  Segments seg;
   cudaGraphExec_t pcg_graph = nullptr;
   int pcg_graph_chunk = 0;
   bool solved = false;
+  bool last_mixed = false;
+  Mixed mx;
+  Amg amg;
+  double *kz = nullptr;                // preconditioned residual (AMG)
+  cudaGraphExec_t pcg_graph_amg = nullptr;
+  size_t amg_graph_nodes = 0;
 
   // transport (device)
   double *Fcn = nullptr;       // [8 nc]
@@ -142,7 +216,8 @@ struct System {
   double *tval = nullptr;      // [nnz_t]
   int64_t t_cap = 0;
   double *cbuf = nullptr;      // [2 n_cv]
-  double *dts = nullptr;       // [4] dt_max, dt, ...
+  double *dts = nullptr;       // [2 n_sys]: per system dt_max, dt
+  std::vector<double> dts_host;
 
   // timing events
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -163,12 +238,32 @@ int scan_exclusive(const int *in, int *out, int n, cudaStream_t st, bool want_to
 int read_status(System *s);
 int grid_for(int64_t n, int block);
 int num_sms();
+// process-wide count of kernels this library has launched (graph launches
+// count their kernel nodes)
+void note_launches(unsigned long long n);
+// while a stream capture is being recorded, launches are not counted (the
+// graph launch counts its nodes instead)
+void set_capturing(bool on);
+unsigned long long launches_so_far();
 
 // ------------------------------------------------------------- phases -----
 void symbolic_phase(System *s);
 void numeric_phase(System *s);
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
+void amg_setup(System *s);
+void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
+void amg_free(System *s);
+void mixed_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
+void ensure_krylov_buffers(System *s);
+// Krylov result in s->kx and per-system scalars in s->ks: scatter into u,
+// recover the cells, compute the fluxes, fill the aggregate info.
+void finish_solve(System *s, vag_solve_info *info, bool mixed);
 void spmv_f64(System *s, const double *x, double *y);
+void build_tiles(System *s);
+void build_sell(System *s);
+void sell_values(System *s);
+void sell_values_scaled_f32(System *s, const double *scale, float *out);
+void solve_infos(const System *s, vag_solve_info *infos);
 void recover_cells_and_fluxes(System *s);
 void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_transport_info *info,
                    const double *phi_m, const double *phi_f, const double *cbar);

@@ -2,72 +2,76 @@
 //
 // The system is the Galerkin form restricted to the non-Dirichlet unknowns,
 // hence symmetric positive definite: conjugate gradients with a Jacobi
-// preconditioner.  Per iteration three kernels:
-//   k_spmv<G>   q = A p (G lanes per CSR row) fused with the partial p.q,
-//               the last block computes alpha = r.z / p.q;
-//   k_update    x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r,
-//               the last block computes beta and the convergence flag;
+// preconditioner.  A solve handles a batch of independent systems at once
+// (a single system is a batch of one): every kernel runs one thread block per
+// row tile of some system, and each system keeps its own CG scalars.  Per
+// iteration three kernels:
+//   k_spmv      q = A p (sliced ELL, one thread per row) fused with the partial p.q; the
+//               last tile of a system to finish computes its alpha;
+//   k_update    x += alpha p, r -= alpha q, partial r.z and r.r (z = D^-1 r);
+//               the last tile computes beta and the convergence flag;
 //   k_pdir      p = z + beta p.
-// Reductions are deterministic (fixed grid, fixed summation order).  The
-// iteration is captured in a CUDA graph of `chunk` iterations; once the
-// device flag `done` is set every kernel returns at entry, so the host polls
-// the flag only between graph launches.
+// A converged system's tiles return at entry.  Reductions are deterministic
+// and depend only on the system itself (tile sizes come from its own row
+// count), so a system gives bitwise the same iterates alone or in a batch.
+// Iterations are captured in a CUDA graph of `chunk` iterations; the host
+// polls one counter (systems done) between graph launches.
 #include "vag_internal.cuh"
 #include "vag_reduce.cuh"
-#include "vag_hex.cuh"
 
 namespace vag {
 namespace {
 
 constexpr int NT = 256;
 
-template <int G>
-__global__ void __launch_bounds__(NT) k_spmv(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                                             const double *__restrict__ val, const double *__restrict__ x,
-                                             double *__restrict__ y, double *partials, unsigned *counter,
-                                             KrylovScalars *ks, int with_dot) {
-  if (with_dot && ks->done) return;
-  const int lane = threadIdx.x & (G - 1);
-  const int warp_global = (blockIdx.x * NT + threadIdx.x) >> 5;
-  const int warps_total = (gridDim.x * NT) >> 5;
-  constexpr int RPW = 32 / G;   // rows per warp per sweep
-  const int sub = (threadIdx.x & 31) / G;
+// q = A p in the sliced-ELL layout, one thread per row: exactly one FMA per
+// stored entry, in the row's CSR order.
+__global__ void __launch_bounds__(NT) k_spmv(const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
+                                             const int *__restrict__ scol, const double *__restrict__ sval,
+                                             const double *__restrict__ x, double *__restrict__ y, Tiles tl,
+                                             double *partials, unsigned *counter, KrylovScalars *ks, int *n_done,
+                                             int with_dot) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (with_dot && ks[sys].done) return;
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
   double dp = 0.0;
-  for (int base = warp_global * RPW; base < n; base += warps_total * RPW) {
-    const int row = base + sub;
+  for (int row = r0 + threadIdx.x; row < r1; row += NT) {
+    const int len = rowptr[row + 1] - rowptr[row];
+    const int base = slice_ptr[row >> 5] + (row & 31);
     double s = 0.0;
-    if (row < n) {
-      const int b = rowptr[row], e = rowptr[row + 1];
-      for (int k = b + lane; k < e; k += G) s = fma(val[k], __ldg(&x[col[k]]), s);
+#pragma unroll 4
+    for (int k = 0; k < len; ++k) {
+      const int idx = base + 32 * k;
+      s = fma(sval[idx], __ldg(&x[scol[idx]]), s);
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (row < n && lane == 0) {
-      y[row] = s;
-      dp = fma(x[row], s, dp);
-    }
+    y[row] = s;
+    dp = fma(x[row], s, dp);
   }
   if (!with_dot) return;
   double v[1] = {dp}, out[1];
-  if (grid_sum<NT, 1>(v, partials, counter, out) && threadIdx.x == 0) {
-    const double pq = out[0];
-    ks->pq = pq;
-    if (!(pq > 0.0)) {
-      ks->breakdown = 1;
-      ks->done = 1;
-      ks->alpha = 0.0;
+  if (seg_sum<NT, 1>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.pq = out[0];
+    if (!(out[0] > 0.0)) {
+      k.breakdown = 1;
+      k.alpha = 0.0;
+      if (!k.done) { k.done = 1; atomicAdd(n_done, 1); }
     } else {
-      ks->alpha = ks->rz / pq;
+      k.alpha = k.rz / out[0];
     }
   }
 }
 
-__global__ void __launch_bounds__(NT) k_init(int n, const double *__restrict__ b, const double *__restrict__ dinv,
+__global__ void __launch_bounds__(NT) k_init(const double *__restrict__ b, const double *__restrict__ dinv,
                                              double *__restrict__ x, double *__restrict__ r, double *__restrict__ p,
-                                             double *partials, unsigned *counter, KrylovScalars *ks, double rtol,
-                                             int maxit) {
+                                             Tiles tl, double *partials, unsigned *counter, KrylovScalars *ks,
+                                             int *n_done, double rtol, int maxit) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
   double rz = 0.0, rr = 0.0;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) {
     const double bi = b[i];
     const double zi = dinv[i] * bi;
     x[i] = 0.0;
@@ -77,27 +81,34 @@ __global__ void __launch_bounds__(NT) k_init(int n, const double *__restrict__ b
     rr = fma(bi, bi, rr);
   }
   double v[2] = {rz, rr}, out[2];
-  if (grid_sum<NT, 2>(v, partials, counter, out) && threadIdx.x == 0) {
-    ks->rz = out[0];
-    ks->rr = out[1];
-    ks->bb = out[1];
-    ks->tol2 = rtol * rtol * out[1];
-    ks->iter = 0;
-    ks->maxit = maxit;
-    ks->breakdown = 0;
-    ks->done = (out[1] <= ks->tol2) ? 1 : 0;
-    ks->beta = 0.0;
+  if (seg_sum<NT, 2>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.rz = out[0];
+    k.rr = out[1];
+    k.bb = out[1];
+    k.tol2 = rtol * rtol * out[1];
+    k.iter = 0;
+    k.maxit = maxit;
+    k.breakdown = 0;
+    k.stalled = 0;
+    k.inner_total = 0;
+    k.beta = 0.0;
+    k.done = (out[1] <= k.tol2) ? 1 : 0;
+    if (k.done) atomicAdd(n_done, 1);
   }
 }
 
-__global__ void __launch_bounds__(NT) k_update(int n, double *__restrict__ x, double *__restrict__ r,
+__global__ void __launch_bounds__(NT) k_update(double *__restrict__ x, double *__restrict__ r,
                                                const double *__restrict__ p, const double *__restrict__ q,
-                                               const double *__restrict__ dinv, double *partials,
-                                               unsigned *counter, KrylovScalars *ks) {
-  if (ks->done) return;
-  const double alpha = ks->alpha;
+                                               const double *__restrict__ dinv, Tiles tl, double *partials,
+                                               unsigned *counter, KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  const double alpha = ks[sys].alpha;
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
   double rz = 0.0, rr = 0.0;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
@@ -105,33 +116,203 @@ __global__ void __launch_bounds__(NT) k_update(int n, double *__restrict__ x, do
     rr = fma(ri, ri, rr);
   }
   double v[2] = {rz, rr}, out[2];
-  if (grid_sum<NT, 2>(v, partials, counter, out) && threadIdx.x == 0) {
-    const double rzn = out[0];
-    ks->beta = rzn / ks->rz;
-    ks->rz = rzn;
-    ks->rr = out[1];
-    ks->iter += 1;
-    if (out[1] <= ks->tol2 || ks->iter >= ks->maxit) ks->done = 1;
-    if (!(out[1] == out[1])) { ks->breakdown = 1; ks->done = 1; }
+  if (seg_sum<NT, 2>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.beta = out[0] / k.rz;
+    k.rz = out[0];
+    k.rr = out[1];
+    k.iter += 1;
+    bool fin = out[1] <= k.tol2 || k.iter >= k.maxit;
+    if (!(out[1] == out[1])) { k.breakdown = 1; fin = true; }
+    if (fin) { k.done = 1; atomicAdd(n_done, 1); }
   }
 }
 
-__global__ void __launch_bounds__(NT) k_pdir(int n, double *__restrict__ p, const double *__restrict__ r,
-                                             const double *__restrict__ dinv, const KrylovScalars *ks) {
-  if (ks->done) return;
-  const double beta = ks->beta;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) p[i] = fma(beta, p[i], dinv[i] * r[i]);
+__global__ void __launch_bounds__(NT) k_pdir(double *__restrict__ p, const double *__restrict__ r,
+                                             const double *__restrict__ dinv, Tiles tl, const KrylovScalars *ks) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  const double beta = ks[sys].beta;
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) p[i] = fma(beta, p[i], dinv[i] * r[i]);
 }
 
-__global__ void __launch_bounds__(NT) k_resid2(int n, const double *__restrict__ b, const double *__restrict__ Ax,
+// Restart from the current iterate with the true residual: r = b - A x,
+// p = z = D^-1 r.  A system whose true residual already meets the tolerance
+// stays done.
+__global__ void __launch_bounds__(NT) k_restart(const double *__restrict__ b, const double *__restrict__ Ax,
+                                                const double *__restrict__ dinv, double *__restrict__ r,
+                                                double *__restrict__ p, Tiles tl, double *partials, unsigned *counter,
+                                                KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  double rz = 0.0, rr = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) {
+    const double ri = b[i] - Ax[i];
+    const double zi = dinv[i] * ri;
+    r[i] = ri;
+    p[i] = zi;
+    rz = fma(ri, zi, rz);
+    rr = fma(ri, ri, rr);
+  }
+  double v[2] = {rz, rr}, out[2];
+  if (seg_sum<NT, 2>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.rz = out[0];
+    k.rr = out[1];
+    k.beta = 0.0;
+    k.done = (out[1] <= k.tol2 || k.iter >= k.maxit || k.breakdown || k.stalled) ? 1 : 0;
+    if (k.done) atomicAdd(n_done, 1);
+  }
+}
+
+// --- preconditioned by a general operator z = M r (AMG) -------------------
+
+// x = 0, r = b, partial b.b (scalars set by k_rz_start)
+__global__ void __launch_bounds__(NT) k_init_m(const double *__restrict__ b, double *__restrict__ x,
+                                               double *__restrict__ r, Tiles tl, double *partials,
+                                               unsigned *counter, KrylovScalars *ks, double rtol, int maxit) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  double bb = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) {
+    const double bi = b[i];
+    x[i] = 0.0;
+    r[i] = bi;
+    bb = fma(bi, bi, bb);
+  }
+  double v[1] = {bb}, out[1];
+  if (seg_sum<NT, 1>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.bb = out[0];
+    k.rr = out[0];
+    k.tol2 = rtol * rtol * out[0];
+    k.iter = 0;
+    k.maxit = maxit;
+    k.breakdown = 0;
+    k.stalled = 0;
+    k.inner_total = 0;
+    k.beta = 0.0;
+    k.done = 0;
+  }
+}
+
+// p = z, rz = r.z; done if r.r already meets the tolerance (or the system is
+// done for another reason)
+__global__ void __launch_bounds__(NT) k_rz_start(const double *__restrict__ r, const double *__restrict__ z,
+                                                 double *__restrict__ p, Tiles tl, double *partials,
+                                                 unsigned *counter, KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  double rz = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) {
+    const double zi = z[i];
+    p[i] = zi;
+    rz = fma(r[i], zi, rz);
+  }
+  double v[1] = {rz}, out[1];
+  if (seg_sum<NT, 1>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.rz = out[0];
+    k.beta = 0.0;
+    const bool fin = k.rr <= k.tol2 || k.iter >= k.maxit || k.breakdown || k.stalled;
+    k.done = fin ? 1 : 0;
+    if (fin) atomicAdd(n_done, 1);
+    else if (!(out[0] > 0.0)) { k.breakdown = 1; k.done = 1; atomicAdd(n_done, 1); }
+  }
+}
+
+// x += alpha p, r -= alpha q, partial r.r; the last tile counts the iteration
+// and tests convergence
+__global__ void __launch_bounds__(NT) k_update_m(double *__restrict__ x, double *__restrict__ r,
+                                                 const double *__restrict__ p, const double *__restrict__ q, Tiles tl,
+                                                 double *partials, unsigned *counter, KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  const double alpha = ks[sys].alpha;
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  double rr = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+  }
+  double v[1] = {rr}, out[1];
+  if (seg_sum<NT, 1>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.rr = out[0];
+    k.iter += 1;
+    bool fin = out[0] <= k.tol2 || k.iter >= k.maxit;
+    if (!(out[0] == out[0])) { k.breakdown = 1; fin = true; }
+    if (fin) { k.done = 1; atomicAdd(n_done, 1); }
+  }
+}
+
+// beta = (r.z)_new / (r.z)_old and p = z + beta p in one pass: each tile
+// first needs the system's new r.z, so this kernel only reduces; k_pdir_z
+// applies it
+__global__ void __launch_bounds__(NT) k_rz(const double *__restrict__ r, const double *__restrict__ z, Tiles tl,
+                                           double *partials, unsigned *counter, KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  double rz = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) rz = fma(r[i], z[i], rz);
+  double v[1] = {rz}, out[1];
+  if (seg_sum<NT, 1>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.beta = out[0] / k.rz;
+    k.rz = out[0];
+    if (!(out[0] > 0.0)) { k.breakdown = 1; k.done = 1; atomicAdd(n_done, 1); }
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_pdir_z(double *__restrict__ p, const double *__restrict__ z, Tiles tl,
+                                               const KrylovScalars *ks) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  const double beta = ks[sys].beta;
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) p[i] = fma(beta, p[i], z[i]);
+}
+
+// restart for the general preconditioner: r = b - A x and r.r
+__global__ void __launch_bounds__(NT) k_restart_m(const double *__restrict__ b, const double *__restrict__ Ax,
+                                                  double *__restrict__ r, Tiles tl, double *partials,
+                                                  unsigned *counter, KrylovScalars *ks) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  double rr = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) {
+    const double ri = b[i] - Ax[i];
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+  }
+  double v[1] = {rr}, out[1];
+  if (seg_sum<NT, 1>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) ks[sys].rr = out[0];
+}
+
+__global__ void __launch_bounds__(NT) k_resid2(const double *__restrict__ b, const double *__restrict__ Ax, Tiles tl,
                                                double *partials, unsigned *counter, KrylovScalars *ks) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
   double s = 0.0;
-  for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+  for (int i = r0 + threadIdx.x; i < r1; i += NT) {
     const double d = b[i] - Ax[i];
     s = fma(d, d, s);
   }
   double v[1] = {s}, out[1];
-  if (grid_sum<NT, 1>(v, partials, counter, out) && threadIdx.x == 0) ks->res2 = out[0];
+  if (seg_sum<NT, 1>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) ks[sys].res2 = out[0];
 }
 
 // u over [nodes | ffaces | cells]: Krylov rows, then Dirichlet values.
@@ -145,52 +326,73 @@ __global__ void k_scatter_dir(int nd, const int *__restrict__ dn, const double *
   if (i < nd) u[dn[i]] = dv[i];
 }
 
-}  // namespace
-
-int spmv_group(const System *s) {
-  const double avg = s->n_rows ? (double)s->nnz / s->n_rows : 1.0;
-  return avg <= 10.0 ? 4 : (avg <= 40.0 ? 8 : 16);
+Tiles tiles_of(const System *s) {
+  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0};
 }
 
-int red_grid(int64_t n) {
-  const int64_t want = (n + NT - 1) / NT;
-  int64_t g = std::min<int64_t>((int64_t)num_sms() * 4, want);
-  if (g < 1) g = 1;
-  if (g > kMaxRedBlocks) g = kMaxRedBlocks;
-  return (int)g;
+}  // namespace
+
+// Rows per tile of a system with n rows: about n / 1216 (enough tiles to fill
+// every SM several times), a power of two between 256 (one row per thread)
+// and 2048.  It depends on the system alone.
+static int tile_rows(int n) {
+  int t = 256;
+  while (t < 2048 && t * 2 <= n / 1216) t *= 2;
+  return t;
+}
+
+void build_tiles(System *s) {
+  Segments &g = s->seg;
+  std::vector<int> tsys, t0, t1, st(g.n_sys + 1);
+  for (int i = 0; i < g.n_sys; ++i) {
+    st[i] = (int)tsys.size();
+    const int a = g.row_start[i], b = g.row_start[i + 1];
+    const int T = tile_rows(b - a);
+    int r = a;
+    do {   // at least one (possibly empty) tile per system
+      tsys.push_back(i);
+      t0.push_back(r);
+      t1.push_back(std::min(r + T, b));
+      r += T;
+    } while (r < b);
+  }
+  st[g.n_sys] = (int)tsys.size();
+  g.n_tiles = (int)tsys.size();
+  g.tile_start_h = st;
+  g.tile_sys = sys_alloc<int>(s, g.n_tiles);
+  g.tile_row0 = sys_alloc<int>(s, g.n_tiles);
+  g.tile_row1 = sys_alloc<int>(s, g.n_tiles);
+  g.sys_tile0 = sys_alloc<int>(s, g.n_sys + 1);
+  cudaStream_t str = s->ctx->stream;
+  VAG_CUDA(cudaMemcpyAsync(g.tile_sys, tsys.data(), sizeof(int) * g.n_tiles, cudaMemcpyHostToDevice, str));
+  VAG_CUDA(cudaMemcpyAsync(g.tile_row0, t0.data(), sizeof(int) * g.n_tiles, cudaMemcpyHostToDevice, str));
+  VAG_CUDA(cudaMemcpyAsync(g.tile_row1, t1.data(), sizeof(int) * g.n_tiles, cudaMemcpyHostToDevice, str));
+  VAG_CUDA(cudaMemcpyAsync(g.sys_tile0, st.data(), sizeof(int) * (g.n_sys + 1), cudaMemcpyHostToDevice, str));
+  VAG_CUDA(cudaStreamSynchronize(str));   // host vectors go out of scope
 }
 
 static void launch_spmv(System *s, const double *x, double *y, int with_dot, cudaStream_t st) {
-  const int G = spmv_group(s);
-  const int rows_per_block = NT / G;
-  int64_t want = (s->n_rows + rows_per_block - 1) / rows_per_block;
-  int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)num_sms() * 8);
-  if (grid > kMaxRedBlocks) grid = kMaxRedBlocks;
-  switch (G) {
-    case 4:
-      k_spmv<4><<<grid, NT, 0, st>>>(s->n_rows, s->rowptr, s->col, s->val, x, y, s->partials, s->counter, s->ks, with_dot);
-      break;
-    case 8:
-      k_spmv<8><<<grid, NT, 0, st>>>(s->n_rows, s->rowptr, s->col, s->val, x, y, s->partials, s->counter, s->ks, with_dot);
-      break;
-    default:
-      k_spmv<16><<<grid, NT, 0, st>>>(s->n_rows, s->rowptr, s->col, s->val, x, y, s->partials, s->counter, s->ks, with_dot);
-  }
+  k_spmv<<<s->seg.n_tiles, NT, 0, st>>>(s->rowptr, s->slice_ptr, s->scol, s->sval, x, y, tiles_of(s), s->partials,
+                                        s->counter, s->ks, s->n_done, with_dot);
+  note_launches(1);
 }
 
-static void ensure_krylov_buffers(System *s) {
+void ensure_krylov_buffers(System *s) {
   if (s->kx) return;
+  const int ns = s->seg.n_sys;
   s->kx = sys_alloc<double>(s, s->n_rows);
   s->kr = sys_alloc<double>(s, s->n_rows);
   s->kp = sys_alloc<double>(s, s->n_rows);
   s->kq = sys_alloc<double>(s, s->n_rows);
-  s->partials = sys_alloc<double>(s, 4 * (size_t)kMaxRedBlocks);
-  s->counter = sys_alloc<unsigned>(s, 4);
-  s->ks = sys_alloc<KrylovScalars>(s, 1);
+  s->partials = sys_alloc<double>(s, std::max<size_t>(2 * (size_t)s->seg.n_tiles, (size_t)kMaxRedBlocks));
+  s->counter = sys_alloc<unsigned>(s, ns + 1);
+  s->ks = sys_alloc<KrylovScalars>(s, ns);
+  s->n_done = sys_alloc<int>(s, 1);
   s->u = sys_alloc<double>(s, (size_t)s->n_cv);
-  VAG_CUDA(cudaMemsetAsync(s->counter, 0, 4 * sizeof(unsigned), s->ctx->stream));
+  VAG_CUDA(cudaMemsetAsync(s->counter, 0, (ns + 1) * sizeof(unsigned), s->ctx->stream));
   VAG_CUDA(cudaMemsetAsync(s->u, 0, sizeof(double) * s->n_cv, s->ctx->stream));
-  if (!s->ks_host) VAG_CUDA(cudaMallocHost(&s->ks_host, sizeof(KrylovScalars)));
+  if (!s->ks_host) VAG_CUDA(cudaMallocHost(&s->ks_host, sizeof(KrylovScalars) * ns));
+  if (!s->n_done_host) VAG_CUDA(cudaMallocHost(&s->n_done_host, sizeof(int)));
 }
 
 void spmv_f64(System *s, const double *x, double *y) {
@@ -199,63 +401,170 @@ void spmv_f64(System *s, const double *x, double *y) {
   VAG_CHECK_LAUNCH();
 }
 
-static void pcg_iteration(System *s, cudaStream_t st) {
-  const int g = red_grid(s->n_rows);
+static void pcg_iteration_amg(System *s, cudaStream_t st) {
+  const Tiles tl = tiles_of(s);
+  const int nt = s->seg.n_tiles;
   launch_spmv(s, s->kp, s->kq, 1, st);
-  k_update<<<g, NT, 0, st>>>(s->n_rows, s->kx, s->kr, s->kp, s->kq, s->dinv, s->partials, s->counter, s->ks);
-  k_pdir<<<g, NT, 0, st>>>(s->n_rows, s->kp, s->kr, s->dinv, s->ks);
+  k_update_m<<<nt, NT, 0, st>>>(s->kx, s->kr, s->kp, s->kq, tl, s->partials, s->counter, s->ks, s->n_done);
+  amg_apply(s, s->kr, s->kz, st);
+  k_rz<<<nt, NT, 0, st>>>(s->kr, s->kz, tl, s->partials, s->counter, s->ks, s->n_done);
+  k_pdir_z<<<nt, NT, 0, st>>>(s->kp, s->kz, tl, s->ks);
+  note_launches(3);
+}
+
+static void pcg_iteration(System *s, cudaStream_t st) {
+  const Tiles tl = tiles_of(s);
+  launch_spmv(s, s->kp, s->kq, 1, st);
+  k_update<<<s->seg.n_tiles, NT, 0, st>>>(s->kx, s->kr, s->kp, s->kq, s->dinv, tl, s->partials, s->counter, s->ks,
+                                          s->n_done);
+  note_launches(1);
+  k_pdir<<<s->seg.n_tiles, NT, 0, st>>>(s->kp, s->kr, s->dinv, tl, s->ks);
+  note_launches(1);
 }
 
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   cudaStream_t st = s->ctx->stream;
   ensure_krylov_buffers(s);
-  const int n = s->n_rows;
-  const int g = red_grid(n);
+  const bool amg = o->precond == VAG_PC_AMG;
+  const int ns = s->seg.n_sys;
+  const int nt = s->seg.n_tiles;
+  const Tiles tl = tiles_of(s);
+  float setup_ms = 0.f;
   VAG_CUDA(cudaEventRecord(s->ev0, st));
-  k_init<<<g, NT, 0, st>>>(n, s->rhs, s->dinv, s->kx, s->kr, s->kp, s->partials, s->counter, s->ks, o->rtol,
-                           o->maxit);
+  if (amg) {
+    if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
+    amg_setup(s);
+    VAG_CUDA(cudaEventRecord(s->ev1, st));
+    VAG_CUDA(cudaEventSynchronize(s->ev1));
+    cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);
+  }
+  VAG_CUDA(cudaMemsetAsync(s->n_done, 0, sizeof(int), st));
+  if (amg) {
+    k_init_m<<<nt, NT, 0, st>>>(s->rhs, s->kx, s->kr, tl, s->partials, s->counter, s->ks, o->rtol, o->maxit);
+    amg_apply(s, s->kr, s->kz, st);
+    k_rz_start<<<nt, NT, 0, st>>>(s->kr, s->kz, s->kp, tl, s->partials, s->counter, s->ks, s->n_done);
+    note_launches(2);
+  } else {
+    k_init<<<nt, NT, 0, st>>>(s->rhs, s->dinv, s->kx, s->kr, s->kp, tl, s->partials, s->counter, s->ks,
+                              s->n_done, o->rtol, o->maxit);
+    note_launches(1);
+  }
   VAG_CHECK_LAUNCH();
-  // graph of `chunk` iterations, captured once per system
   const int chunk = 16;
-  if (!s->pcg_graph || s->pcg_graph_chunk != chunk) {
-    if (s->pcg_graph) cudaGraphExecDestroy(s->pcg_graph);
+  cudaGraphExec_t &gexec = amg ? s->pcg_graph_amg : s->pcg_graph;
+  if (amg && gexec) {   // the hierarchy (and its pointers) is rebuilt every solve
+    cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
+  if (!gexec) {
     cudaGraph_t graph;
     VAG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < chunk; ++i) pcg_iteration(s, st);
+    set_capturing(true);
+    for (int i = 0; i < chunk; ++i) {
+      if (amg) pcg_iteration_amg(s, st);
+      else pcg_iteration(s, st);
+    }
+    set_capturing(false);
     VAG_CUDA(cudaStreamEndCapture(st, &graph));
-    VAG_CUDA(cudaGraphInstantiate(&s->pcg_graph, graph, 0));
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    VAG_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
     cudaGraphDestroy(graph);
-    s->pcg_graph_chunk = chunk;
+    if (amg) s->amg_graph_nodes = nodes;
   }
+  const unsigned long long per_launch = amg ? s->amg_graph_nodes : 3ull * chunk;
   const int max_chunks = (o->maxit + chunk - 1) / chunk;
-  for (int c = 0; c < max_chunks + 1; ++c) {
-    VAG_CUDA(cudaGraphLaunch(s->pcg_graph, st));
-    VAG_CUDA(cudaMemcpyAsync(s->ks_host, s->ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st));
+  // The recursive residual can drift below the true one; after convergence
+  // the true residual is recomputed and CG restarts from the current iterate
+  // (a few times at most) for every system still above its tolerance whose
+  // true residual still falls.
+  std::vector<double> prev_res2;
+  for (int attempt = 0;; ++attempt) {
+    for (int c = 0; c < max_chunks + 1; ++c) {
+      VAG_CUDA(cudaMemcpyAsync(s->n_done_host, s->n_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      VAG_CUDA(cudaStreamSynchronize(st));
+      if (*s->n_done_host >= ns) break;
+      VAG_CUDA(cudaGraphLaunch(gexec, st));
+      note_launches(per_launch);
+    }
+    launch_spmv(s, s->kx, s->kq, 0, st);
+    k_resid2<<<nt, NT, 0, st>>>(s->rhs, s->kq, tl, s->partials, s->counter, s->ks);
+    note_launches(1);
+    VAG_CHECK_LAUNCH();
+    if (attempt == 3) break;
+    VAG_CUDA(cudaMemcpyAsync(s->ks_host, s->ks, sizeof(KrylovScalars) * ns, cudaMemcpyDeviceToHost, st));
     VAG_CUDA(cudaStreamSynchronize(st));
-    if (s->ks_host->done) break;
+    bool again = false;
+    prev_res2.resize(ns, INFINITY);
+    for (int i = 0; i < ns; ++i) {
+      const KrylovScalars &k = s->ks_host[i];
+      const bool improving = k.res2 < 0.25 * prev_res2[i];
+      again |= (k.res2 > k.tol2 && k.iter < k.maxit && !k.breakdown && improving);
+      prev_res2[i] = k.res2;
+      s->ks_host[i].stalled = !improving;
+    }
+    if (!again) break;
+    // push the stall flags back before the restart kernels read them
+    VAG_CUDA(cudaMemcpyAsync(s->ks, s->ks_host, sizeof(KrylovScalars) * ns, cudaMemcpyHostToDevice, st));
+    VAG_CUDA(cudaMemsetAsync(s->n_done, 0, sizeof(int), st));
+    if (amg) {
+      k_restart_m<<<nt, NT, 0, st>>>(s->rhs, s->kq, s->kr, tl, s->partials, s->counter, s->ks);
+      amg_apply(s, s->kr, s->kz, st);
+      k_rz_start<<<nt, NT, 0, st>>>(s->kr, s->kz, s->kp, tl, s->partials, s->counter, s->ks, s->n_done);
+      note_launches(2);
+    } else {
+      k_restart<<<nt, NT, 0, st>>>(s->rhs, s->kq, s->dinv, s->kr, s->kp, tl, s->partials, s->counter, s->ks,
+                                   s->n_done);
+      note_launches(1);
+    }
   }
-  // true residual and the full solution vector
-  launch_spmv(s, s->kx, s->kq, 0, st);
-  k_resid2<<<g, NT, 0, st>>>(n, s->rhs, s->kq, s->partials, s->counter, s->ks);
+  finish_solve(s, info, false);
+  info->ms_setup = setup_ms;
+  info->ms_solve -= setup_ms;
+}
+
+static vag_solve_info info_of(const KrylovScalars &k, bool mixed) {
+  vag_solve_info o{};
+  o.iterations = mixed ? k.inner_total : k.iter;
+  o.outer = mixed ? k.iter : 1;
+  o.rel_residual = k.bb > 0 ? sqrt(k.res2 / k.bb) : 0.0;
+  o.status = k.breakdown ? VAG_EBREAKDOWN : (k.res2 > k.tol2 ? VAG_ENOTCONVERGED : VAG_OK);
+  return o;
+}
+
+void finish_solve(System *s, vag_solve_info *info, bool mixed) {
+  cudaStream_t st = s->ctx->stream;
+  const int n = s->n_rows, ns = s->seg.n_sys;
   k_scatter_rows<<<grid_for(n, NT), NT, 0, st>>>(n, s->dof_of_row, s->kx, s->u);
+  note_launches(1);
   k_scatter_dir<<<grid_for(s->nd, NT), NT, 0, st>>>(s->nd, s->dir_nodes, s->dir_vals, s->u);
+  note_launches(1);
   VAG_CHECK_LAUNCH();
   recover_cells_and_fluxes(s);
   VAG_CUDA(cudaEventRecord(s->ev1, st));
-  VAG_CUDA(cudaMemcpyAsync(s->ks_host, s->ks, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st));
+  VAG_CUDA(cudaMemcpyAsync(s->ks_host, s->ks, sizeof(KrylovScalars) * ns, cudaMemcpyDeviceToHost, st));
   VAG_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, s->ev0, s->ev1);
-  const KrylovScalars &k = *s->ks_host;
-  info->iterations = k.iter;
-  info->outer = 1;
-  info->rel_residual = k.bb > 0 ? sqrt(k.res2 / k.bb) : 0.0;
-  info->ms_setup = 0.0;
-  info->ms_solve = ms;
-  if (k.breakdown) info->status = VAG_EBREAKDOWN;
-  else if (k.rr > k.tol2) info->status = VAG_ENOTCONVERGED;
-  else info->status = VAG_OK;
+  // aggregate over the batch: most iterations, worst residual, worst status
+  vag_solve_info agg{};
+  agg.ms_solve = ms;
+  agg.status = VAG_OK;
+  for (int i = 0; i < ns; ++i) {
+    const vag_solve_info o = info_of(s->ks_host[i], mixed);
+    agg.iterations = std::max(agg.iterations, o.iterations);
+    agg.outer = std::max(agg.outer, o.outer);
+    agg.rel_residual = std::max(agg.rel_residual, o.rel_residual);
+    if (o.status == VAG_EBREAKDOWN) agg.status = VAG_EBREAKDOWN;
+    else if (o.status == VAG_ENOTCONVERGED && agg.status == VAG_OK) agg.status = VAG_ENOTCONVERGED;
+  }
+  *info = agg;
   s->solved = true;
+  s->last_mixed = mixed;
+}
+
+void solve_infos(const System *s, vag_solve_info *infos) {
+  for (int i = 0; i < s->seg.n_sys; ++i) infos[i] = info_of(s->ks_host[i], s->last_mixed);
 }
 
 }  // namespace vag

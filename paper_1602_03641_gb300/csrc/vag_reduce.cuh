@@ -54,4 +54,42 @@ __device__ __forceinline__ bool grid_sum(const double (&v)[K], double *partials,
   return true;
 }
 
+// Row tiles of a batch: tile t covers rows [row0[t], row1[t]) of system
+// sys[t]; sys_tile0 gives the first tile of each system (n_sys+1 entries).
+struct Tiles {
+  const int *sys, *row0, *row1, *sys_tile0;
+};
+
+// Sums K values per system: per-tile block sums go to partials[K*t + k]; the
+// last tile of system `sys` to arrive adds its system's partials in tile
+// order and returns true in all its threads with out[] valid in thread 0.
+template <int NT, int K>
+__device__ __forceinline__ bool seg_sum(const double (&v)[K], double *partials, unsigned *counter, const Tiles &tl,
+                                        int t, int sys, double (&out)[K]) {
+  __shared__ double sh[NT / 32];
+  __shared__ bool last;
+  double bs[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) bs[k] = block_sum<NT>(v[k], sh);
+  const int t0 = tl.sys_tile0[sys], t1 = tl.sys_tile0[sys + 1];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)K * t + k] = bs[k];
+    __threadfence();
+    const unsigned ticket = atomicAdd(&counter[sys], 1u);
+    last = (ticket == (unsigned)(t1 - t0 - 1));
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double acc = 0.0;
+    for (int b = t0 + threadIdx.x; b < t1; b += NT) acc += __ldcg(&partials[(size_t)K * b + k]);
+    out[k] = block_sum<NT>(acc, sh);
+  }
+  if (threadIdx.x == 0) counter[sys] = 0u;
+  return true;
+}
+
 }  // namespace vag

@@ -1,0 +1,100 @@
+// Sliced-ELL copy (slices of 32 consecutive rows, column-major inside a
+// slice) of the eliminated system, for thread-per-row SpMV: the 32 threads of
+// a warp read entry k of their 32 rows as one contiguous 256-byte (FP64) or
+// 128-byte (FP32) segment, and a row costs exactly one FMA per stored entry
+// (no cross-lane reduction -- on GB300 the FP64 pipe, not HBM, limits a
+// lane-split CSR SpMV).  Entries of a row keep their CSR order, so a row sum
+// is the same sequence of FMAs whatever the slice layout.
+#include "vag_internal.cuh"
+
+namespace vag {
+namespace {
+
+constexpr int TB = 256;
+
+__global__ void k_slice_width(int n, int n_slices, const int *__restrict__ rowptr, int *__restrict__ width) {
+  const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= n_slices) return;
+  int w = 0;
+  const int r1 = min(n, (sl + 1) * 32);
+  for (int r = sl * 32; r < r1; ++r) w = max(w, rowptr[r + 1] - rowptr[r]);
+  width[sl] = 32 * w;
+}
+
+__global__ void k_sell_cols(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                            const int *__restrict__ slice_ptr, int *__restrict__ scol) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const int b = rowptr[row], e = rowptr[row + 1];
+  const int base = slice_ptr[row >> 5] + (row & 31);
+  for (int k = 0; k < e - b; ++k) scol[base + 32 * k] = col[b + k];
+}
+
+// padding slots point at the row itself (never read: rows stop at their length)
+__global__ void k_sell_pad(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
+                           int *__restrict__ scol) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= ((n + 31) / 32) * 32) return;
+  const int sl = row >> 5;
+  const int w = (slice_ptr[sl + 1] - slice_ptr[sl]) / 32;
+  const int len = row < n ? rowptr[row + 1] - rowptr[row] : 0;
+  const int base = slice_ptr[sl] + (row & 31);
+  for (int k = len; k < w; ++k) scol[base + 32 * k] = row < n ? row : 0;
+}
+
+template <class T>
+__global__ void k_sell_vals(int n, const int *__restrict__ rowptr, const double *__restrict__ val,
+                            const double *__restrict__ scale, const int *__restrict__ col,
+                            const int *__restrict__ slice_ptr, T *__restrict__ sval) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const int b = rowptr[row], e = rowptr[row + 1];
+  const int base = slice_ptr[row >> 5] + (row & 31);
+  const double sr = scale ? scale[row] : 1.0;
+  for (int k = 0; k < e - b; ++k) {
+    const double v = scale ? sr * val[b + k] * scale[col[b + k]] : val[b + k];
+    sval[base + 32 * k] = (T)v;
+  }
+}
+
+}  // namespace
+
+void build_sell(System *s) {
+  cudaStream_t st = s->ctx->stream;
+  const int n = s->n_rows;
+  s->n_slices = (n + 31) / 32;
+  s->slice_ptr = sys_alloc<int>(s, (size_t)s->n_slices + 1);
+  int *width;
+  VAG_CUDA(cudaMallocAsync(&width, sizeof(int) * ((size_t)s->n_slices + 1), st));
+  k_slice_width<<<grid_for(s->n_slices, TB), TB, 0, st>>>(n, s->n_slices, s->rowptr, width);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
+  s->sell_nnz = scan_exclusive(width, s->slice_ptr, s->n_slices, st);
+  VAG_CUDA(cudaFreeAsync(width, st));
+  s->scol = sys_alloc<int>(s, (size_t)s->sell_nnz);
+  s->sval = sys_alloc<double>(s, (size_t)s->sell_nnz);
+  k_sell_cols<<<grid_for(n, TB), TB, 0, st>>>(n, s->rowptr, s->col, s->slice_ptr, s->scol);
+  k_sell_pad<<<grid_for((int64_t)s->n_slices * 32, TB), TB, 0, st>>>(n, s->rowptr, s->slice_ptr, s->scol);
+  note_launches(2);
+  VAG_CHECK_LAUNCH();
+}
+
+void sell_values(System *s) {
+  cudaStream_t st = s->ctx->stream;
+  k_sell_vals<double><<<grid_for(s->n_rows, TB), TB, 0, st>>>(s->n_rows, s->rowptr, s->val, nullptr, s->col,
+                                                               s->slice_ptr, s->sval);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
+}
+
+// FP32 copy of D^{-1/2} A D^{-1/2} (scale = D^{-1/2}, FP64) for the inner
+// solve of the mixed-precision path.
+void sell_values_scaled_f32(System *s, const double *scale, float *out) {
+  cudaStream_t st = s->ctx->stream;
+  k_sell_vals<float><<<grid_for(s->n_rows, TB), TB, 0, st>>>(s->n_rows, s->rowptr, s->val, scale, s->col,
+                                                              s->slice_ptr, out);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
+}
+
+}  // namespace vag

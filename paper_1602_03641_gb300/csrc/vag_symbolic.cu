@@ -171,22 +171,47 @@ __global__ void k_sort_segments(int n, const int *__restrict__ ptr, int *adj) {
   }
 }
 
-__global__ void k_row_flags(int nv, int nf, const int *__restrict__ node_dir, int *flagv) {
+__global__ void k_node_flags(int nv, const int *__restrict__ node_dir, int *flagv) {
   int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= nv + nf) return;
-  flagv[d] = (d >= nv) ? 1 : (node_dir[d] < 0);
+  if (d >= nv) return;
+  flagv[d] = node_dir[d] < 0;
 }
 
-__global__ void k_row_maps(int nv, int nf, const int *__restrict__ flagv, const int *__restrict__ scan,
-                           int *row_of_dof, int *dof_of_row) {
+// system of entity i given the segment starts (n_sys+1 entries, increasing)
+__device__ __forceinline__ int seg_of(int i, const int *__restrict__ start, int n_sys) {
+  int lo = 0, hi = n_sys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Krylov rows, system by system: the non-Dirichlet nodes of system g in
+// increasing id, then the fracture faces of g.  With node_rank the exclusive
+// scan of the non-Dirichlet flags, node s of g gets row node_rank[s] +
+// ff_start[g] and fracture face f of g gets node_rank[node_start[g+1]] + f.
+__global__ void k_row_maps(int nv, int nf, int n_sys, const int *__restrict__ node_start,
+                           const int *__restrict__ ff_start, const int *__restrict__ flagv,
+                           const int *__restrict__ node_rank, int *row_of_dof, int *dof_of_row) {
   int d = blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= nv + nf) return;
-  if (flagv[d]) {
-    row_of_dof[d] = scan[d];
-    dof_of_row[scan[d]] = d;
+  int row = -1;
+  if (d < nv) {
+    if (flagv[d]) row = node_rank[d] + ff_start[seg_of(d, node_start, n_sys)];
   } else {
-    row_of_dof[d] = -1;
+    const int f = d - nv;
+    row = node_rank[node_start[seg_of(f, ff_start, n_sys) + 1]] + f;
   }
+  row_of_dof[d] = row;
+  if (row >= 0) dof_of_row[row] = d;
+}
+
+__global__ void k_row_starts(int n_sys, const int *__restrict__ node_start, const int *__restrict__ ff_start,
+                             const int *__restrict__ node_rank, int *row_start) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g > n_sys) return;
+  row_start[g] = node_rank[node_start[g]] + ff_start[g];
 }
 
 struct PatView {
@@ -319,11 +344,11 @@ void symbolic_phase(System *s) {
   VAG_CUDA(cudaMemsetAsync(table, 0xff, sizeof(int) * H, st));
   VAG_CUDA(cudaMemsetAsync(ff_cnt, 0, sizeof(int) * (size_t)(nf > 0 ? nf : 1), st));
 
-  k_mark_dirichlet<<<grid_for(nd, TB), TB, 0, st>>>(nd, s->dir_nodes, nv, s->node_dir, s->status);
-  k_check_cells<<<grid_for((int64_t)nc * 8, TB), TB, 0, st>>>(nc, s->cell_nodes, nv, n2c_cnt, s->status);
+  k_mark_dirichlet<<<grid_for(nd, TB), TB, 0, st>>>(nd, s->dir_nodes, nv, s->node_dir, s->status); note_launches(1);
+  k_check_cells<<<grid_for((int64_t)nc * 8, TB), TB, 0, st>>>(nc, s->cell_nodes, nv, n2c_cnt, s->status); note_launches(1);
   if (nf) {
-    k_ff_prep<<<grid_for(nf, TB), TB, 0, st>>>(nf, s->ff_nodes, nv, ffs, s->node_isfrac, n2f_cnt, s->status);
-    k_ff_insert<<<grid_for(nf, TB), TB, 0, st>>>(nf, ffs, table, H - 1, s->status);
+    k_ff_prep<<<grid_for(nf, TB), TB, 0, st>>>(nf, s->ff_nodes, nv, ffs, s->node_isfrac, n2f_cnt, s->status); note_launches(1);
+    k_ff_insert<<<grid_for(nf, TB), TB, 0, st>>>(nf, ffs, table, H - 1, s->status); note_launches(1);
   }
   VAG_CHECK_LAUNCH();
   // bad indices make every later kernel unsafe: stop here
@@ -334,38 +359,52 @@ void symbolic_phase(System *s) {
   if (st0 & ST_HASH_FULL) fail(VAG_EMESH, "fracture-face table overflow");
 
   k_cell_face_lookup<<<grid_for((int64_t)nc * 6, TB), TB, 0, st>>>(
-      nc, s->cell_nodes, ffs, table, H - 1, nf, s->cell_ff, ff_cnt, s->ff_cells, s->ff_lface, s->status);
-  if (nf) k_ff_finish<<<grid_for(nf, TB), TB, 0, st>>>(nf, ff_cnt, s->ff_cells, s->ff_lface, s->status);
+      nc, s->cell_nodes, ffs, table, H - 1, nf, s->cell_ff, ff_cnt, s->ff_cells, s->ff_lface, s->status); note_launches(1);
+  if (nf) {
+    k_ff_finish<<<grid_for(nf, TB), TB, 0, st>>>(nf, ff_cnt, s->ff_cells, s->ff_lface, s->status);
+    note_launches(1);
+  }
   VAG_CHECK_LAUNCH();
 
   // fracture cells
-  k_fc_flag<<<grid_for(nc, TB), TB, 0, st>>>(nc, s->cell_ff, flagv);
+  k_fc_flag<<<grid_for(nc, TB), TB, 0, st>>>(nc, s->cell_ff, flagv); note_launches(1);
   s->n_fc = scan_exclusive(flagv, scanv, nc, st);
-  k_fc_index<<<grid_for(nc, TB), TB, 0, st>>>(nc, flagv, scanv, s->fc_index);
+  k_fc_index<<<grid_for(nc, TB), TB, 0, st>>>(nc, flagv, scanv, s->fc_index); note_launches(1);
 
   // node -> cell adjacency, sorted by cell id
   scan_exclusive(n2c_cnt, s->n2c_ptr, nv, st, false);
   VAG_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * ncnt, st));
   k_fill_adj<<<grid_for((int64_t)nc * 8, TB), TB, 0, st>>>((int64_t)nc * 8, 8, s->cell_nodes, s->n2c_ptr,
-                                                          cursor, s->n2c);
-  k_sort_segments<<<grid_for(nv, TB), TB, 0, st>>>(nv, s->n2c_ptr, s->n2c);
+                                                          cursor, s->n2c); note_launches(1);
+  k_sort_segments<<<grid_for(nv, TB), TB, 0, st>>>(nv, s->n2c_ptr, s->n2c); note_launches(1);
   // node -> fracture-face adjacency
   scan_exclusive(n2f_cnt, s->n2f_ptr, nv, st, false);
   if (nf) {
     VAG_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * ncnt, st));
     k_fill_adj<<<grid_for((int64_t)nf * 4, TB), TB, 0, st>>>((int64_t)nf * 4, 4, s->ff_nodes, s->n2f_ptr,
-                                                            cursor, s->n2f);
-    k_sort_segments<<<grid_for(nv, TB), TB, 0, st>>>(nv, s->n2f_ptr, s->n2f);
+                                                            cursor, s->n2f); note_launches(1);
+    k_sort_segments<<<grid_for(nv, TB), TB, 0, st>>>(nv, s->n2f_ptr, s->n2f); note_launches(1);
   }
   VAG_CHECK_LAUNCH();
 
-  // Krylov unknowns
-  k_row_flags<<<grid_for(nv + nf, TB), TB, 0, st>>>(nv, nf, s->node_dir, flagv);
-  s->n_rows = scan_exclusive(flagv, scanv, nv + nf, st);
-  s->n_row_nodes = s->n_rows - nf;
+  // Krylov unknowns, contiguous per system of the batch
+  k_node_flags<<<grid_for(nv, TB), TB, 0, st>>>(nv, s->node_dir, flagv);
+  note_launches(1);
+  const int n_row_nodes = scan_exclusive(flagv, scanv, nv, st);
+  s->n_rows = n_row_nodes + nf;
+  s->n_row_nodes = n_row_nodes;
   s->dof_of_row = sys_alloc<int>(s, s->n_rows);
-  k_row_maps<<<grid_for(nv + nf, TB), TB, 0, st>>>(nv, nf, flagv, scanv, s->row_of_dof, s->dof_of_row);
+  Segments &g = s->seg;
+  k_row_maps<<<grid_for(nv + nf, TB), TB, 0, st>>>(nv, nf, g.n_sys, g.d_node_start, g.d_ff_start, flagv, scanv,
+                                                   s->row_of_dof, s->dof_of_row);
+  note_launches(1);
+  k_row_starts<<<grid_for(g.n_sys + 1, TB), TB, 0, st>>>(g.n_sys, g.d_node_start, g.d_ff_start, scanv,
+                                                         g.d_row_start);
+  note_launches(1);
   VAG_CHECK_LAUNCH();
+  g.row_start.assign(g.n_sys + 1, 0);
+  VAG_CUDA(cudaMemcpyAsync(g.row_start.data(), g.d_row_start, sizeof(int) * (g.n_sys + 1), cudaMemcpyDeviceToHost,
+                           st));
 
   int st1 = read_status(s);
   if (st1 & ST_FFACE_NOT_FACE) fail(VAG_EMESH, "a fracture face is not a face of any cell");
@@ -378,7 +417,7 @@ void symbolic_phase(System *s) {
   s->diag_pos = sys_alloc<int>(s, s->n_rows);
   int *cnt;
   VAG_CUDA(cudaMallocAsync(&cnt, sizeof(int) * ((size_t)s->n_rows + 1), st));
-  k_row_count<<<grid_for(s->n_rows, 128), 128, 0, st>>>(pv, s->n_rows, s->dof_of_row, cnt, s->status);
+  k_row_count<<<grid_for(s->n_rows, 128), 128, 0, st>>>(pv, s->n_rows, s->dof_of_row, cnt, s->status); note_launches(1);
   VAG_CHECK_LAUNCH();
   s->nnz = scan_exclusive(cnt, s->rowptr, s->n_rows, st);
   const int st2 = read_status(s);
@@ -386,7 +425,7 @@ void symbolic_phase(System *s) {
   if (st2 & ST_ISOLATED) fail(VAG_EMESH, "a node belongs to no cell");
   s->col = sys_alloc<int>(s, (size_t)s->nnz);
   k_row_fill<<<grid_for(s->n_rows, 128), 128, 0, st>>>(pv, s->n_rows, s->dof_of_row, s->rowptr, s->col,
-                                                      s->diag_pos);
+                                                      s->diag_pos); note_launches(1);
   VAG_CHECK_LAUNCH();
 
   VAG_CUDA(cudaFreeAsync(cnt, st));

@@ -197,58 +197,47 @@ __device__ __forceinline__ void for_edges(const TView &t, int mu, Fn &&fn) {
 
 __device__ __forceinline__ bool is_dir(const TView &t, int mu) { return mu < t.nv && t.node_dir[mu] >= 0; }
 
-// Per CV: number of inflow edges and the CFL ratio phi / outflow.
-__global__ void __launch_bounds__(TB) k_map_count(TView t, const double *__restrict__ phi, int *__restrict__ cnt,
-                                                  double *partials, unsigned *counter, double *dts) {
+// Per CV: number of inflow edges and the CFL ratio phi / outflow; the ratio
+// is min-reduced per system with atomicMin on the bit pattern of a positive
+// double (order-independent, hence deterministic).
+__global__ void __launch_bounds__(TB) k_map_count(TView t, const double *__restrict__ phi, const int *__restrict__ cv_sys,
+                                                  int *__restrict__ cnt, unsigned long long *dt_bits) {
   const int n = t.nv + t.nf + t.nc;
-  double best = INFINITY;
-  for (int mu = blockIdx.x * TB + threadIdx.x; mu < n; mu += gridDim.x * TB) {
-    if (is_dir(t, mu)) { cnt[mu] = 0; continue; }
-    int c = 0;
-    double out = 0.0;
-    for_edges(t, mu, [&](double Fin, int) {
-      if (Fin > 0.0) ++c;
-      else out -= Fin;
-    });
-    cnt[mu] = c;
-    if (out > 0.0) best = fmin(best, phi[mu] / out);
-  }
-  // min-reduction (order-independent); reuse the sum helper on -1/x is not
-  // exact, so reduce explicitly with shared memory
-  __shared__ double sh[TB / 32];
-  __shared__ bool last;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = best;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = sh[0];
-    for (int w = 1; w < TB / 32; ++w) m = fmin(m, sh[w]);
-    partials[blockIdx.x] = m;
-    __threadfence();
-    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double m = INFINITY;
-    for (int b = 0; b < (int)gridDim.x; ++b) m = fmin(m, __ldcg(&partials[b]));
-    dts[0] = m;
-    *counter = 0u;
-  }
+  const int mu = blockIdx.x * TB + threadIdx.x;
+  if (mu >= n) return;
+  if (is_dir(t, mu)) { cnt[mu] = 0; return; }
+  int c = 0;
+  double out = 0.0;
+  for_edges(t, mu, [&](double Fin, int) {
+    if (Fin > 0.0) ++c;
+    else out -= Fin;
+  });
+  cnt[mu] = c;
+  if (out > 0.0) atomicMin(&dt_bits[cv_sys[mu]], (unsigned long long)__double_as_longlong(phi[mu] / out));
 }
 
-// dts[1] = cfl * dts[0] (cfl > 0) or the given dt.
-__global__ void k_pick_dt(double *dts, double cfl, double dt) { dts[1] = cfl > 0 ? cfl * dts[0] : dt; }
+// Per system: dts[2g] = CFL bound (bits -> double), dts[2g+1] = the step
+// (cfl * bound, or the given dt; 0 when no control volume has outflow).
+__global__ void k_pick_dt(int n_sys, const unsigned long long *__restrict__ dt_bits, double *dts, double cfl,
+                          double dt) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_sys) return;
+  double m = __longlong_as_double((long long)dt_bits[g]);
+  if (m > 1e300) m = INFINITY;   // no control volume of this system has outflow
+  dts[2 * g] = m;
+  double h = cfl > 0 ? cfl * m : dt;
+  if (!(h < INFINITY)) h = 0.0;
+  dts[2 * g + 1] = h;
+}
 
-__global__ void k_map_fill(TView t, const double *__restrict__ phi, const int *__restrict__ rowptr,
-                           const double *__restrict__ dts, double *__restrict__ diag, int *__restrict__ col,
-                           double *__restrict__ w) {
+__global__ void k_map_fill(TView t, const double *__restrict__ phi, const int *__restrict__ cv_sys,
+                           const int *__restrict__ rowptr, const double *__restrict__ dts, double *__restrict__ diag,
+                           int *__restrict__ col, double *__restrict__ w) {
   const int n = t.nv + t.nf + t.nc;
   const int mu = blockIdx.x * blockDim.x + threadIdx.x;
   if (mu >= n) return;
   if (is_dir(t, mu)) { diag[mu] = 1.0; return; }
-  const double h = dts[1] / phi[mu];
+  const double h = dts[2 * cv_sys[mu] + 1] / phi[mu];
   int k = rowptr[mu];
   double out = 0.0;
   for_edges(t, mu, [&](double Fin, int nb) {
@@ -261,6 +250,24 @@ __global__ void k_map_fill(TView t, const double *__restrict__ phi, const int *_
     }
   });
   diag[mu] = 1.0 - h * out;
+}
+
+// system of every control volume of the union ([nodes | ffaces | cells])
+__global__ void k_cv_sys(int nv, int nf, int nc, int n_sys, const int *__restrict__ node_start,
+                         const int *__restrict__ ff_start, const int *__restrict__ cell_start, int *cv_sys) {
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mu >= nv + nf + nc) return;
+  const int *st;
+  int i;
+  if (mu < nv) { st = node_start; i = mu; }
+  else if (mu < nv + nf) { st = ff_start; i = mu - nv; }
+  else { st = cell_start; i = mu - nv - nf; }
+  int lo = 0, hi = n_sys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (st[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  cv_sys[mu] = lo;
 }
 
 __global__ void __launch_bounds__(TB) k_step(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
@@ -289,10 +296,13 @@ void recover_cells_and_fluxes(System *s) {
     s->Fff = sys_alloc<double>(s, 4 * (size_t)(s->nf > 0 ? s->nf : 1));
   }
   k_recover<<<grid_for(s->nc, TB), TB, 0, st>>>(s->nc, s->nv, s->cell_nodes, s->cell_ff, s->fc_index, s->n_fc,
-                                                s->Mc, s->Mfc, s->u, s->nf);
+                                                s->Mc, s->Mfc, s->u, s->nf); note_launches(1);
   k_cell_flux<<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, s->nv, s->nf, s->cell_nodes, s->cell_ff, s->fc_index,
-                                                    s->n_fc, s->Mc, s->Mfc, s->u, s->Fcn, s->Fcf);
-  if (s->nf) k_ff_flux<<<grid_for(s->nf, TB), TB, 0, st>>>(s->nf, s->nv, s->ff_nodes, s->Mff, s->u, s->Fff);
+                                                    s->n_fc, s->Mc, s->Mfc, s->u, s->Fcn, s->Fcf); note_launches(1);
+  if (s->nf) {
+    k_ff_flux<<<grid_for(s->nf, TB), TB, 0, st>>>(s->nf, s->nv, s->ff_nodes, s->Mff, s->u, s->Fff);
+    note_launches(1);
+  }
   VAG_CHECK_LAUNCH();
   s->have_flux = true;
 }
@@ -302,31 +312,37 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
                    const double *phi_m, const double *phi_f, const double *cbar) {
   cudaStream_t st = s->ctx->stream;
   const int n = s->n_cv;
+  const int ns = s->seg.n_sys;
   if (!s->phi) {
     s->phi = sys_alloc<double>(s, n);
     s->tdiag = sys_alloc<double>(s, n);
     s->trowptr = sys_alloc<int>(s, (size_t)n + 1);
     s->cbuf = sys_alloc<double>(s, 2 * (size_t)n);
-    s->dts = sys_alloc<double>(s, 4);
-  }
-  if (!s->partials) {
-    s->partials = sys_alloc<double>(s, 4 * (size_t)kMaxRedBlocks);
-    s->counter = sys_alloc<unsigned>(s, 4);
-    VAG_CUDA(cudaMemsetAsync(s->counter, 0, 4 * sizeof(unsigned), st));
+    s->dts = sys_alloc<double>(s, 2 * (size_t)ns);
+    s->seg.cv_sys = sys_alloc<int>(s, n);
+    k_cv_sys<<<grid_for(n, TB), TB, 0, st>>>(s->nv, s->nf, s->nc, ns, s->seg.d_node_start, s->seg.d_ff_start,
+                                             s->seg.d_cell_start, s->seg.cv_sys);
+    note_launches(1);
   }
   TView t{s->nv, s->nf, s->nc, s->cell_nodes, s->ff_nodes, s->cell_ff, s->ff_cells, s->ff_lface,
           s->node_dir, s->node_isfrac, s->n2c_ptr, s->n2c, s->n2f_ptr, s->n2f, s->cvol, s->ffarea, s->df,
           phi_m, phi_f, s->Fcn, s->Fcf, s->Fff, o->omega};
   VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   k_porous<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->status);
+  note_launches(1);
   int *cnt;
+  unsigned long long *dt_bits;
   VAG_CUDA(cudaMallocAsync(&cnt, sizeof(int) * ((size_t)n + 1), st));
-  int g = (int)std::min<int64_t>(grid_for(n, TB), std::min(num_sms() * 4, kMaxRedBlocks));
-  k_map_count<<<g, TB, 0, st>>>(t, s->phi, cnt, s->partials, s->counter, s->dts);
-  k_pick_dt<<<1, 1, 0, st>>>(s->dts, o->cfl, o->dt);
+  VAG_CUDA(cudaMallocAsync(&dt_bits, sizeof(unsigned long long) * ns, st));
+  VAG_CUDA(cudaMemsetAsync(dt_bits, 0x7f, sizeof(unsigned long long) * ns, st));   // > every finite ratio
+  k_map_count<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->seg.cv_sys, cnt, dt_bits);
+  note_launches(1);
+  k_pick_dt<<<grid_for(ns, TB), TB, 0, st>>>(ns, dt_bits, s->dts, o->cfl, o->dt);
+  note_launches(1);
   VAG_CHECK_LAUNCH();
   const int64_t nnz_t = scan_exclusive(cnt, s->trowptr, n, st);
   VAG_CUDA(cudaFreeAsync(cnt, st));
+  VAG_CUDA(cudaFreeAsync(dt_bits, st));
   if (read_status(s) & ST_NONPOSITIVE) fail(VAG_EINVAL, "a control volume has a non-positive porous volume");
   if (nnz_t > s->t_cap) {
     // grow the inflow-edge arrays (kept across calls)
@@ -335,28 +351,38 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     s->t_cap = nnz_t;
   }
   s->nnz_t = nnz_t;
-  k_map_fill<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->trowptr, s->dts, s->tdiag, s->tcol, s->tval);
+  k_map_fill<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->seg.cv_sys, s->trowptr, s->dts, s->tdiag, s->tcol,
+                                             s->tval);
+  note_launches(1);
   // c^0 with the Dirichlet values
   double *c0 = s->cbuf, *c1 = s->cbuf + n;
   VAG_CUDA(cudaMemcpyAsync(c0, c_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   k_set_dir<<<grid_for(s->nd, TB), TB, 0, st>>>(s->nd, s->dir_nodes, cbar, c0);
+  note_launches(1);
   VAG_CHECK_LAUNCH();
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   const int gs = grid_for(n, TB);
   for (int k = 0; k < o->n_steps; ++k) {
     k_step<<<gs, TB, 0, st>>>(n, s->trowptr, s->tcol, s->tval, s->tdiag, c0, c1);
+    note_launches(1);
     std::swap(c0, c1);
   }
   VAG_CHECK_LAUNCH();
   VAG_CUDA(cudaEventRecord(s->ev1, st));
   VAG_CUDA(cudaMemcpyAsync(c_dev, c0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  double dts[2];
-  VAG_CUDA(cudaMemcpyAsync(dts, s->dts, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  s->dts_host.resize(2 * (size_t)ns);
+  VAG_CUDA(cudaMemcpyAsync(s->dts_host.data(), s->dts, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, st));
   VAG_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, s->ev0, s->ev1);
-  info->dt_max = dts[0];
-  info->dt = dts[1];
+  // a batch reports its smallest bound and step; vag_transport_get_dts gives each
+  double dmax = s->dts_host[0], dt = s->dts_host[1];
+  for (int g = 1; g < ns; ++g) {
+    dmax = std::min(dmax, s->dts_host[2 * g]);
+    dt = std::min(dt, s->dts_host[2 * g + 1]);
+  }
+  info->dt_max = dmax;
+  info->dt = dt;
   info->steps = o->n_steps;
   info->ms = ms;
 }

@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys as _sys
 from typing import Optional
 
 import numpy as np
@@ -72,9 +73,15 @@ _SIGS = {
     "vag_ctx_set_stream": (C.c_int, [P, P]),
     "vag_last_error": (C.c_char_p, [P]),
     "vag_ctx_bytes_in_use": (C.c_size_t, [P]),
+    "vag_launch_count": (C.c_ulonglong, []),
     "vag_assemble": (C.c_int, [P, C.POINTER(vag_mesh), C.POINTER(vag_props), C.POINTER(vag_dirichlet),
                                C.c_int, C.POINTER(P)]),
     "vag_update_props": (C.c_int, [P, C.POINTER(vag_props), C.c_int]),
+    "vag_assemble_batch": (C.c_int, [P, C.c_int32, C.POINTER(vag_mesh), C.POINTER(vag_props),
+                                     C.POINTER(vag_dirichlet), C.c_int, C.POINTER(P)]),
+    "vag_system_get_batch": (C.c_int, [P, C.POINTER(C.c_int32), P, P, P, P]),
+    "vag_solve_get_infos": (C.c_int, [P, C.POINTER(vag_solve_info)]),
+    "vag_transport_get_dts": (C.c_int, [P, P, P]),
     "vag_system_destroy": (None, [P]),
     "vag_system_get_info": (C.c_int, [P, C.POINTER(vag_system_info)]),
     "vag_solve": (C.c_int, [P, C.POINTER(vag_solve_opts), P, C.POINTER(vag_solve_info)]),
@@ -107,6 +114,11 @@ def lib():
 
 def declared_symbols():
     return list(_SIGS)
+
+
+def launch_count() -> int:
+    """Kernels launched by libvag in this process so far."""
+    return int(lib().vag_launch_count())
 
 
 class VagError(RuntimeError):
@@ -173,6 +185,8 @@ class Context:
             self.h = None
 
     def __del__(self):
+        if _sys.is_finalizing():      # the CUDA runtime may already be gone
+            return
         try:
             self.close()
         except Exception:
@@ -193,6 +207,34 @@ class Context:
         self.check(self._L.vag_assemble(self.h, C.byref(m), C.byref(p), C.byref(b), mem, C.byref(h)))
         return System(self, h)
 
+    def assemble_batch(self, problems):
+        """problems: list of dicts with keys xyz, cell_nodes, ff_nodes,
+        lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values (numpy host or
+        CUDA tensors, all of one kind)."""
+        n = len(problems)
+        ms, ps, bs = (vag_mesh * n)(), (vag_props * n)(), (vag_dirichlet * n)()
+        keep = []
+        mem = None
+        for i, q in enumerate(problems):
+            arrs = [q["xyz"], q["cell_nodes"], q["ff_nodes"], q["lambda_m"], q["lambda_f"], q["d_f"],
+                    q["dir_nodes"], q["dir_values"]]
+            keep.append(arrs)
+            mm = _mem_of(*arrs)
+            if mem is None:
+                mem = mm
+            elif mm != mem:
+                raise ValueError("mix of host and device arrays in one batch")
+            size = (lambda a: int(a.numel() if _is_torch(a) else a.size))
+            ms[i] = vag_mesh(size(q["xyz"]) // 3, _ptr(q["xyz"], np.float64), size(q["cell_nodes"]) // 8,
+                             _ptr(q["cell_nodes"], np.int32), size(q["ff_nodes"]) // 4, _ptr(q["ff_nodes"], np.int32))
+            ps[i] = vag_props(_ptr(q["lambda_m"], np.float64), _ptr(q["lambda_f"], np.float64),
+                              _ptr(q["d_f"], np.float64), float(q["mu"]))
+            bs[i] = vag_dirichlet(size(q["dir_nodes"]), _ptr(q["dir_nodes"], np.int32),
+                                  _ptr(q["dir_values"], np.float64))
+        h = P()
+        self.check(self._L.vag_assemble_batch(self.h, n, ms, ps, bs, mem, C.byref(h)))
+        return System(self, h)
+
 
 class System:
     def __init__(self, ctx: Context, h):
@@ -206,6 +248,8 @@ class System:
             self.h = None
 
     def __del__(self):
+        if _sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -215,6 +259,28 @@ class System:
         i = vag_system_info()
         self.ctx.check(self._L.vag_system_get_info(self.h, C.byref(i)))
         return i
+
+    def batch_layout(self):
+        """dict of numpy arrays (n_sys+1): node_start, ff_start, cell_start, row_start."""
+        n = C.c_int32()
+        self.ctx.check(self._L.vag_system_get_batch(self.h, C.byref(n), None, None, None, None))
+        out = {k: np.empty(n.value + 1, np.int32) for k in ("node_start", "ff_start", "cell_start", "row_start")}
+        self.ctx.check(self._L.vag_system_get_batch(self.h, C.byref(n), _ptr(out["node_start"]), _ptr(out["ff_start"]),
+                                                    _ptr(out["cell_start"]), _ptr(out["row_start"])))
+        out["n_sys"] = n.value
+        return out
+
+    def solve_infos(self):
+        n = self.batch_layout()["n_sys"]
+        arr = (vag_solve_info * n)()
+        self.ctx.check(self._L.vag_solve_get_infos(self.h, arr))
+        return list(arr)
+
+    def transport_dts(self):
+        n = self.batch_layout()["n_sys"]
+        dmax = np.empty(n); dt = np.empty(n)
+        self.ctx.check(self._L.vag_transport_get_dts(self.h, _ptr(dmax), _ptr(dt)))
+        return dmax, dt
 
     def update_props(self, lambda_m, lambda_f, d_f, mu):
         mem = _mem_of(lambda_m, lambda_f, d_f)
@@ -282,6 +348,22 @@ class System:
         phi = np.empty(self.info().n_cv)
         self.ctx.check(self._L.vag_export_porous_volumes(self.h, _ptr(phi), VAG_MEM_HOST))
         return phi
+
+
+def problem_arrays(pb, device=False):
+    """The ABI arrays of a ``vag_inputs.Problem``-like object as a dict."""
+    q = dict(xyz=np.ascontiguousarray(pb.xyz, np.float64).ravel(),
+             cell_nodes=np.ascontiguousarray(pb.cell_nodes, np.int32).ravel(),
+             ff_nodes=np.ascontiguousarray(pb.ff_nodes, np.int32).ravel(),
+             lambda_m=np.ascontiguousarray(pb.lambda_m, np.float64).ravel(),
+             lambda_f=np.ascontiguousarray(pb.lambda_f, np.float64), d_f=np.ascontiguousarray(pb.d_f, np.float64),
+             dir_nodes=np.ascontiguousarray(pb.dir_nodes, np.int32),
+             dir_values=np.ascontiguousarray(pb.dir_values, np.float64))
+    if device:
+        import torch
+        q = {k: torch.from_numpy(v).cuda() for k, v in q.items()}
+    q["mu"] = pb.mu
+    return q
 
 
 def assemble_problem(ctx: Context, pb, device=False):
