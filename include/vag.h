@@ -275,6 +275,35 @@ vag_status vag_set_fluxes(vag_system *sys, const double *F_cell_nodes, const dou
 /* Porous volumes phi_mu [n_cv] of the last vag_transport (0 at Dirichlet nodes). */
 vag_status vag_export_porous_volumes(const vag_system *sys, double *phi, int mem);
 
+/* ------------------------------------------------- allocation-free variant */
+
+/* Largest matrix (rows) vag_spmv_dot_noalloc accepts: its scratch holds one
+ * partial sum per 32 rows in a fixed 1 MiB device array. */
+#define VAG_NOALLOC_MAX_ROWS (1 << 22)
+
+/*
+ * y = A x and *xdoty = x . y for a CSR matrix the caller owns, allocating
+ * nothing -- for callers that cannot call cudaMalloc where they need the
+ * product (inside their own stream capture, allocation-free serving threads,
+ * memory fully reserved by another runtime).  The paper has no counterpart:
+ * this is the library's SpMV with the fused dot of its CG iteration, with the
+ * block partial sums kept in a fixed file-scope device array (1 MiB plus a
+ * counter) that every GPU which loads the library holds until the process
+ * exits.
+ *   n_rows  rows and columns, 0 <= n_rows <= VAG_NOALLOC_MAX_ROWS (else
+ *           VAG_EINVAL, nothing launched);
+ *   rowptr [n_rows+1], col [nnz] (int32), val [nnz], x [n_rows], y [n_rows],
+ *           xdoty [1]: device pointers owned by the caller;
+ *   stream  cudaStream_t (void*), NULL = the legacy default stream.
+ * Stream-ordered: returns without waiting.  VAG_ECUDA if a CUDA call fails.
+ * The first call on a device looks up the scratch address (no allocation);
+ * make it before any stream capture that includes a call.  All calls on a
+ * device share the scratch: calls whose kernels overlap on the GPU race and
+ * must be ordered (same stream, or events).
+ */
+vag_status vag_spmv_dot_noalloc(int32_t n_rows, const int32_t *rowptr, const int32_t *col, const double *val,
+                                const double *x, double *y, double *xdoty, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

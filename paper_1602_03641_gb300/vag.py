@@ -91,6 +91,7 @@ _SIGS = {
     "vag_export_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
     "vag_set_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
     "vag_export_porous_volumes": (C.c_int, [P, P, C.c_int]),
+    "vag_spmv_dot_noalloc": (C.c_int, [C.c_int32, P, P, P, P, P, P, P]),
 }
 
 _LIB = None
