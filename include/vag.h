@@ -275,6 +275,75 @@ vag_status vag_set_fluxes(vag_system *sys, const double *F_cell_nodes, const dou
 /* Porous volumes phi_mu [n_cv] of the last vag_transport (0 at Dirichlet nodes). */
 vag_status vag_export_porous_volumes(const vag_system *sys, double *phi, int mem);
 
+/* ---------------------------------------------------------------- server */
+
+/*
+ * Request server with continuous batching (the paper has no counterpart: its
+ * runs are single MPI jobs).  `slots` worker threads each own a context
+ * (stream and memory pool) on `device`.  A free slot takes the oldest queued
+ * request together with every queued request of identical solver settings
+ * (precision, preconditioner, rtol, maxit, n_steps, omega, cfl, mu) whose
+ * estimated device memory still fits mem_budget_bytes, runs them as one batch
+ * (vag_assemble_batch, vag_solve, vag_transport) and completes them.
+ * Requests that arrive while batches run are admitted as slots and budget
+ * free up; batches of different slots overlap on the GPU.  A request's
+ * results are bitwise the same as when it is solved alone.
+ */
+typedef struct vag_server vag_server;
+
+typedef struct {
+  int device;
+  size_t mem_budget_bytes;   /* admission budget for batches in flight (0 = none) */
+  int32_t slots;             /* concurrent batches (<= 0: 2)                      */
+  int32_t max_batch;         /* requests per batch (<= 0: 64)                     */
+} vag_server_opts;
+
+typedef struct {
+  vag_mesh mesh;             /* host pointers; everything is copied at submit     */
+  vag_props props;
+  vag_dirichlet bc;
+  const double *phi_m, *phi_f, *cbar;   /* transport data (when n_steps > 0)      */
+  const double *c0;          /* optional [n_cv] initial concentration (NULL: cbar
+                                on Dirichlet nodes, 0 elsewhere)                 */
+  double omega, cfl;
+  int32_t n_steps;
+  int precision, precond;
+  double rtol;
+  int32_t maxit;
+  double *u_out;             /* host [n_cv] or NULL: pressures ([nodes|ffaces|cells]) */
+  double *c_out;             /* host [n_cv] or NULL: c after n_steps; both must stay
+                                valid until vag_server_wait returns VAG_OK      */
+} vag_request;
+
+typedef struct {
+  vag_status status;         /* of the request's batch (VAG_ETIMEOUT: cancelled by
+                                vag_server_destroy before it ran)                 */
+  vag_solve_info solve;      /* this request's system                            */
+  vag_transport_info transport; /* dt_max and dt of this request's system        */
+  double latency_ms;         /* submit -> results written                        */
+  double queue_ms;           /* submit -> start of its batch                     */
+  int32_t batch_size;
+} vag_result;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, in_queue, in_flight;
+  double p50_ms, p99_ms;     /* latency over completed requests                   */
+  double solves_per_s;       /* completed / (last completion - first submit)     */
+  size_t bytes_reserved, peak_bytes;   /* admission estimates                     */
+} vag_server_stats;
+
+vag_status vag_server_create(const vag_server_opts *opts, vag_server **out);
+/* Non-blocking.  VAG_EBUDGET if the request alone exceeds the budget (it
+ * could never be admitted); VAG_EINVAL for malformed requests. */
+vag_status vag_server_submit(vag_server *srv, const vag_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (< 0: no limit) for a ticket; VAG_ETIMEOUT when it is
+ * not done yet (the ticket stays valid).  After VAG_OK the ticket is released. */
+vag_status vag_server_wait(vag_server *srv, uint64_t ticket, int32_t timeout_ms, vag_result *out);
+vag_status vag_server_get_stats(vag_server *srv, vag_server_stats *stats);
+const char *vag_server_last_error(const vag_server *srv);
+/* Cancels queued requests, finishes the batches in flight, joins the slots. */
+void vag_server_destroy(vag_server *srv);
+
 /* ------------------------------------------------- allocation-free variant */
 
 /* Largest matrix (rows) vag_spmv_dot_noalloc accepts: its scratch holds one

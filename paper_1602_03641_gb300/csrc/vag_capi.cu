@@ -73,10 +73,12 @@ __global__ void k_add_offset(int *a, int64_t n, int off) {
 }
 
 void free_ctx(vag_ctx *ctx) {
+  if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
   if (ctx->c.own_stream) {
     cudaStreamSynchronize(ctx->c.own_stream);
     cudaStreamDestroy(ctx->c.own_stream);
   }
+  if (ctx->c.pool) cudaMemPoolDestroy(ctx->c.pool);
   delete ctx;
 }
 
@@ -90,6 +92,7 @@ void destroy_system(vag_system *sys) {
   if (s->pcg_graph) cudaGraphExecDestroy(s->pcg_graph);
   if (s->mx.graph) cudaGraphExecDestroy(s->mx.graph);
   if (s->pcg_graph_amg) cudaGraphExecDestroy(s->pcg_graph_amg);
+  if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   amg_free(s);
   if (s->ks_host) cudaFreeHost(s->ks_host);
   if (s->n_done_host) cudaFreeHost(s->n_done_host);
@@ -123,6 +126,19 @@ vag_status vag_ctx_create(int device, size_t mem_budget_bytes, vag_ctx **out) {
     VAG_CUDA(cudaSetDevice(device));
     VAG_CUDA(cudaStreamCreateWithFlags(&c->c.own_stream, cudaStreamNonBlocking));
     c->c.stream = c->c.own_stream;
+    // a private stream-ordered pool that keeps freed memory for reuse, so
+    // systems assembled one after another do not pay for cudaMalloc/cudaFree
+    cudaMemPoolProps pp{};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    if (cudaMemPoolCreate(&c->c.pool, &pp) == cudaSuccess) {
+      unsigned long long keep = ~0ull;
+      cudaMemPoolSetAttribute(c->c.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      c->c.pool = nullptr;   // fall back to cudaMalloc
+    }
   });
   if (st != VAG_OK) return st;
   *out = c.release();
@@ -138,6 +154,9 @@ void vag_ctx_destroy(vag_ctx *ctx) {
 vag_status vag_ctx_set_stream(vag_ctx *ctx, void *stream) {
   if (!ctx) return VAG_EINVAL;
   return guarded(&ctx->c, [&] {
+    // work (and pool allocations) ordered on the old stream must be complete
+    // before the new stream uses or frees them
+    VAG_CUDA(cudaStreamSynchronize(ctx->c.stream));
     if (stream == nullptr) {
       ctx->c.stream = ctx->c.own_stream;
       return;
@@ -384,10 +403,10 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     if (opts->precision != VAG_FP64 && opts->precision != VAG_MIXED) fail(VAG_EINVAL, "unknown precision");
     if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_AMG)
       fail(VAG_EINVAL, "preconditioner not available in this build");
-    if (opts->precision == VAG_MIXED && opts->precond != VAG_PC_JACOBI)
-      fail(VAG_EINVAL, "the mixed-precision path takes the Jacobi preconditioner in this build");
     use_device(s->ctx);
-    if (opts->precision == VAG_MIXED) mixed_solve(s, opts, inf);
+    // VAG_MIXED: Jacobi -> FP64 refinement around FP32 CG; AMG -> FP64 CG
+    // preconditioned by an FP32 copy of the AMG hierarchy
+    if (opts->precision == VAG_MIXED && opts->precond == VAG_PC_JACOBI) mixed_solve(s, opts, inf);
     else pcg_solve(s, opts, inf);
     copy_out(s, u_out, s->u, (size_t)s->n_cv, opts->mem);
     VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));

@@ -13,18 +13,29 @@ void note_launches(unsigned long long n) {
 }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+void *ctx_alloc(Ctx *c, size_t bytes) {
+  void *p = nullptr;
+  cudaError_t e = c->pool ? cudaMallocFromPoolAsync(&p, bytes, c->pool, c->stream) : cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(VAG_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  return p;
+}
+
+void ctx_free(Ctx *c, void *p) {
+  if (!p) return;
+  if (c->pool) cudaFreeAsync(p, c->stream);
+  else cudaFree(p);
+}
+
 void *sys_alloc_bytes(System *s, size_t bytes) {
   Ctx *c = s->ctx;
   bytes = (bytes + 255) & ~size_t(255);
   if (c->budget && c->in_use + bytes > c->budget)
     fail(VAG_EBUDGET, "device memory budget exceeded (" + std::to_string(c->in_use + bytes) +
                           " > " + std::to_string(c->budget) + " bytes)");
-  void *p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    fail(VAG_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
-  }
+  void *p = ctx_alloc(c, bytes);
   s->allocs.push_back({p, bytes});
   s->bytes += bytes;
   c->in_use += bytes;
@@ -32,7 +43,7 @@ void *sys_alloc_bytes(System *s, size_t bytes) {
 }
 
 void sys_free_all(System *s) {
-  for (auto &a : s->allocs) cudaFree(a.ptr);
+  for (auto &a : s->allocs) ctx_free(s->ctx, a.ptr);
   if (s->ctx) s->ctx->in_use -= s->bytes;
   s->allocs.clear();
   s->bytes = 0;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -60,6 +61,7 @@ struct Ctx {
   struct ::vag_ctx *owner = nullptr;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;   // stream-ordered pool for every device buffer of the context's systems
   std::string last_error;
 };
 
@@ -86,17 +88,32 @@ struct AmgLevel {
   std::vector<int> sys_start;      // host, n_sys+1: first row of each system
   int *d_sys_start = nullptr;
   int *agg = nullptr;              // [n] aggregate (row of the next level) or -1
+  // systems that end their hierarchy at this level (at most kDenseMax rows)
+  // are solved densely here: per-row skip mask and dense inverses
+  uint8_t *skip = nullptr;         // [n] row belongs to a terminal system
+  bool any_term = false, all_term = false;
+  double *inv = nullptr;           // dense inverses of the terminal blocks
+  long long *inv_off = nullptr;    // [n_sys+1] offsets (0-sized for other systems)
+  long long n_inv = 0;             // entries of inv
   int nc = 0;
   int *mptr = nullptr, *mem = nullptr;   // members of each aggregate, sorted
   double *x = nullptr, *b = nullptr, *t = nullptr;   // V-cycle work vectors
+  // sliced-ELL copy of the level (coarse levels; level 0 uses the system's)
+  int *slice_ptr = nullptr, *scol = nullptr;
+  double *sval = nullptr;
+  float *sval32 = nullptr;
+  int64_t sell_nnz = 0;
+  // FP32 copy (mixed-precision path)
+  float *val32 = nullptr, *dinv32 = nullptr, *inv32 = nullptr;
+  float *x32 = nullptr, *b32 = nullptr, *t32 = nullptr;
 };
 struct Amg {
   std::vector<AmgLevel> levels;
   std::vector<void *> allocs;
   size_t bytes = 0;
-  double *inv = nullptr;           // dense inverses of the coarsest blocks
-  long long *inv_off = nullptr;
   bool built = false;
+  bool f32 = false;                // V-cycle in FP32
+  float *sval32 = nullptr;         // FP32 sliced-ELL values of A (finest level)
 };
 
 // State of the mixed-precision solve (FP32 inner CG inside FP64 refinement).
@@ -217,6 +234,8 @@ struct System {
   int64_t t_cap = 0;
   double *cbuf = nullptr;      // [2 n_cv]
   double *dts = nullptr;       // [2 n_sys]: per system dt_max, dt
+  cudaGraphExec_t step_graph = nullptr;   // kStepChunk transport steps
+  int64_t step_graph_cap = -1;
   std::vector<double> dts_host;
 
   // timing events
@@ -225,6 +244,9 @@ struct System {
 
 // allocation helpers (budget-checked)
 void *sys_alloc_bytes(System *s, size_t bytes);
+// device allocation from the context's pool (stream-ordered on its stream)
+void *ctx_alloc(Ctx *c, size_t bytes);
+void ctx_free(Ctx *c, void *p);
 template <class T>
 T *sys_alloc(System *s, size_t n) {
   return static_cast<T *>(sys_alloc_bytes(s, (n ? n : 1) * sizeof(T)));
@@ -250,7 +272,7 @@ unsigned long long launches_so_far();
 void symbolic_phase(System *s);
 void numeric_phase(System *s);
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
-void amg_setup(System *s);
+void amg_setup(System *s, bool f32);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
 void amg_free(System *s);
 void mixed_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
@@ -263,6 +285,12 @@ void build_tiles(System *s);
 void build_sell(System *s);
 void sell_values(System *s);
 void sell_values_scaled_f32(System *s, const double *scale, float *out);
+void sell_values_f32(System *s, float *out);
+int64_t sell_structure(cudaStream_t st, int n, const int *rowptr, const int *col, int **slice_ptr_out,
+                       int **scol_out, const std::function<void *(size_t)> &alloc);
+template <class T>
+void sell_fill(cudaStream_t st, int n, const int *rowptr, const int *col, const double *val, const int *slice_ptr,
+               T *sval);
 void solve_infos(const System *s, vag_solve_info *infos);
 void recover_cells_and_fluxes(System *s);
 void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_transport_info *info,

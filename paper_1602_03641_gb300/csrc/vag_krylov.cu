@@ -433,7 +433,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   if (amg) {
     if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
-    amg_setup(s);
+    amg_setup(s, o->precision == VAG_MIXED);
     VAG_CUDA(cudaEventRecord(s->ev1, st));
     VAG_CUDA(cudaEventSynchronize(s->ev1));
     cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);

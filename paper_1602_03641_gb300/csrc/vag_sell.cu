@@ -5,6 +5,8 @@
 // (no cross-lane reduction -- on GB300 the FP64 pipe, not HBM, limits a
 // lane-split CSR SpMV).  Entries of a row keep their CSR order, so a row sum
 // is the same sequence of FMAs whatever the slice layout.
+#include <functional>
+
 #include "vag_internal.cuh"
 
 namespace vag {
@@ -59,6 +61,43 @@ __global__ void k_sell_vals(int n, const int *__restrict__ rowptr, const double 
 
 }  // namespace
 
+// Sliced-ELL structure of any CSR matrix (n rows): slice_ptr [n_slices+1]
+// and scol [total]; returns total.  The caller supplies the allocator.
+int64_t sell_structure(cudaStream_t st, int n, const int *rowptr, const int *col, int **slice_ptr_out,
+                       int **scol_out, const std::function<void *(size_t)> &alloc) {
+  const int n_slices = (n + 31) / 32;
+  int *slice_ptr = static_cast<int *>(alloc(sizeof(int) * ((size_t)n_slices + 1)));
+  int *width;
+  VAG_CUDA(cudaMallocAsync(&width, sizeof(int) * ((size_t)n_slices + 1), st));
+  k_slice_width<<<grid_for(n_slices, TB), TB, 0, st>>>(n, n_slices, rowptr, width);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
+  const int64_t total = n_slices ? scan_exclusive(width, slice_ptr, n_slices, st) : 0;
+  if (!n_slices) VAG_CUDA(cudaMemsetAsync(slice_ptr, 0, sizeof(int), st));
+  VAG_CUDA(cudaFreeAsync(width, st));
+  int *scol = static_cast<int *>(alloc(sizeof(int) * (size_t)std::max<int64_t>(total, 1)));
+  if (n > 0) {
+    k_sell_cols<<<grid_for(n, TB), TB, 0, st>>>(n, rowptr, col, slice_ptr, scol);
+    k_sell_pad<<<grid_for((int64_t)n_slices * 32, TB), TB, 0, st>>>(n, rowptr, slice_ptr, scol);
+    note_launches(2);
+    VAG_CHECK_LAUNCH();
+  }
+  *slice_ptr_out = slice_ptr;
+  *scol_out = scol;
+  return total;
+}
+
+template <class T>
+void sell_fill(cudaStream_t st, int n, const int *rowptr, const int *col, const double *val, const int *slice_ptr,
+               T *sval) {
+  if (n <= 0) return;
+  k_sell_vals<T><<<grid_for(n, TB), TB, 0, st>>>(n, rowptr, val, nullptr, col, slice_ptr, sval);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
+}
+template void sell_fill<double>(cudaStream_t, int, const int *, const int *, const double *, const int *, double *);
+template void sell_fill<float>(cudaStream_t, int, const int *, const int *, const double *, const int *, float *);
+
 void build_sell(System *s) {
   cudaStream_t st = s->ctx->stream;
   const int n = s->n_rows;
@@ -96,5 +135,7 @@ void sell_values_scaled_f32(System *s, const double *scale, float *out) {
   note_launches(1);
   VAG_CHECK_LAUNCH();
 }
+
+void sell_values_f32(System *s, float *out) { sell_values_scaled_f32(s, nullptr, out); }
 
 }  // namespace vag

@@ -362,7 +362,34 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
   VAG_CHECK_LAUNCH();
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   const int gs = grid_for(n, TB);
-  for (int k = 0; k < o->n_steps; ++k) {
+  // steps in CUDA graphs of kStepChunk launches (an even count: the chunk
+  // starts and ends in the same buffer), the remainder launched directly
+  constexpr int kStepChunk = 20;
+  const int chunks = o->n_steps / kStepChunk;
+  if (chunks > 0) {
+    if (!s->step_graph || s->step_graph_cap != s->t_cap) {
+      if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
+      s->step_graph = nullptr;
+      cudaGraph_t graph;
+      VAG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      set_capturing(true);
+      double *a = s->cbuf, *b = s->cbuf + n;
+      for (int k = 0; k < kStepChunk; ++k) {
+        k_step<<<gs, TB, 0, st>>>(n, s->trowptr, s->tcol, s->tval, s->tdiag, a, b);
+        std::swap(a, b);
+      }
+      set_capturing(false);
+      VAG_CUDA(cudaStreamEndCapture(st, &graph));
+      VAG_CUDA(cudaGraphInstantiate(&s->step_graph, graph, 0));
+      cudaGraphDestroy(graph);
+      s->step_graph_cap = s->t_cap;
+    }
+    for (int c = 0; c < chunks; ++c) {
+      VAG_CUDA(cudaGraphLaunch(s->step_graph, st));
+      note_launches(kStepChunk);
+    }
+  }
+  for (int k = chunks * kStepChunk; k < o->n_steps; ++k) {
     k_step<<<gs, TB, 0, st>>>(n, s->trowptr, s->tcol, s->tval, s->tdiag, c0, c1);
     note_launches(1);
     std::swap(c0, c1);

@@ -66,6 +66,30 @@ class vag_transport_info(C.Structure):
     _fields_ = [("dt_max", C.c_double), ("dt", C.c_double), ("steps", C.c_int32), ("ms", C.c_double)]
 
 
+class vag_server_opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("mem_budget_bytes", C.c_size_t), ("slots", C.c_int32),
+                ("max_batch", C.c_int32)]
+
+
+class vag_request(C.Structure):
+    _fields_ = [("mesh", vag_mesh), ("props", vag_props), ("bc", vag_dirichlet),
+                ("phi_m", C.c_void_p), ("phi_f", C.c_void_p), ("cbar", C.c_void_p), ("c0", C.c_void_p),
+                ("omega", C.c_double), ("cfl", C.c_double), ("n_steps", C.c_int32),
+                ("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int32),
+                ("u_out", C.c_void_p), ("c_out", C.c_void_p)]
+
+
+class vag_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("solve", vag_solve_info), ("transport", vag_transport_info),
+                ("latency_ms", C.c_double), ("queue_ms", C.c_double), ("batch_size", C.c_int32)]
+
+
+class vag_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("in_queue", C.c_uint64), ("in_flight", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("solves_per_s", C.c_double), ("bytes_reserved", C.c_size_t), ("peak_bytes", C.c_size_t)]
+
+
 P = C.c_void_p
 _SIGS = {
     "vag_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(P)]),
@@ -82,6 +106,13 @@ _SIGS = {
     "vag_system_get_batch": (C.c_int, [P, C.POINTER(C.c_int32), P, P, P, P]),
     "vag_solve_get_infos": (C.c_int, [P, C.POINTER(vag_solve_info)]),
     "vag_transport_get_dts": (C.c_int, [P, P, P]),
+    "vag_spmv_dot_noalloc": (C.c_int, [C.c_int32, P, P, P, P, P, P, P]),
+    "vag_server_create": (C.c_int, [C.POINTER(vag_server_opts), C.POINTER(P)]),
+    "vag_server_submit": (C.c_int, [P, C.POINTER(vag_request), C.POINTER(C.c_uint64)]),
+    "vag_server_wait": (C.c_int, [P, C.c_uint64, C.c_int32, C.POINTER(vag_result)]),
+    "vag_server_get_stats": (C.c_int, [P, C.POINTER(vag_server_stats)]),
+    "vag_server_last_error": (C.c_char_p, [P]),
+    "vag_server_destroy": (None, [P]),
     "vag_system_destroy": (None, [P]),
     "vag_system_get_info": (C.c_int, [P, C.POINTER(vag_system_info)]),
     "vag_solve": (C.c_int, [P, C.POINTER(vag_solve_opts), P, C.POINTER(vag_solve_info)]),
@@ -91,7 +122,6 @@ _SIGS = {
     "vag_export_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
     "vag_set_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
     "vag_export_porous_volumes": (C.c_int, [P, P, C.c_int]),
-    "vag_spmv_dot_noalloc": (C.c_int, [C.c_int32, P, P, P, P, P, P, P]),
 }
 
 _LIB = None
@@ -382,3 +412,64 @@ def assemble_problem(ctx: Context, pb, device=False):
         dv = torch.from_numpy(dv).cuda()
     xyz, cn, ffn, lam, lamf, df = arrs
     return ctx.assemble(xyz, cn, ffn, lam, lamf, df, pb.mu, dn, dv)
+
+
+class Server:
+    """Continuous-batching request server (vag_server_*).  Requests are
+    ``vag_inputs.Problem``-like objects; inputs are copied at submit, outputs
+    land in numpy arrays owned by this object until the ticket is waited."""
+
+    def __init__(self, device=0, budget_bytes=0, slots=2, max_batch=64):
+        self._L = lib()
+        h = P()
+        st = self._L.vag_server_create(C.byref(vag_server_opts(device, budget_bytes, slots, max_batch)), C.byref(h))
+        if st != VAG_OK:
+            raise VagError(st, "vag_server_create failed")
+        self.h = h
+        self._out = {}
+
+    def submit(self, pb, n_steps=0, precision=VAG_FP64, precond=VAG_PC_JACOBI, rtol=1e-8, maxit=20000,
+               cfl=0.9, omega=0.5):
+        a = problem_arrays(pb)
+        n_cv = pb.n_nodes + pb.n_ff + pb.n_cells
+        u = np.empty(n_cv)
+        c = np.empty(n_cv)
+        keep = [a, np.ascontiguousarray(pb.phi_m, np.float64), np.ascontiguousarray(pb.phi_f, np.float64),
+                np.ascontiguousarray(pb.cbar, np.float64)]
+        m = vag_mesh(pb.n_nodes, _ptr(a["xyz"]), pb.n_cells, _ptr(a["cell_nodes"]), pb.n_ff, _ptr(a["ff_nodes"]))
+        pr = vag_props(_ptr(a["lambda_m"]), _ptr(a["lambda_f"]), _ptr(a["d_f"]), float(pb.mu))
+        bc = vag_dirichlet(len(a["dir_nodes"]), _ptr(a["dir_nodes"]), _ptr(a["dir_values"]))
+        q = vag_request(m, pr, bc, _ptr(keep[1]), _ptr(keep[2]), _ptr(keep[3]), None, float(omega), float(cfl),
+                        int(n_steps), precision, precond, float(rtol), int(maxit), _ptr(u), _ptr(c))
+        t = C.c_uint64()
+        st = self._L.vag_server_submit(self.h, C.byref(q), C.byref(t))
+        if st != VAG_OK:
+            raise VagError(st, self._L.vag_server_last_error(self.h).decode())
+        self._out[t.value] = (u, c)
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        r = vag_result()
+        st = self._L.vag_server_wait(self.h, ticket, int(timeout_ms), C.byref(r))
+        if st != VAG_OK:
+            raise VagError(st, "wait")
+        u, c = self._out.pop(ticket)
+        return u, c, r
+
+    def stats(self):
+        s = vag_server_stats()
+        self._L.vag_server_get_stats(self.h, C.byref(s))
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.vag_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if _sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -46,7 +46,8 @@ def test_library_exports_every_declared_symbol(vag):
 
 
 STRUCTS = ["vag_mesh", "vag_props", "vag_dirichlet", "vag_system_info", "vag_solve_opts", "vag_solve_info",
-           "vag_transport_opts", "vag_transport_info"]
+           "vag_transport_opts", "vag_transport_info", "vag_server_opts", "vag_request", "vag_result",
+           "vag_server_stats"]
 
 
 def test_ctypes_layout_matches_c(vag):
