@@ -32,6 +32,7 @@ constexpr double kOmega = 2.0 / 3.0;
 constexpr int kDenseMax = 48;       // two 48x48 FP64 blocks fit the static shared limit
 constexpr int kMaxLevels = 16;
 constexpr int kCoarseWidth = 160;   // unique columns of one coarse row (< 256)
+constexpr int kTailRows = 1024;     // FP32 levels at most this big per system run in one kernel
 
 constexpr unsigned long long KEY_IN = ~0ull;
 constexpr unsigned long long KEY_OUT = 0ull;
@@ -50,9 +51,16 @@ __device__ __forceinline__ int sys_of_row(int i, const int *__restrict__ start, 
   return lo;
 }
 
-// strength mask per CSR entry, isolated flag per row, diagonal inverse
+// sqrt of each diagonal entry, FP32 (the strength test is a heuristic: FP32
+// decides it, deterministically)
+__global__ void k_sqrt_diag(int n, const double *__restrict__ dinv, float *__restrict__ sd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) sd[i] = (float)sqrt(1.0 / dinv[i]);
+}
+
+// strength mask per CSR entry and isolated flag per row
 __global__ void k_strength(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                           const double *__restrict__ val, const double *__restrict__ dinv,
+                           const double *__restrict__ val, const float *__restrict__ sd,
                            const uint8_t *__restrict__ skip, uint8_t *strong, int8_t *state) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -61,14 +69,13 @@ __global__ void k_strength(int n, const int *__restrict__ rowptr, const int *__r
     state[i] = -2;
     return;
   }
-  const double di = 1.0 / dinv[i];
+  const float ti = (float)kTheta * sd[i];
   int cnt = 0;
   for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
     const int j = col[k];
-    const double dj = 1.0 / dinv[j];
-    const bool s = (j != i) && fabs(val[k]) >= kTheta * sqrt(fabs(di * dj));
-    strong[k] = s;
-    cnt += s;
+    const bool st = (j != i) && fabsf((float)val[k]) >= ti * sd[j];
+    strong[k] = st;
+    cnt += st;
   }
   state[i] = cnt ? 0 : -2;   // 0 undecided, 1 root, -1 out, -2 isolated
 }
@@ -146,19 +153,19 @@ __global__ void k_agg_pass1(int n, const int *__restrict__ rowptr, const int *__
 
 // pass 2: remaining nodes join their strongest aggregated neighbour
 __global__ void k_agg_pass2(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                            const double *__restrict__ val, const double *__restrict__ dinv,
+                            const double *__restrict__ val, const float *__restrict__ sd,
                             const uint8_t *__restrict__ strong, const int8_t *__restrict__ state,
                             const int *__restrict__ agg1, int *agg) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int a = agg1[i];
   if (a < 0 && state[i] != -2) {
-    double best = -1.0;
+    float best = -1.f;
     for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
       if (!strong[k]) continue;
       const int j = col[k];
       if (agg1[j] < 0) continue;
-      const double w = fabs(val[k]) * sqrt(dinv[j]);
+      const float w = fabsf((float)val[k]) / sd[j];
       if (w > best) { best = w; a = agg1[j]; }
     }
   }
@@ -306,9 +313,45 @@ __global__ void k_dense_inverse(const int *__restrict__ sys_start, const int *__
 // copy of the hierarchy, for the mixed-precision path).
 
 template <class T>
+__device__ __forceinline__ T row_sell(int i, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
+                                      const int *__restrict__ scol, const T *__restrict__ sval,
+                                      const T *__restrict__ x) {
+  const int len = rowptr[i + 1] - rowptr[i];
+  const int base = slice_ptr[i >> 5] + (i & 31);
+  T s = 0;
+#pragma unroll 4
+  for (int k = 0; k < len; ++k) {
+    const int idx = base + 32 * k;
+    s = fma(sval[idx], x[scol[idx]], s);
+  }
+  return s;
+}
+
+// Row product of a coarse level: 8 lanes per CSR row, lane l takes entries
+// l, l+8, ... and the partial sums meet in a fixed shuffle tree.  All 32 lanes
+// of the warp must call it together (rows past the end pass valid = false).
+template <class T>
+__device__ __forceinline__ T row_csr8(int i, bool valid, int lane, const int *__restrict__ rowptr,
+                                      const int *__restrict__ col, const T *__restrict__ val,
+                                      const T *__restrict__ x) {
+  T s = 0;
+  if (valid)
+    for (int k = rowptr[i] + lane; k < rowptr[i + 1]; k += 8) s = fma(val[k], x[col[k]], s);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  return s;
+}
+
+template <class T>
+__device__ __forceinline__ T jac_first_row(T b, T dinv) { return (T)kOmega * dinv * b; }
+template <class T>
+__device__ __forceinline__ T jac_row(T xin, T dinv, T b, T ax) { return fma((T)kOmega * dinv, b - ax, xin); }
+
+template <class T>
 __global__ void k_jac_first(int n, const T *__restrict__ b, const T *__restrict__ dinv, T *x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = (T)kOmega * dinv[i] * b[i];
+  if (i < n) x[i] = jac_first_row(b[i], dinv[i]);
 }
 
 // x_out = x_in + omega D^-1 (b - A x_in), CSR, one thread per row
@@ -320,10 +363,34 @@ __global__ void k_jac_csr(int n, const int *__restrict__ rowptr, const int *__re
   if (i >= n || skip[i]) return;
   T s = 0;
   for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(val[k], xin[col[k]], s);
-  xout[i] = fma((T)kOmega * dinv[i], b[i] - s, xin[i]);
+  xout[i] = jac_row(xin[i], dinv[i], b[i], s);
 }
 
-// same sweep in the sliced-ELL layout (finest level)
+// coarse-level sweep and residual, 8 lanes per row (32 rows per block)
+template <class T>
+__global__ void __launch_bounds__(256) k_jac_csr8(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                                  const T *__restrict__ val, const T *__restrict__ dinv,
+                                                  const T *__restrict__ b, const T *__restrict__ xin,
+                                                  T *__restrict__ xout, const uint8_t *__restrict__ skip) {
+  const int lane = threadIdx.x & 7;
+  const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const bool valid = i < n;
+  const T s = row_csr8(i, valid, lane, rowptr, col, val, xin);
+  if (valid && lane == 0 && !skip[i]) xout[i] = jac_row(xin[i], dinv[i], b[i], s);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_resid_csr8(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                                    const T *__restrict__ val, const T *__restrict__ b,
+                                                    const T *__restrict__ x, T *__restrict__ r) {
+  const int lane = threadIdx.x & 7;
+  const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const bool valid = i < n;
+  const T s = row_csr8(i, valid, lane, rowptr, col, val, x);
+  if (valid && lane == 0) r[i] = b[i] - s;
+}
+
+// same sweep in the sliced-ELL layout
 template <class T>
 __global__ void k_jac_sell(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                            const int *__restrict__ scol, const T *__restrict__ sval, const T *__restrict__ dinv,
@@ -331,18 +398,9 @@ __global__ void k_jac_sell(int n, const int *__restrict__ rowptr, const int *__r
                            const uint8_t *__restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || skip[i]) return;
-  const int len = rowptr[i + 1] - rowptr[i];
-  const int base = slice_ptr[i >> 5] + (i & 31);
-  T s = 0;
-#pragma unroll 4
-  for (int k = 0; k < len; ++k) {
-    const int idx = base + 32 * k;
-    s = fma(sval[idx], __ldg(&xin[scol[idx]]), s);
-  }
-  xout[i] = fma((T)kOmega * dinv[i], b[i] - s, xin[i]);
+  xout[i] = jac_row(xin[i], dinv[i], b[i], row_sell(i, rowptr, slice_ptr, scol, sval, xin));
 }
 
-// r = b - A x, one thread per row (CSR / sliced ELL)
 template <class T>
 __global__ void k_resid_csr(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
                             const T *__restrict__ val, const T *__restrict__ b, const T *__restrict__ x,
@@ -360,26 +418,24 @@ __global__ void k_resid_sell(int n, const int *__restrict__ rowptr, const int *_
                              const T *__restrict__ x, T *__restrict__ r) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int len = rowptr[i + 1] - rowptr[i];
-  const int base = slice_ptr[i >> 5] + (i & 31);
-  T s = 0;
-#pragma unroll 4
-  for (int k = 0; k < len; ++k) {
-    const int idx = base + 32 * k;
-    s = fma(sval[idx], __ldg(&x[scol[idx]]), s);
-  }
-  r[i] = b[i] - s;
+  r[i] = b[i] - row_sell(i, rowptr, slice_ptr, scol, sval, x);
 }
 
 // b_c[I] = sum of r over the members of aggregate I (row order)
+template <class T>
+__device__ __forceinline__ T restrict_row(int I, const int *__restrict__ mptr, const int *__restrict__ mem,
+                                          const T *__restrict__ r) {
+  T acc = 0;
+  for (int p = mptr[I]; p < mptr[I + 1]; ++p) acc += r[mem[p]];
+  return acc;
+}
+
 template <class T>
 __global__ void k_restrict(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
                            const T *__restrict__ r, T *__restrict__ bc) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nc) return;
-  T acc = 0;
-  for (int p = mptr[I]; p < mptr[I + 1]; ++p) acc += r[mem[p]];
-  bc[I] = acc;
+  bc[I] = restrict_row(I, mptr, mem, r);
 }
 
 template <class T>
@@ -390,16 +446,88 @@ __global__ void k_prolong(int n, const int *__restrict__ agg, const T *__restric
 
 // x = inv_g b per system block (one thread block per system)
 template <class T>
+__device__ __forceinline__ T dense_row(int i, int m, const T *__restrict__ M, const T *__restrict__ b) {
+  T s = 0;
+  for (int j = 0; j < m; ++j) s = fma(M[i * m + j], b[j], s);
+  return s;
+}
+
+template <class T>
 __global__ void k_dense_apply(const int *__restrict__ sys_start, const long long *__restrict__ off,
                               const T *__restrict__ inv, const T *__restrict__ b, T *x) {
   const int g = blockIdx.x;
   const int r0 = sys_start[g], m = sys_start[g + 1] - r0;
   if (m == 0 || off[g + 1] - off[g] != (long long)m * m) return;   // not terminal here
   const T *M = inv + off[g];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    T s = 0;
-    for (int j = 0; j < m; ++j) s = fma(M[i * m + j], b[r0 + j], s);
-    x[r0 + i] = s;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) x[r0 + i] = dense_row(i, m, M, b + r0);
+}
+
+// The lower part of the FP32 V-cycle (levels with at most kTailRows rows per
+// system) in one kernel: one thread block per system walks its levels down
+// and up with a barrier between phases.  Same row arithmetic as the grid
+// kernels, so the result is identical to launching them level by level.
+constexpr int kTailLevels = 10;
+struct TailLevel {
+  const int *sys_start, *rowptr, *col, *agg, *mptr, *mem;
+  const float *val, *dinv, *inv;
+  const long long *inv_off;
+  float *x, *b, *t;
+};
+struct TailDesc {
+  TailLevel lv[kTailLevels];
+  int nlev;
+};
+
+__global__ void __launch_bounds__(1024) k_vcycle_tail32(TailDesc d) {
+  const int g = blockIdx.x;
+  const int lane = threadIdx.x & 7, grp = threadIdx.x >> 3;   // 128 groups of 8 lanes
+  int last = d.nlev - 1;   // deepest level with a coarse correction below it
+  // one op per row over [r0, r0+m), 8 lanes per row, uniform loop bound
+  auto rows8 = [&](const TailLevel &L, int r0, int m, const float *x, auto &&emit) {
+    for (int base = 0; base < m; base += 128) {
+      const int i = r0 + base + grp;
+      const bool valid = base + grp < m;
+      const float s = row_csr8(i, valid, lane, L.rowptr, L.col, L.val, x);
+      if (valid && lane == 0) emit(i, s);
+    }
+  };
+  for (int l = 0; l < d.nlev; ++l) {
+    const TailLevel &L = d.lv[l];
+    const int r0 = L.sys_start[g], m = L.sys_start[g + 1] - r0;
+    if (m == 0) { last = l - 1; break; }
+    if (L.inv_off && L.inv_off[g + 1] - L.inv_off[g] == (long long)m * m) {   // terminal here
+      const float *M = L.inv + L.inv_off[g];
+      for (int i = threadIdx.x; i < m; i += blockDim.x) L.x[r0 + i] = dense_row(i, m, M, L.b + r0);
+      __syncthreads();
+      last = l - 1;
+      break;
+    }
+    for (int i = r0 + threadIdx.x; i < r0 + m; i += blockDim.x) L.t[i] = jac_first_row(L.b[i], L.dinv[i]);
+    __syncthreads();
+    rows8(L, r0, m, L.t, [&](int i, float s) { L.x[i] = jac_row(L.t[i], L.dinv[i], L.b[i], s); });
+    __syncthreads();
+    rows8(L, r0, m, L.x, [&](int i, float s) { L.t[i] = L.b[i] - s; });
+    __syncthreads();
+    if (l + 1 < d.nlev) {
+      const TailLevel &C = d.lv[l + 1];
+      for (int I = C.sys_start[g] + threadIdx.x; I < C.sys_start[g + 1]; I += blockDim.x)
+        C.b[I] = restrict_row(I, L.mptr, L.mem, L.t);
+    }
+    __syncthreads();
+  }
+  for (int l = last; l >= 0; --l) {
+    const TailLevel &L = d.lv[l];
+    const int r0 = L.sys_start[g], m = L.sys_start[g + 1] - r0;
+    if (l + 1 < d.nlev) {
+      const float *xc = d.lv[l + 1].x;
+      for (int i = r0 + threadIdx.x; i < r0 + m; i += blockDim.x)
+        if (L.agg[i] >= 0) L.x[i] += xc[L.agg[i]];
+    }
+    __syncthreads();
+    rows8(L, r0, m, L.x, [&](int i, float s) { L.t[i] = jac_row(L.x[i], L.dinv[i], L.b[i], s); });
+    __syncthreads();
+    rows8(L, r0, m, L.t, [&](int i, float s) { L.x[i] = jac_row(L.t[i], L.dinv[i], L.b[i], s); });
+    __syncthreads();
   }
 }
 
@@ -502,15 +630,21 @@ void amg_setup(System *s, bool f32) {
     int8_t *state = static_cast<int8_t *>(alloc(n));
     int8_t *next = static_cast<int8_t *>(alloc(n));
     unsigned long long *m1 = static_cast<unsigned long long *>(alloc(8 * (size_t)n));
-    k_strength<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, L.val, L.dinv, L.skip, strong, state);
-    note_launches(1);
-    for (int it = 0; it < 64; ++it) {
-      VAG_CUDA(cudaMemsetAsync(undecided, 0, sizeof(int), st));
-      k_mis_max1<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, L.d_sys_start, ns, m1);
-      k_mis_max2_decide<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, m1, L.d_sys_start, ns,
-                                                         next, undecided);
-      note_launches(2);
-      VAG_CUDA(cudaMemcpyAsync(state, next, n, cudaMemcpyDeviceToDevice, st));
+    float *sd = static_cast<float *>(alloc(4 * (size_t)std::max(n, 1)));
+    k_sqrt_diag<<<grid_for(n, TB), TB, 0, st>>>(n, L.dinv, sd);
+    k_strength<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, L.val, sd, L.skip, strong, state);
+    note_launches(2);
+    // MIS(2) rounds, three between polls (a round after the last decision
+    // changes nothing)
+    for (int it = 0; it < 64; it += 3) {
+      for (int r = 0; r < 3; ++r) {
+        VAG_CUDA(cudaMemsetAsync(undecided, 0, sizeof(int), st));
+        k_mis_max1<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, L.d_sys_start, ns, m1);
+        k_mis_max2_decide<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, m1, L.d_sys_start,
+                                                           ns, next, undecided);
+        note_launches(2);
+        VAG_CUDA(cudaMemcpyAsync(state, next, n, cudaMemcpyDeviceToDevice, st));
+      }
       VAG_CUDA(cudaMemcpyAsync(und_host, undecided, sizeof(int), cudaMemcpyDeviceToHost, st));
       VAG_CUDA(cudaStreamSynchronize(st));
       if (*und_host == 0) break;
@@ -524,7 +658,7 @@ void amg_setup(System *s, bool f32) {
     int *agg1 = static_cast<int *>(alloc(4 * (size_t)n));
     L.agg = static_cast<int *>(alloc(4 * (size_t)n));
     k_agg_pass1<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, rscan, agg1);
-    k_agg_pass2<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, L.val, L.dinv, strong, state, agg1, L.agg);
+    k_agg_pass2<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, L.val, sd, strong, state, agg1, L.agg);
     note_launches(2);
     // members of every aggregate, sorted by row
     L.nc = nc;
@@ -599,14 +733,26 @@ void amg_setup(System *s, bool f32) {
       if (l == 0) {
         L.sval32 = A.sval32;
       } else {
-        L.sval32 = static_cast<float *>(alloc(4 * (size_t)std::max<int64_t>(L.sell_nnz, 1)));
-        sell_fill<float>(st, L.n, L.rowptr, L.col, L.val, L.slice_ptr, L.sval32);
+        L.val32 = cast(L.val, L.nnz);
       }
       L.dinv32 = cast(L.dinv, L.n);
       L.inv32 = L.any_term ? cast(L.inv, L.n_inv) : nullptr;
       L.x32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
       L.b32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
       L.t32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
+    }
+  }
+  // first level where every system has at most kTailRows rows: from there
+  // the FP32 V-cycle runs in one kernel
+  A.tail_start = -1;
+  if (f32) {
+    for (size_t l = 1; l < A.levels.size(); ++l) {
+      int mx = 0;
+      for (int g = 0; g < ns; ++g) mx = std::max(mx, A.levels[l].sys_start[g + 1] - A.levels[l].sys_start[g]);
+      if (mx <= kTailRows && (int)(A.levels.size() - l) <= kTailLevels) {
+        A.tail_start = (int)l;
+        break;
+      }
     }
   }
   VAG_CHECK_LAUNCH();
@@ -628,15 +774,33 @@ LV<double> lv<double>(System *, AmgLevel &L) {
 template <>
 LV<float> lv<float>(System *, AmgLevel &L) {
   return {L.val32, L.dinv32, L.inv32, L.sval32, L.x32, L.b32, L.t32};
-}
+}   // val32 on coarse levels, sval32 on level 0
 
 // x = V(b): one V(2,2) cycle from a zero initial guess.  Systems that end at
 // this level are solved exactly; the others are smoothed, restricted,
 // corrected from the next level and smoothed again.
+static void tail32(System *s, int lvl, cudaStream_t st) {
+  Amg &A = s->amg;
+  TailDesc d{};
+  d.nlev = (int)A.levels.size() - lvl;
+  if (d.nlev > kTailLevels) fail(VAG_ECUDA, "AMG: too many levels below the tail start");
+  for (int k = 0; k < d.nlev; ++k) {
+    AmgLevel &L = A.levels[lvl + k];
+    d.lv[k] = TailLevel{L.d_sys_start, L.rowptr, L.col, L.agg, L.mptr, L.mem, L.val32, L.dinv32,
+                        L.inv32, L.any_term ? L.inv_off : nullptr, L.x32, L.b32, L.t32};
+  }
+  k_vcycle_tail32<<<s->seg.n_sys, 1024, 0, st>>>(d);
+  note_launches(1);
+}
+
 template <class T>
 static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
   Amg &A = s->amg;
   AmgLevel &L = A.levels[lvl];
+  if (sizeof(T) == 4 && lvl > 0 && lvl == A.tail_start) {   // b, x are this level's b32, x32
+    tail32(s, lvl, st);
+    return;
+  }
   const LV<T> v = lv<T>(s, L);
   const int n = L.n;
   const int g = grid_for(n, TB);
@@ -647,18 +811,29 @@ static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
   if (L.all_term) return;
   AmgLevel &C = A.levels[lvl + 1];
   const LV<T> c = lv<T>(s, C);
+  // level 0: sliced ELL, one thread per row; coarser levels: CSR, 8 lanes per row
+  const int g8 = grid_for(n, 32);
+  auto sweep = [&](const T *xin, T *xout) {
+    if (lvl == 0)
+      k_jac_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, v.dinv, b, xin, xout, L.skip);
+    else
+      k_jac_csr8<T><<<g8, 256, 0, st>>>(n, L.rowptr, L.col, v.val, v.dinv, b, xin, xout, L.skip);
+  };
   // pre-smoothing: two damped Jacobi sweeps from x = 0
   k_jac_first<T><<<g, TB, 0, st>>>(n, b, v.dinv, v.t);
-  k_jac_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, v.dinv, b, v.t, x, L.skip);
+  sweep(v.t, x);
   // residual, restricted to the coarse level (t is free again)
-  k_resid_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, b, x, v.t);
+  if (lvl == 0)
+    k_resid_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, b, x, v.t);
+  else
+    k_resid_csr8<T><<<g8, 256, 0, st>>>(n, L.rowptr, L.col, v.val, b, x, v.t);
   k_restrict<T><<<grid_for(C.n, TB), TB, 0, st>>>(C.n, L.mptr, L.mem, v.t, c.b);
   note_launches(4);
   vcycle<T>(s, lvl + 1, c.b, c.x, st);
   k_prolong<T><<<g, TB, 0, st>>>(n, L.agg, c.x, x);
   // post-smoothing: two sweeps
-  k_jac_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, v.dinv, b, x, v.t, L.skip);
-  k_jac_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, v.dinv, b, v.t, x, L.skip);
+  sweep(x, v.t);
+  sweep(v.t, x);
   note_launches(3);
 }
 

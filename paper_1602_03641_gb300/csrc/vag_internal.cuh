@@ -113,6 +113,7 @@ struct Amg {
   size_t bytes = 0;
   bool built = false;
   bool f32 = false;                // V-cycle in FP32
+  int tail_start = -1;             // FP32: first level run by the one-kernel tail
   float *sval32 = nullptr;         // FP32 sliced-ELL values of A (finest level)
 };
 

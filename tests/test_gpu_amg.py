@@ -100,3 +100,26 @@ def test_fp32_hierarchy_preconditions_fp64_cg(ctx, name):
     assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-10
     _, i64 = s.solve(precond=pkg.VAG_PC_AMG, rtol=1e-12, maxit=2000, raise_on_error=False)
     assert info.iterations <= i64.iterations + 10
+
+
+def test_fp32_hierarchy_batch_equals_alone_bitwise(ctx):
+    """The FP32 V-cycle (grid kernels on the big levels, one-kernel tail on
+    the small ones) keeps a system's result independent of its batch."""
+    import paper_1602_03641_gb300 as pkg
+    pbs = [vi.random_dfn_problem(18, 9, 1e5, seed=11), vi.config_plain16(6), vi.random_dfn_problem(11, 4, 1e3, seed=12),
+           vi.build_problem((1, 1, 1), [])]
+    bs = ctx.assemble_batch([pkg.problem_arrays(p) for p in pbs])
+    lay = bs.batch_layout()
+    nv, nf = lay["node_start"][-1], lay["ff_start"][-1]
+    ub, _ = bs.solve(precision=pkg.VAG_MIXED, precond=pkg.VAG_PC_AMG, rtol=1e-10, maxit=2000, raise_on_error=False)
+    infos = bs.solve_infos()
+    ns, fs, cs = lay["node_start"], lay["ff_start"], lay["cell_start"]
+    for i, pb in enumerate(pbs):
+        s1 = pkg.assemble_problem(ctx, pb)
+        u1, inf1 = s1.solve(precision=pkg.VAG_MIXED, precond=pkg.VAG_PC_AMG, rtol=1e-10, maxit=2000,
+                            raise_on_error=False)
+        ui = np.concatenate([ub[ns[i]:ns[i + 1]], ub[nv + fs[i]:nv + fs[i + 1]], ub[nv + nf + cs[i]:nv + nf + cs[i + 1]]])
+        np.testing.assert_array_equal(ui, u1)
+        assert infos[i].iterations == inf1.iterations
+        assert inf1.rel_residual <= 1e-10
+        s1.close()
