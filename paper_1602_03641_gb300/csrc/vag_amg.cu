@@ -28,7 +28,15 @@ namespace {
 
 constexpr int TB = 256;
 constexpr double kTheta = 0.08;
-constexpr double kOmega = 2.0 / 3.0;
+// Smoother: l1-Jacobi, x += omega (b - A x) / sum_j |a_ij| (Baker, Falgout,
+// Kolev, Yang, "Multigrid smoothers for ultraparallel computing", SIAM J. Sci.
+// Comput. 33 (2011)).  diag(sum_j |a_ij|) - A is diagonally dominant, hence
+// A <= D_l1 and the sweep is A-norm convergent for any SPD A and omega < 2; on
+// zero-row-sum rows with non-positive couplings D_l1 = 2 a_ii, so omega = 4/3
+// equals damped Jacobi with 2/3 there.  Plain damped Jacobi diverges on VAG
+// rows where lambda_max(D^-1 A) > 3 (jittered, anisotropic cells), and the
+// V-cycle then stops being positive definite.
+constexpr double kOmega = 4.0 / 3.0;
 constexpr int kDenseMax = 48;       // two 48x48 FP64 blocks fit the static shared limit
 constexpr int kMaxLevels = 16;
 constexpr int kCoarseWidth = 160;   // unique columns of one coarse row (< 256)
@@ -49,6 +57,15 @@ __device__ __forceinline__ int sys_of_row(int i, const int *__restrict__ start, 
     if (start[mid] <= i) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+__global__ void k_l1_inv(int n, const int *__restrict__ rowptr, const double *__restrict__ val,
+                         double *__restrict__ sinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) a += fabs(val[k]);
+  sinv[i] = 1.0 / a;
 }
 
 // sqrt of each diagonal entry, FP32 (the strength test is a heuristic: FP32
@@ -344,39 +361,39 @@ __device__ __forceinline__ T row_csr8(int i, bool valid, int lane, const int *__
 }
 
 template <class T>
-__device__ __forceinline__ T jac_first_row(T b, T dinv) { return (T)kOmega * dinv * b; }
+__device__ __forceinline__ T jac_first_row(T b, T sinv) { return (T)kOmega * sinv * b; }
 template <class T>
-__device__ __forceinline__ T jac_row(T xin, T dinv, T b, T ax) { return fma((T)kOmega * dinv, b - ax, xin); }
+__device__ __forceinline__ T jac_row(T xin, T sinv, T b, T ax) { return fma((T)kOmega * sinv, b - ax, xin); }
 
 template <class T>
-__global__ void k_jac_first(int n, const T *__restrict__ b, const T *__restrict__ dinv, T *x) {
+__global__ void k_jac_first(int n, const T *__restrict__ b, const T *__restrict__ sinv, T *x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = jac_first_row(b[i], dinv[i]);
+  if (i < n) x[i] = jac_first_row(b[i], sinv[i]);
 }
 
 // x_out = x_in + omega D^-1 (b - A x_in), CSR, one thread per row
 template <class T>
 __global__ void k_jac_csr(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                          const T *__restrict__ val, const T *__restrict__ dinv, const T *__restrict__ b,
+                          const T *__restrict__ val, const T *__restrict__ sinv, const T *__restrict__ b,
                           const T *__restrict__ xin, T *__restrict__ xout, const uint8_t *__restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || skip[i]) return;
   T s = 0;
   for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(val[k], xin[col[k]], s);
-  xout[i] = jac_row(xin[i], dinv[i], b[i], s);
+  xout[i] = jac_row(xin[i], sinv[i], b[i], s);
 }
 
 // coarse-level sweep and residual, 8 lanes per row (32 rows per block)
 template <class T>
 __global__ void __launch_bounds__(256) k_jac_csr8(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                                                  const T *__restrict__ val, const T *__restrict__ dinv,
+                                                  const T *__restrict__ val, const T *__restrict__ sinv,
                                                   const T *__restrict__ b, const T *__restrict__ xin,
                                                   T *__restrict__ xout, const uint8_t *__restrict__ skip) {
   const int lane = threadIdx.x & 7;
   const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
   const bool valid = i < n;
   const T s = row_csr8(i, valid, lane, rowptr, col, val, xin);
-  if (valid && lane == 0 && !skip[i]) xout[i] = jac_row(xin[i], dinv[i], b[i], s);
+  if (valid && lane == 0 && !skip[i]) xout[i] = jac_row(xin[i], sinv[i], b[i], s);
 }
 
 template <class T>
@@ -393,12 +410,12 @@ __global__ void __launch_bounds__(256) k_resid_csr8(int n, const int *__restrict
 // same sweep in the sliced-ELL layout
 template <class T>
 __global__ void k_jac_sell(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
-                           const int *__restrict__ scol, const T *__restrict__ sval, const T *__restrict__ dinv,
+                           const int *__restrict__ scol, const T *__restrict__ sval, const T *__restrict__ sinv,
                            const T *__restrict__ b, const T *__restrict__ xin, T *__restrict__ xout,
                            const uint8_t *__restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || skip[i]) return;
-  xout[i] = jac_row(xin[i], dinv[i], b[i], row_sell(i, rowptr, slice_ptr, scol, sval, xin));
+  xout[i] = jac_row(xin[i], sinv[i], b[i], row_sell(i, rowptr, slice_ptr, scol, sval, xin));
 }
 
 template <class T>
@@ -469,7 +486,7 @@ __global__ void k_dense_apply(const int *__restrict__ sys_start, const long long
 constexpr int kTailLevels = 10;
 struct TailLevel {
   const int *sys_start, *rowptr, *col, *agg, *mptr, *mem;
-  const float *val, *dinv, *inv;
+  const float *val, *sinv, *inv;
   const long long *inv_off;
   float *x, *b, *t;
 };
@@ -502,9 +519,9 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail32(TailDesc d) {
       last = l - 1;
       break;
     }
-    for (int i = r0 + threadIdx.x; i < r0 + m; i += blockDim.x) L.t[i] = jac_first_row(L.b[i], L.dinv[i]);
+    for (int i = r0 + threadIdx.x; i < r0 + m; i += blockDim.x) L.t[i] = jac_first_row(L.b[i], L.sinv[i]);
     __syncthreads();
-    rows8(L, r0, m, L.t, [&](int i, float s) { L.x[i] = jac_row(L.t[i], L.dinv[i], L.b[i], s); });
+    rows8(L, r0, m, L.t, [&](int i, float s) { L.x[i] = jac_row(L.t[i], L.sinv[i], L.b[i], s); });
     __syncthreads();
     rows8(L, r0, m, L.x, [&](int i, float s) { L.t[i] = L.b[i] - s; });
     __syncthreads();
@@ -524,9 +541,9 @@ __global__ void __launch_bounds__(1024) k_vcycle_tail32(TailDesc d) {
         if (L.agg[i] >= 0) L.x[i] += xc[L.agg[i]];
     }
     __syncthreads();
-    rows8(L, r0, m, L.x, [&](int i, float s) { L.t[i] = jac_row(L.x[i], L.dinv[i], L.b[i], s); });
+    rows8(L, r0, m, L.x, [&](int i, float s) { L.t[i] = jac_row(L.x[i], L.sinv[i], L.b[i], s); });
     __syncthreads();
-    rows8(L, r0, m, L.t, [&](int i, float s) { L.x[i] = jac_row(L.t[i], L.dinv[i], L.b[i], s); });
+    rows8(L, r0, m, L.t, [&](int i, float s) { L.x[i] = jac_row(L.t[i], L.sinv[i], L.b[i], s); });
     __syncthreads();
   }
 }
@@ -709,8 +726,13 @@ void amg_setup(System *s, bool f32) {
     VAG_CUDA(cudaStreamSynchronize(st));
     A.levels.push_back(C);   // invalidates L
   }
-  // work vectors per level (x, b, t)
+  // work vectors per level (x, b, t) and the l1 smoother scaling
   for (auto &L : A.levels) {
+    L.sinv = static_cast<double *>(alloc(8 * (size_t)std::max(L.n, 1)));
+    if (L.n > 0) {
+      k_l1_inv<<<grid_for(L.n, TB), TB, 0, st>>>(L.n, L.rowptr, L.val, L.sinv);
+      note_launches(1);
+    }
     L.x = static_cast<double *>(alloc(8 * (size_t)std::max(L.n, 1)));
     L.b = static_cast<double *>(alloc(8 * (size_t)std::max(L.n, 1)));
     L.t = static_cast<double *>(alloc(8 * (size_t)std::max(L.n, 1)));
@@ -735,7 +757,7 @@ void amg_setup(System *s, bool f32) {
       } else {
         L.val32 = cast(L.val, L.nnz);
       }
-      L.dinv32 = cast(L.dinv, L.n);
+      L.sinv32 = cast(L.sinv, L.n);
       L.inv32 = L.any_term ? cast(L.inv, L.n_inv) : nullptr;
       L.x32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
       L.b32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
@@ -762,18 +784,18 @@ void amg_setup(System *s, bool f32) {
 // Level arrays of one precision.
 template <class T>
 struct LV {
-  const T *val, *dinv, *inv, *sval;
+  const T *val, *sinv, *inv, *sval;
   T *x, *b, *t;
 };
 template <class T>
 static LV<T> lv(System *s, AmgLevel &L);
 template <>
 LV<double> lv<double>(System *, AmgLevel &L) {
-  return {L.val, L.dinv, L.inv, L.sval, L.x, L.b, L.t};
+  return {L.val, L.sinv, L.inv, L.sval, L.x, L.b, L.t};
 }
 template <>
 LV<float> lv<float>(System *, AmgLevel &L) {
-  return {L.val32, L.dinv32, L.inv32, L.sval32, L.x32, L.b32, L.t32};
+  return {L.val32, L.sinv32, L.inv32, L.sval32, L.x32, L.b32, L.t32};
 }   // val32 on coarse levels, sval32 on level 0
 
 // x = V(b): one V(2,2) cycle from a zero initial guess.  Systems that end at
@@ -786,7 +808,7 @@ static void tail32(System *s, int lvl, cudaStream_t st) {
   if (d.nlev > kTailLevels) fail(VAG_ECUDA, "AMG: too many levels below the tail start");
   for (int k = 0; k < d.nlev; ++k) {
     AmgLevel &L = A.levels[lvl + k];
-    d.lv[k] = TailLevel{L.d_sys_start, L.rowptr, L.col, L.agg, L.mptr, L.mem, L.val32, L.dinv32,
+    d.lv[k] = TailLevel{L.d_sys_start, L.rowptr, L.col, L.agg, L.mptr, L.mem, L.val32, L.sinv32,
                         L.inv32, L.any_term ? L.inv_off : nullptr, L.x32, L.b32, L.t32};
   }
   k_vcycle_tail32<<<s->seg.n_sys, 1024, 0, st>>>(d);
@@ -815,12 +837,12 @@ static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
   const int g8 = grid_for(n, 32);
   auto sweep = [&](const T *xin, T *xout) {
     if (lvl == 0)
-      k_jac_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, v.dinv, b, xin, xout, L.skip);
+      k_jac_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, v.sinv, b, xin, xout, L.skip);
     else
-      k_jac_csr8<T><<<g8, 256, 0, st>>>(n, L.rowptr, L.col, v.val, v.dinv, b, xin, xout, L.skip);
+      k_jac_csr8<T><<<g8, 256, 0, st>>>(n, L.rowptr, L.col, v.val, v.sinv, b, xin, xout, L.skip);
   };
   // pre-smoothing: two damped Jacobi sweeps from x = 0
-  k_jac_first<T><<<g, TB, 0, st>>>(n, b, v.dinv, v.t);
+  k_jac_first<T><<<g, TB, 0, st>>>(n, b, v.sinv, v.t);
   sweep(v.t, x);
   // residual, restricted to the coarse level (t is free again)
   if (lvl == 0)

@@ -85,6 +85,7 @@ struct AmgLevel {
   int64_t nnz = 0;
   int *rowptr = nullptr, *col = nullptr;
   double *val = nullptr, *dinv = nullptr;
+  double *sinv = nullptr;          // [n] smoother scaling 1 / sum_j |a_ij| (l1-Jacobi)
   std::vector<int> sys_start;      // host, n_sys+1: first row of each system
   int *d_sys_start = nullptr;
   int *agg = nullptr;              // [n] aggregate (row of the next level) or -1
@@ -104,7 +105,7 @@ struct AmgLevel {
   float *sval32 = nullptr;
   int64_t sell_nnz = 0;
   // FP32 copy (mixed-precision path)
-  float *val32 = nullptr, *dinv32 = nullptr, *inv32 = nullptr;
+  float *val32 = nullptr, *sinv32 = nullptr, *inv32 = nullptr;
   float *x32 = nullptr, *b32 = nullptr, *t32 = nullptr;
 };
 struct Amg {

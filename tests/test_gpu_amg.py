@@ -123,3 +123,23 @@ def test_fp32_hierarchy_batch_equals_alone_bitwise(ctx):
         assert infos[i].iterations == inf1.iterations
         assert inf1.rel_residual <= 1e-10
         s1.close()
+
+
+@pytest.mark.parametrize("index", [252, 144])
+def test_amg_on_rows_where_damped_jacobi_diverges(ctx, index):
+    """Realisations of the 256-system batch (seed 99) whose eliminated matrix
+    has lambda_max(D^-1 A) > 3: a damped-Jacobi smoother with omega = 2/3 is
+    not convergent there, the V-cycle is indefinite and CG breaks down.  The
+    l1-Jacobi smoother keeps the preconditioner positive definite."""
+    import paper_1602_03641_gb300 as pkg
+    pb = vi.random_dfn_problem(*vi.batch_params(256, seed=99)[index])
+    s = pkg.assemble_problem(ctx, pb)
+    for prec in (pkg.VAG_FP64, pkg.VAG_MIXED):
+        _, info = s.solve(precision=prec, precond=pkg.VAG_PC_AMG, rtol=1e-10, maxit=2000, raise_on_error=False)
+        assert info.status == pkg.VAG_OK and info.rel_residual <= 1e-10, (prec, info.status, info.rel_residual)
+        assert info.iterations <= 80, info.iterations
+    if index == 252:
+        u, info = s.solve(precond=pkg.VAG_PC_AMG, rtol=1e-12, maxit=2000, raise_on_error=False)
+        assert info.rel_residual <= 1e-11, (info.status, info.rel_residual)
+        ref = vo.DarcyTransport(pb)
+        assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-10

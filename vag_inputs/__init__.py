@@ -335,9 +335,8 @@ def config_mixed128(n=128, ratio=1e4, seed=4321) -> Problem:
     return random_dfn_problem(n, 50, ratio, seed)
 
 
-def batch_problems(count, seed=99, n_lo=16, n_hi=48):
-    """Independent realisations: n ~ U{n_lo..n_hi}, 1-20 rectangles,
-    fracture/matrix ratio log-uniform in [1e2, 1e6], lognormal matrix K."""
+def batch_params(count, seed=99, n_lo=16, n_hi=48):
+    """(n, number of rectangles, ratio, seed) of each realisation of a batch."""
     rng = np.random.default_rng(seed)
     out = []
     for b in range(count):
@@ -345,8 +344,14 @@ def batch_problems(count, seed=99, n_lo=16, n_hi=48):
         nf = int(rng.integers(1, 21))
         ratio = float(10.0 ** rng.uniform(2.0, 6.0))
         s = int(rng.integers(0, 2**31 - 1))
-        out.append(random_dfn_problem(n, nf, ratio, s))
+        out.append((n, nf, ratio, s))
     return out
+
+
+def batch_problems(count, seed=99, n_lo=16, n_hi=48):
+    """Independent realisations: n ~ U{n_lo..n_hi}, 1-20 rectangles,
+    fracture/matrix ratio log-uniform in [1e2, 1e6], lognormal matrix K."""
+    return [random_dfn_problem(*p) for p in batch_params(count, seed, n_lo, n_hi)]
 
 
 # ----------------------------------------------------------------------------
