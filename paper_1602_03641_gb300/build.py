@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
                     raise RuntimeError("nvcc failed: " + " ".join(cmd))
     if force or cmds or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+        cmd = [nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs, "-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(r.stdout + r.stderr)

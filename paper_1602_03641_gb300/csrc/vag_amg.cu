@@ -18,8 +18,10 @@
 //             hierarchy there: its block is inverted densely (Gauss-Jordan,
 //             SPD) and applied exactly in the cycle.  The depth of a system's
 //             hierarchy therefore depends on that system alone.
-// Apply: a V(2,2) cycle with damped Jacobi (omega = 2/3) before and after the
-// coarse correction; it is a fixed symmetric linear operator, as CG needs.
+// Apply: a V(2,2) cycle with l1-Jacobi sweeps before and after the coarse
+// correction; it is a fixed symmetric linear operator, as CG needs.
+#include <cstdio>
+
 #include "vag_internal.cuh"
 #include "vag_reduce.cuh"
 
@@ -40,7 +42,6 @@ constexpr double kOmega = 4.0 / 3.0;
 constexpr int kDenseMax = 48;       // two 48x48 FP64 blocks fit the static shared limit
 constexpr int kMaxLevels = 16;
 constexpr int kCoarseWidth = 160;   // unique columns of one coarse row (< 256)
-constexpr int kTailRows = 1024;     // FP32 levels at most this big per system run in one kernel
 
 constexpr unsigned long long KEY_IN = ~0ull;
 constexpr unsigned long long KEY_OUT = 0ull;
@@ -273,6 +274,13 @@ __global__ void k_coarse_compact(int nc, const int *__restrict__ tcol, const dou
   }
 }
 
+// first nonzero of each system's rows: rowptr[sys_start[g]]
+__global__ void k_nz_starts(int n_sys, const int *__restrict__ sys_start, const int *__restrict__ rowptr,
+                            int *__restrict__ nz_start) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g <= n_sys) nz_start[g] = rowptr[sys_start[g]];
+}
+
 __global__ void k_coarse_starts(int n_sys, const int *__restrict__ sys_start, const int *__restrict__ rscan,
                                 int *csys_start) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -344,20 +352,64 @@ __device__ __forceinline__ T row_sell(int i, const int *__restrict__ rowptr, con
   return s;
 }
 
-// Row product of a coarse level: 8 lanes per CSR row, lane l takes entries
-// l, l+8, ... and the partial sums meet in a fixed shuffle tree.  All 32 lanes
-// of the warp must call it together (rows past the end pass valid = false).
+// Row product of a coarse level: LN lanes per CSR row, lane l takes entries
+// l, l+LN, ... and the partial sums meet in a fixed shuffle tree.  All 32
+// lanes of the warp must call it together (rows past the end pass valid =
+// false).  Coarse levels are latency-bound: 8 lanes per row keep each lane's
+// chain of dependent loads short (measured on GB300: 2 lanes per row, which
+// halves the FP64 instructions, made the FP64 sweeps 1.6x slower).
 template <class T>
-__device__ __forceinline__ T row_csr8(int i, bool valid, int lane, const int *__restrict__ rowptr,
-                                      const int *__restrict__ col, const T *__restrict__ val,
-                                      const T *__restrict__ x) {
+__host__ __device__ constexpr int row_lanes() { return 8; }
+
+template <int LN, class T>
+__device__ __forceinline__ T lane_reduce(T s) {
+#pragma unroll
+  for (int o = LN / 2; o >= 1; o /= 2) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <int LN, class T>
+__device__ __forceinline__ T row_csr(int i, bool valid, int lane, const int *__restrict__ rowptr,
+                                     const int *__restrict__ col, const T *__restrict__ val,
+                                     const T *__restrict__ x) {
   T s = 0;
   if (valid)
-    for (int k = rowptr[i] + lane; k < rowptr[i + 1]; k += 8) s = fma(val[k], x[col[k]], s);
-  s += __shfl_xor_sync(0xffffffffu, s, 4);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  return s;
+    for (int k = rowptr[i] + lane; k < rowptr[i + 1]; k += LN) s = fma(val[k], x[col[k]], s);
+  return lane_reduce<LN>(s);
+}
+
+// The same row product split in two for programmatic dependent launch: the
+// first kPF entries of each lane (matrix data, written by no kernel of the
+// cycle) are loaded before pdl_wait(), the x gathers after it.  Entries are
+// multiplied in the same order as row_csr, so the sum is identical.
+constexpr int kPF = 4;
+template <class T>
+struct RowPF {
+  int k, ke;
+  int c[kPF];
+  T v[kPF];
+};
+template <int LN, class T>
+__device__ __forceinline__ void row_prefetch(RowPF<T> &f, int i, bool valid, int lane, const int *__restrict__ rowptr,
+                                             const int *__restrict__ col, const T *__restrict__ val) {
+  f.k = valid ? rowptr[i] + lane : 0;
+  f.ke = valid ? rowptr[i + 1] : 0;
+#pragma unroll
+  for (int u = 0; u < kPF; ++u) {
+    const int k = f.k + LN * u;
+    f.c[u] = k < f.ke ? col[k] : 0;
+    f.v[u] = k < f.ke ? val[k] : (T)0;
+  }
+}
+template <int LN, class T>
+__device__ __forceinline__ T row_finish(const RowPF<T> &f, const int *__restrict__ col, const T *__restrict__ val,
+                                        const T *__restrict__ x) {
+  T s = 0;
+#pragma unroll
+  for (int u = 0; u < kPF; ++u)
+    if (f.k + LN * u < f.ke) s = fma(f.v[u], x[f.c[u]], s);
+  for (int k = f.k + LN * kPF; k < f.ke; k += LN) s = fma(val[k], x[col[k]], s);
+  return lane_reduce<LN>(s);
 }
 
 template <class T>
@@ -368,65 +420,44 @@ __device__ __forceinline__ T jac_row(T xin, T sinv, T b, T ax) { return fma((T)k
 template <class T>
 __global__ void k_jac_first(int n, const T *__restrict__ b, const T *__restrict__ sinv, T *x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (i < n) x[i] = jac_first_row(b[i], sinv[i]);
 }
 
-// x_out = x_in + omega D^-1 (b - A x_in), CSR, one thread per row
+// x_out = x_in + omega D_l1^-1 (b - A x_in) on a coarse level, row_lanes<T>()
+// lanes per row (256 / LN rows per block); rows of systems solved densely here
+// are skipped
 template <class T>
-__global__ void k_jac_csr(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                          const T *__restrict__ val, const T *__restrict__ sinv, const T *__restrict__ b,
-                          const T *__restrict__ xin, T *__restrict__ xout, const uint8_t *__restrict__ skip) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || skip[i]) return;
-  T s = 0;
-  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(val[k], xin[col[k]], s);
-  xout[i] = jac_row(xin[i], sinv[i], b[i], s);
-}
-
-// coarse-level sweep and residual, 8 lanes per row (32 rows per block)
-template <class T>
-__global__ void __launch_bounds__(256) k_jac_csr8(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                                                  const T *__restrict__ val, const T *__restrict__ sinv,
-                                                  const T *__restrict__ b, const T *__restrict__ xin,
-                                                  T *__restrict__ xout, const uint8_t *__restrict__ skip) {
-  const int lane = threadIdx.x & 7;
-  const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
+__global__ void __launch_bounds__(256) k_jac_csr(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                                 const T *__restrict__ val, const T *__restrict__ sinv,
+                                                 const T *__restrict__ b, const T *__restrict__ xin,
+                                                 T *__restrict__ xout, const uint8_t *__restrict__ skip) {
+  constexpr int LN = row_lanes<T>();
+  const int lane = threadIdx.x & (LN - 1);
+  const int i = blockIdx.x * (256 / LN) + threadIdx.x / LN;
   const bool valid = i < n;
-  const T s = row_csr8(i, valid, lane, rowptr, col, val, xin);
-  if (valid && lane == 0 && !skip[i]) xout[i] = jac_row(xin[i], sinv[i], b[i], s);
+  RowPF<T> f;
+  row_prefetch<LN>(f, i, valid, lane, rowptr, col, val);
+  const bool own = valid && lane == 0 && !skip[i];
+  const T si = own ? sinv[i] : (T)0;
+  pdl_wait();
+  pdl_trigger();
+  const T s = row_finish<LN>(f, col, val, xin);
+  if (own) xout[i] = jac_row(xin[i], si, b[i], s);
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_resid_csr8(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                                                    const T *__restrict__ val, const T *__restrict__ b,
-                                                    const T *__restrict__ x, T *__restrict__ r) {
-  const int lane = threadIdx.x & 7;
-  const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
-  const bool valid = i < n;
-  const T s = row_csr8(i, valid, lane, rowptr, col, val, x);
-  if (valid && lane == 0) r[i] = b[i] - s;
-}
-
-// same sweep in the sliced-ELL layout
+// same sweep in the sliced-ELL layout (level 0), one thread per row
 template <class T>
 __global__ void k_jac_sell(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                            const int *__restrict__ scol, const T *__restrict__ sval, const T *__restrict__ sinv,
                            const T *__restrict__ b, const T *__restrict__ xin, T *__restrict__ xout,
                            const uint8_t *__restrict__ skip) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (i >= n || skip[i]) return;
   xout[i] = jac_row(xin[i], sinv[i], b[i], row_sell(i, rowptr, slice_ptr, scol, sval, xin));
-}
-
-template <class T>
-__global__ void k_resid_csr(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                            const T *__restrict__ val, const T *__restrict__ b, const T *__restrict__ x,
-                            T *__restrict__ r) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  T s = 0;
-  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(val[k], x[col[k]], s);
-  r[i] = b[i] - s;
 }
 
 template <class T>
@@ -434,6 +465,8 @@ __global__ void k_resid_sell(int n, const int *__restrict__ rowptr, const int *_
                              const int *__restrict__ scol, const T *__restrict__ sval, const T *__restrict__ b,
                              const T *__restrict__ x, T *__restrict__ r) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (i >= n) return;
   r[i] = b[i] - row_sell(i, rowptr, slice_ptr, scol, sval, x);
 }
@@ -447,18 +480,114 @@ __device__ __forceinline__ T restrict_row(int I, const int *__restrict__ mptr, c
   return acc;
 }
 
-template <class T>
-__global__ void k_restrict(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
-                           const T *__restrict__ r, T *__restrict__ bc) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nc) return;
-  bc[I] = restrict_row(I, mptr, mem, r);
-}
 
 template <class T>
 __global__ void k_prolong(int n, const int *__restrict__ agg, const T *__restrict__ xc, T *x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && agg[i] >= 0) x[i] += xc[agg[i]];
+  const int J = i < n ? agg[i] : -1;
+  pdl_wait();
+  pdl_trigger();
+  if (J >= 0) x[i] += xc[J];
+}
+
+// Restriction fused with the first (zero-start) sweep of the coarse level:
+// bc = P^T r, tc = omega D_l1^-1 bc.
+template <class T>
+__global__ void k_restrict_first(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
+                                 const T *__restrict__ r, const T *__restrict__ sinv_c, T *__restrict__ bc,
+                                 T *__restrict__ tc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
+  if (I >= nc) return;
+  const T v = restrict_row(I, mptr, mem, r);
+  bc[I] = v;
+  tc[I] = jac_first_row(v, sinv_c[I]);
+}
+
+// Residual of a coarse level, restricted and turned into the next level's
+// first sweep, in one pass: one warp per coarse row I, its member rows taken
+// four at a time (8 lanes each); lane 0 adds the member residuals in member
+// order, exactly as restrict_row does with a stored residual.
+template <class T>
+__global__ void __launch_bounds__(256) k_resid_restrict8(int nc, const int *__restrict__ mptr,
+                                                         const int *__restrict__ mem, const int *__restrict__ rowptr,
+                                                         const int *__restrict__ col, const T *__restrict__ val,
+                                                         const T *__restrict__ b, const T *__restrict__ x,
+                                                         const T *__restrict__ sinv_c, T *__restrict__ bc,
+                                                         T *__restrict__ tc) {
+  const int I = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int wl = threadIdx.x & 31, grp = wl >> 3, lane = wl & 7;
+  // first member chunk's matrix rows before the dependency wait
+  const int p0 = I < nc ? mptr[I] : 0, p1 = I < nc ? mptr[I + 1] : 0;
+  RowPF<T> f;
+  {
+    const bool valid = p0 + grp < p1;
+    row_prefetch<8>(f, valid ? mem[p0 + grp] : 0, valid, lane, rowptr, col, val);
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (I >= nc) return;   // whole warps leave together
+  T acc = 0;
+  for (int base = p0; base < p1; base += 4) {
+    const bool valid = base + grp < p1;
+    const int i = valid ? mem[base + grp] : 0;
+    const T s = base == p0 ? row_finish<8>(f, col, val, x) : row_csr<8>(i, valid, lane, rowptr, col, val, x);
+    const T r = valid ? b[i] - s : (T)0;
+    const int cnt = min(4, p1 - base);
+    for (int q = 0; q < cnt; ++q) {
+      const T rq = __shfl_sync(0xffffffffu, r, 8 * q);
+      acc += rq;
+    }
+  }
+  if (wl == 0) {
+    bc[I] = acc;
+    tc[I] = jac_first_row(acc, sinv_c[I]);
+  }
+}
+
+// Prolongation fused with the first post-smoothing sweep of a coarse level:
+// the corrected iterate x + P xc is formed on the fly for every entry read,
+// t = (x + P xc) + omega D_l1^-1 (b - A (x + P xc)).
+template <class T>
+__global__ void __launch_bounds__(256) k_prolong_jac8(int n, const int *__restrict__ rowptr,
+                                                      const int *__restrict__ col, const T *__restrict__ val,
+                                                      const T *__restrict__ sinv, const T *__restrict__ b,
+                                                      const T *__restrict__ x, const int *__restrict__ agg,
+                                                      const T *__restrict__ xc, T *__restrict__ t,
+                                                      const uint8_t *__restrict__ skip) {
+  const int lane = threadIdx.x & 7;
+  const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const bool valid = i < n;
+  RowPF<T> f;
+  row_prefetch<8>(f, i, valid, lane, rowptr, col, val);
+  int fa[kPF];
+#pragma unroll
+  for (int u = 0; u < kPF; ++u) fa[u] = f.k + 8 * u < f.ke ? agg[f.c[u]] : -1;
+  pdl_wait();
+  pdl_trigger();
+  T s = 0;
+#pragma unroll
+  for (int u = 0; u < kPF; ++u)
+    if (f.k + 8 * u < f.ke) {
+      const int j = f.c[u], J = fa[u];
+      const T xj = J >= 0 ? x[j] + xc[J] : x[j];
+      s = fma(f.v[u], xj, s);
+    }
+  for (int k = f.k + 8 * kPF; k < f.ke; k += 8) {
+    const int j = col[k];
+    const int J = agg[j];
+    const T xj = J >= 0 ? x[j] + xc[J] : x[j];
+    s = fma(val[k], xj, s);
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  if (valid && lane == 0 && !skip[i]) {
+    const int J = agg[i];
+    const T xi = J >= 0 ? x[i] + xc[J] : x[i];
+    t[i] = jac_row(xi, sinv[i], b[i], s);
+  }
 }
 
 // x = inv_g b per system block (one thread block per system)
@@ -474,93 +603,258 @@ __global__ void k_dense_apply(const int *__restrict__ sys_start, const long long
                               const T *__restrict__ inv, const T *__restrict__ b, T *x) {
   const int g = blockIdx.x;
   const int r0 = sys_start[g], m = sys_start[g + 1] - r0;
-  if (m == 0 || off[g + 1] - off[g] != (long long)m * m) return;   // not terminal here
+  const bool term = m > 0 && off[g + 1] - off[g] == (long long)m * m;
+  pdl_wait();
+  pdl_trigger();
+  if (!term) return;   // not terminal here
   const T *M = inv + off[g];
   for (int i = threadIdx.x; i < m; i += blockDim.x) x[r0 + i] = dense_row(i, m, M, b + r0);
 }
 
-// The lower part of the FP32 V-cycle (levels with at most kTailRows rows per
-// system) in one kernel: one thread block per system walks its levels down
-// and up with a barrier between phases.  Same row arithmetic as the grid
-// kernels, so the result is identical to launching them level by level.
+// The lower part of the V-cycle in one kernel, out of shared memory: one
+// thread block per system copies its rows of the tail levels (matrix, l1
+// scaling, aggregates, members, dense inverse of its terminal block) into
+// shared memory, walks the levels down and up with a block barrier between
+// phases, and writes the first tail level's x back.  Same row arithmetic in
+// the same order as the grid kernels, so the result is identical.
 constexpr int kTailLevels = 10;
-struct TailLevel {
-  const int *sys_start, *rowptr, *col, *agg, *mptr, *mem;
-  const float *val, *sinv, *inv;
-  const long long *inv_off;
-  float *x, *b, *t;
+constexpr int kTailThreads = 1024;              // 128 groups of 8 lanes
+constexpr size_t kTailSmem = 200 * 1024;        // dynamic shared memory cap
+
+__host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// cp.async of one 4- or 8-byte element, global -> shared (Ampere and later)
+template <class E>
+__device__ __forceinline__ void cp_async(E *dst, const E *src) {
+  static_assert(sizeof(E) == 4 || sizeof(E) == 8, "4- or 8-byte elements");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(E) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// bytes one system's level takes in the tail's shared memory: m rows, z
+// nonzeros, mc rows of the next level, terminal or not
+template <class T>
+__host__ __device__ inline size_t tail_level_bytes(int m, int z, int mc, bool term) {
+  size_t b = a16(4 * ((size_t)m + 1)) + a16(4 * (size_t)z) + a16(sizeof(T) * (size_t)z) + 4 * a16(sizeof(T) * (size_t)m);
+  if (term) b += a16(sizeof(T) * (size_t)m * m);
+  else b += a16(4 * (size_t)m) + a16(4 * ((size_t)mc + 1)) + a16(4 * (size_t)m);
+  return b;
+}
+
+template <class T>
+struct TailLevel {   // one level, whole batch (global memory)
+  const int *sys_start, *nz_start, *rowptr, *col, *agg, *mptr, *mem;
+  const T *val, *sinv, *inv;
+  const long long *inv_off;   // null if no system is terminal here
+  T *x, *b;
 };
+template <class T>
 struct TailDesc {
-  TailLevel lv[kTailLevels];
+  TailLevel<T> lv[kTailLevels];
   int nlev;
+  unsigned smem;
+};
+template <class T>
+struct TailLoc {   // one level of this block's system (shared memory)
+  int m, mc, term;
+  int *rp, *col, *agg, *mp, *mem;
+  T *val, *sinv, *x, *b, *t, *inv;
 };
 
-__global__ void __launch_bounds__(1024) k_vcycle_tail32(TailDesc d) {
+template <class T>
+__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailDesc<T> d, int *status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ TailLoc<T> loc[kTailLevels];
+  __shared__ long long hdr[kTailLevels][10];   // per level: the scalars below
+  __shared__ int nl;                           // levels this system has in the tail
+  constexpr int NG = kTailThreads / 8;
   const int g = blockIdx.x;
-  const int lane = threadIdx.x & 7, grp = threadIdx.x >> 3;   // 128 groups of 8 lanes
-  int last = d.nlev - 1;   // deepest level with a coarse correction below it
-  // one op per row over [r0, r0+m), 8 lanes per row, uniform loop bound
-  auto rows8 = [&](const TailLevel &L, int r0, int m, const float *x, auto &&emit) {
-    for (int base = 0; base < m; base += 128) {
-      const int i = r0 + base + grp;
-      const bool valid = base + grp < m;
-      const float s = row_csr8(i, valid, lane, L.rowptr, L.col, L.val, x);
+  const int lane = threadIdx.x & 7, grp = threadIdx.x >> 3;
+  // 1. the system's offsets on every tail level, one load per thread
+  //    0,1 rows [r0, r1); 2,3 nonzeros [z0, z1); 4,5 inverse [i0, i1);
+  //    6,7 next level's rows [c0, c1); 8,9 members [q0, q1) (step 2)
+  if (threadIdx.x < 8 * d.nlev) {
+    const int k = threadIdx.x >> 3, j = threadIdx.x & 7;
+    const TailLevel<T> &G = d.lv[k];
+    long long v = 0;
+    switch (j) {
+      case 0: v = G.sys_start[g]; break;
+      case 1: v = G.sys_start[g + 1]; break;
+      case 2: v = G.nz_start[g]; break;
+      case 3: v = G.nz_start[g + 1]; break;
+      case 4: v = G.inv_off ? G.inv_off[g] : 0; break;
+      case 5: v = G.inv_off ? G.inv_off[g + 1] : 0; break;
+      case 6: v = k + 1 < d.nlev ? d.lv[k + 1].sys_start[g] : 0; break;
+      default: v = k + 1 < d.nlev ? d.lv[k + 1].sys_start[g + 1] : 0; break;
+    }
+    hdr[k][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * d.nlev) {   // members of the next level's rows
+    const int k = threadIdx.x >> 1, j = threadIdx.x & 1;
+    const long long m = hdr[k][1] - hdr[k][0];
+    const bool term = m > 0 && hdr[k][5] - hdr[k][4] == m * m;
+    hdr[k][8 + j] = (!term && m > 0 && k + 1 < d.nlev) ? d.lv[k].mptr[hdr[k][6 + j]] : 0;
+  }
+  // 2. shared-memory layout
+  if (threadIdx.x == 0) {
+    size_t off = 0;
+    int k = 0;
+    for (; k < d.nlev; ++k) {
+      const int m = (int)(hdr[k][1] - hdr[k][0]);
+      if (m == 0) break;
+      const int z = (int)(hdr[k][3] - hdr[k][2]);
+      const bool term = hdr[k][5] - hdr[k][4] == (long long)m * m;
+      const int mc = (!term && k + 1 < d.nlev) ? (int)(hdr[k][7] - hdr[k][6]) : 0;
+      TailLoc<T> &L = loc[k];
+      L.m = m; L.mc = mc; L.term = term;
+      auto take = [&](size_t bytes) { unsigned char *p = sm + off; off += a16(bytes); return p; };
+      L.rp = (int *)take(4 * ((size_t)m + 1));
+      L.col = (int *)take(4 * (size_t)z);
+      L.val = (T *)take(sizeof(T) * (size_t)z);
+      L.sinv = (T *)take(sizeof(T) * (size_t)m);
+      L.x = (T *)take(sizeof(T) * (size_t)m);
+      L.b = (T *)take(sizeof(T) * (size_t)m);
+      L.t = (T *)take(sizeof(T) * (size_t)m);
+      if (term) {
+        L.inv = (T *)take(sizeof(T) * (size_t)m * m);
+        L.agg = L.mp = L.mem = nullptr;
+      } else {
+        L.inv = nullptr;
+        L.agg = (int *)take(4 * (size_t)m);
+        L.mp = (int *)take(4 * ((size_t)mc + 1));
+        L.mem = (int *)take(4 * (size_t)m);
+      }
+      if (term) { ++k; break; }
+    }
+    nl = k;
+    if (off > d.smem) {   // cannot happen: the host sized d.smem from the same layout
+      atomicOr(status, ST_TAIL_SMEM);
+      nl = -1;
+    }
+  }
+  __syncthreads();
+  if (nl <= 0) {
+    pdl_wait();
+    return;
+  }
+  // 3. asynchronous copies global -> shared (no register round trip, all in
+  //    flight together), then the indices made local to the system
+  for (int k = 0; k < nl; ++k) {
+    const TailLevel<T> &G = d.lv[k];
+    const TailLoc<T> &L = loc[k];
+    const int r0 = (int)hdr[k][0], z0 = (int)hdr[k][2], m = L.m;
+    const int z = (int)(hdr[k][3] - z0);
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) cp_async(&L.rp[i], &G.rowptr[r0 + i]);
+    for (int q = threadIdx.x; q < z; q += blockDim.x) {
+      cp_async(&L.col[q], &G.col[z0 + q]);
+      cp_async(&L.val[q], &G.val[z0 + q]);
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) cp_async(&L.sinv[i], &G.sinv[r0 + i]);
+    if (L.term) {
+      const T *M = G.inv + hdr[k][4];
+      for (int q = threadIdx.x; q < m * m; q += blockDim.x) cp_async(&L.inv[q], &M[q]);
+    } else {
+      const int c0 = (int)hdr[k][6];
+      const int q0 = (int)hdr[k][8], nm = (int)(hdr[k][9] - q0);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) cp_async(&L.agg[i], &G.agg[r0 + i]);
+      for (int I = threadIdx.x; I <= L.mc; I += blockDim.x) cp_async(&L.mp[I], &G.mptr[c0 + I]);
+      for (int p = threadIdx.x; p < nm; p += blockDim.x) cp_async(&L.mem[p], &G.mem[q0 + p]);
+    }
+  }
+  // the right-hand side comes from the preceding kernel
+  pdl_wait();
+  pdl_trigger();
+  {
+    const int r0 = (int)hdr[0][0];
+    for (int i = threadIdx.x; i < loc[0].m; i += blockDim.x) cp_async(&loc[0].b[i], &d.lv[0].b[r0 + i]);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int k = 0; k < nl; ++k) {
+    const TailLoc<T> &L = loc[k];
+    const int r0 = (int)hdr[k][0], z0 = (int)hdr[k][2], m = L.m;
+    const int z = (int)(hdr[k][3] - z0);
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) L.rp[i] -= z0;
+    for (int q = threadIdx.x; q < z; q += blockDim.x) L.col[q] -= r0;
+    if (!L.term) {
+      const int c0 = (int)hdr[k][6], q0 = (int)hdr[k][8], nm = (int)(hdr[k][9] - q0);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) L.agg[i] = L.agg[i] >= 0 ? L.agg[i] - c0 : -1;
+      for (int I = threadIdx.x; I <= L.mc; I += blockDim.x) L.mp[I] -= q0;
+      for (int p = threadIdx.x; p < nm; p += blockDim.x) L.mem[p] -= r0;
+    }
+  }
+  __syncthreads();
+  // one op per row, 8 lanes per row, uniform loop bound
+  auto rows8 = [&](const TailLoc<T> &L, const T *x, auto &&emit) {
+    for (int base = 0; base < L.m; base += NG) {
+      const int i = base + grp;
+      const bool valid = i < L.m;
+      const T s = row_csr<8>(i, valid, lane, L.rp, L.col, L.val, x);
       if (valid && lane == 0) emit(i, s);
     }
   };
-  for (int l = 0; l < d.nlev; ++l) {
-    const TailLevel &L = d.lv[l];
-    const int r0 = L.sys_start[g], m = L.sys_start[g + 1] - r0;
-    if (m == 0) { last = l - 1; break; }
-    if (L.inv_off && L.inv_off[g + 1] - L.inv_off[g] == (long long)m * m) {   // terminal here
-      const float *M = L.inv + L.inv_off[g];
-      for (int i = threadIdx.x; i < m; i += blockDim.x) L.x[r0 + i] = dense_row(i, m, M, L.b + r0);
+  int last = nl - 1;   // deepest level with a coarse correction below it
+  for (int k = 0; k < nl; ++k) {
+    const TailLoc<T> &L = loc[k];
+    if (L.term) {
+      for (int i = threadIdx.x; i < L.m; i += blockDim.x) L.x[i] = dense_row(i, L.m, L.inv, L.b);
       __syncthreads();
-      last = l - 1;
+      last = k - 1;
       break;
     }
-    for (int i = r0 + threadIdx.x; i < r0 + m; i += blockDim.x) L.t[i] = jac_first_row(L.b[i], L.sinv[i]);
+    for (int i = threadIdx.x; i < L.m; i += blockDim.x) L.t[i] = jac_first_row(L.b[i], L.sinv[i]);
     __syncthreads();
-    rows8(L, r0, m, L.t, [&](int i, float s) { L.x[i] = jac_row(L.t[i], L.sinv[i], L.b[i], s); });
+    rows8(L, L.t, [&](int i, T s) { L.x[i] = jac_row(L.t[i], L.sinv[i], L.b[i], s); });
     __syncthreads();
-    rows8(L, r0, m, L.x, [&](int i, float s) { L.t[i] = L.b[i] - s; });
+    rows8(L, L.x, [&](int i, T s) { L.t[i] = L.b[i] - s; });
     __syncthreads();
-    if (l + 1 < d.nlev) {
-      const TailLevel &C = d.lv[l + 1];
-      for (int I = C.sys_start[g] + threadIdx.x; I < C.sys_start[g + 1]; I += blockDim.x)
-        C.b[I] = restrict_row(I, L.mptr, L.mem, L.t);
+    if (k + 1 < nl) {
+      const TailLoc<T> &C = loc[k + 1];
+      for (int I = threadIdx.x; I < C.m; I += blockDim.x) C.b[I] = restrict_row(I, L.mp, L.mem, L.t);
     }
     __syncthreads();
   }
-  for (int l = last; l >= 0; --l) {
-    const TailLevel &L = d.lv[l];
-    const int r0 = L.sys_start[g], m = L.sys_start[g + 1] - r0;
-    if (l + 1 < d.nlev) {
-      const float *xc = d.lv[l + 1].x;
-      for (int i = r0 + threadIdx.x; i < r0 + m; i += blockDim.x)
+  for (int k = last; k >= 0; --k) {
+    const TailLoc<T> &L = loc[k];
+    if (k + 1 < nl) {
+      const T *xc = loc[k + 1].x;
+      for (int i = threadIdx.x; i < L.m; i += blockDim.x)
         if (L.agg[i] >= 0) L.x[i] += xc[L.agg[i]];
     }
     __syncthreads();
-    rows8(L, r0, m, L.x, [&](int i, float s) { L.t[i] = jac_row(L.x[i], L.sinv[i], L.b[i], s); });
+    rows8(L, L.x, [&](int i, T s) { L.t[i] = jac_row(L.x[i], L.sinv[i], L.b[i], s); });
     __syncthreads();
-    rows8(L, r0, m, L.t, [&](int i, float s) { L.x[i] = jac_row(L.t[i], L.sinv[i], L.b[i], s); });
+    rows8(L, L.t, [&](int i, T s) { L.x[i] = jac_row(L.t[i], L.sinv[i], L.b[i], s); });
     __syncthreads();
+  }
+  {
+    const TailLoc<T> &L = loc[0];
+    T *gx = d.lv[0].x + d.lv[0].sys_start[g];
+    for (int i = threadIdx.x; i < L.m; i += blockDim.x) gx[i] = L.x[i];
   }
 }
 
 __global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (i < n) b[i] = (float)a[i];
 }
 
 __global__ void k_to_f64(int n, const float *__restrict__ a, double *__restrict__ b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (i < n) b[i] = (double)a[i];
 }
 
 }  // namespace
 
-static void free_later(std::vector<void *> &v, void *p) { v.push_back(p); }
 
 // Build the hierarchy for the current matrix values (called before every
 // AMG solve: the numeric phase may have changed them).
@@ -651,6 +945,7 @@ void amg_setup(System *s, bool f32) {
     k_sqrt_diag<<<grid_for(n, TB), TB, 0, st>>>(n, L.dinv, sd);
     k_strength<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, L.val, sd, L.skip, strong, state);
     note_launches(2);
+    trace_mark(st, "level: terminal blocks + strength");
     // MIS(2) rounds, three between polls (a round after the last decision
     // changes nothing)
     for (int it = 0; it < 64; it += 3) {
@@ -667,6 +962,7 @@ void amg_setup(System *s, bool f32) {
       if (*und_host == 0) break;
     }
     if (*und_host != 0) fail(VAG_ECUDA, "AMG: MIS(2) did not finish in 64 rounds");
+    trace_mark(st, "level: MIS(2)");
     int *flag = static_cast<int *>(alloc(4 * (size_t)n));
     int *rscan = static_cast<int *>(alloc(4 * ((size_t)n + 1)));
     k_root_flags<<<grid_for(n, TB), TB, 0, st>>>(n, state, flag);
@@ -691,7 +987,8 @@ void amg_setup(System *s, bool f32) {
     k_member_fill<<<grid_for(n, TB), TB, 0, st>>>(n, L.agg, L.mptr, cursor, L.mem);
     k_sort_members<<<grid_for(nc, TB), TB, 0, st>>>(nc, L.mptr, L.mem);
     note_launches(2);
-    // Galerkin coarse matrix, then its sliced-ELL copy
+    trace_mark(st, "level: aggregates + members");
+    // Galerkin coarse matrix (coarse levels are swept in CSR, 8 lanes per row)
     AmgLevel C;
     C.n = nc;
     C.rowptr = static_cast<int *>(alloc(4 * ((size_t)nc + 1)));
@@ -714,10 +1011,7 @@ void amg_setup(System *s, bool f32) {
     note_launches(1);
     VAG_CUDA(cudaFreeAsync(tcol, st));
     VAG_CUDA(cudaFreeAsync(tval, st));
-    const int64_t snnz = sell_structure(st, nc, C.rowptr, C.col, &C.slice_ptr, &C.scol, alloc);
-    C.sval = static_cast<double *>(alloc(8 * (size_t)std::max<int64_t>(snnz, 1)));
-    C.sell_nnz = snnz;
-    sell_fill<double>(st, nc, C.rowptr, C.col, C.val, C.slice_ptr, C.sval);
+    trace_mark(st, "level: Galerkin product");
     C.d_sys_start = static_cast<int *>(alloc(4 * ((size_t)ns + 1)));
     k_coarse_starts<<<grid_for(ns + 1, TB), TB, 0, st>>>(ns, L.d_sys_start, rscan, C.d_sys_start);
     note_launches(1);
@@ -725,6 +1019,7 @@ void amg_setup(System *s, bool f32) {
     VAG_CUDA(cudaMemcpyAsync(C.sys_start.data(), C.d_sys_start, 4 * (ns + 1), cudaMemcpyDeviceToHost, st));
     VAG_CUDA(cudaStreamSynchronize(st));
     A.levels.push_back(C);   // invalidates L
+    trace_mark(st, "level: coarse row starts");
   }
   // work vectors per level (x, b, t) and the l1 smoother scaling
   for (auto &L : A.levels) {
@@ -764,20 +1059,67 @@ void amg_setup(System *s, bool f32) {
       L.t32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
     }
   }
-  // first level where every system has at most kTailRows rows: from there
-  // the FP32 V-cycle runs in one kernel
+  // first nonzero of each system on every coarse level (the tail's layout)
+  for (size_t l = 1; l < A.levels.size(); ++l) {
+    AmgLevel &L = A.levels[l];
+    L.d_nz_start = static_cast<int *>(alloc(4 * ((size_t)ns + 1)));
+    k_nz_starts<<<grid_for(ns + 1, TB), TB, 0, st>>>(ns, L.d_sys_start, L.rowptr, L.d_nz_start);
+    note_launches(1);
+    L.nz_start.assign(ns + 1, 0);
+    VAG_CUDA(cudaMemcpyAsync(L.nz_start.data(), L.d_nz_start, 4 * ((size_t)ns + 1), cudaMemcpyDeviceToHost, st));
+  }
+  VAG_CUDA(cudaStreamSynchronize(st));
+  // FP32 hierarchy: first level from which every system's remaining levels
+  // fit the tail's shared memory; from there the V-cycle runs in one kernel.
+  // (Not for FP64: one SM issues about two FP64 FMAs per clock on GB300, so
+  // FP64 work must spread over the whole GPU.)
   A.tail_start = -1;
-  if (f32) {
-    for (size_t l = 1; l < A.levels.size(); ++l) {
-      int mx = 0;
-      for (int g = 0; g < ns; ++g) mx = std::max(mx, A.levels[l].sys_start[g + 1] - A.levels[l].sys_start[g]);
-      if (mx <= kTailRows && (int)(A.levels.size() - l) <= kTailLevels) {
-        A.tail_start = (int)l;
-        break;
+  for (size_t l0 = 1; f32 && l0 < A.levels.size() && A.tail_start < 0; ++l0) {
+    if ((int)(A.levels.size() - l0) > kTailLevels) continue;
+    size_t need[2] = {0, 0};
+    for (int g = 0; g < ns; ++g) {
+      size_t b64 = 0, b32 = 0;
+      for (size_t l = l0; l < A.levels.size(); ++l) {
+        const AmgLevel &L = A.levels[l];
+        const int m = L.sys_start[g + 1] - L.sys_start[g];
+        if (m == 0) break;
+        const int z = L.nz_start[g + 1] - L.nz_start[g];
+        const bool term = m <= kDenseMax;
+        const int mc = (!term && l + 1 < A.levels.size())
+                           ? A.levels[l + 1].sys_start[g + 1] - A.levels[l + 1].sys_start[g] : 0;
+        b64 += tail_level_bytes<double>(m, z, mc, term);
+        b32 += tail_level_bytes<float>(m, z, mc, term);
+        if (term) break;
       }
+      need[0] = std::max(need[0], b64);
+      need[1] = std::max(need[1], b32);
+    }
+    if (need[f32 ? 1 : 0] <= kTailSmem) {
+      A.tail_start = (int)l0;
+      A.tail_smem[0] = need[0];
+      A.tail_smem[1] = need[1];
     }
   }
+  if (A.tail_start >= 0) {   // opt in to more than 48 KB of dynamic shared memory
+    if (f32)
+      VAG_CUDA(cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem));
+    else
+      VAG_CUDA(cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kTailSmem));
+  }
   VAG_CHECK_LAUNCH();
+  trace_mark(st, "smoother scaling, work vectors, FP32 copy");
+  if (trace_enabled()) {
+    std::fprintf(stderr, "[vag trace] AMG hierarchy: %zu levels, tail from level %d (%zu bytes of shared memory)\n",
+                 A.levels.size(), A.tail_start, A.tail_smem[f32 ? 1 : 0]);
+    for (size_t l = 0; l < A.levels.size(); ++l) {
+      const AmgLevel &L = A.levels[l];
+      int mx = 0;
+      for (int g = 0; g < ns; ++g) mx = std::max(mx, L.sys_start[g + 1] - L.sys_start[g]);
+      std::fprintf(stderr, "  level %zu: rows %d (largest system %d), nnz %lld%s%s\n", l, L.n, mx, (long long)L.nnz,
+                   L.any_term ? ", terminal systems" : "", L.all_term ? " (all)" : "");
+    }
+  }
   A.built = true;
 }
 
@@ -801,62 +1143,85 @@ LV<float> lv<float>(System *, AmgLevel &L) {
 // x = V(b): one V(2,2) cycle from a zero initial guess.  Systems that end at
 // this level are solved exactly; the others are smoothed, restricted,
 // corrected from the next level and smoothed again.
-static void tail32(System *s, int lvl, cudaStream_t st) {
+template <class T>
+static void tail(System *s, int lvl, cudaStream_t st) {
   Amg &A = s->amg;
-  TailDesc d{};
+  TailDesc<T> d{};
   d.nlev = (int)A.levels.size() - lvl;
   if (d.nlev > kTailLevels) fail(VAG_ECUDA, "AMG: too many levels below the tail start");
   for (int k = 0; k < d.nlev; ++k) {
     AmgLevel &L = A.levels[lvl + k];
-    d.lv[k] = TailLevel{L.d_sys_start, L.rowptr, L.col, L.agg, L.mptr, L.mem, L.val32, L.sinv32,
-                        L.inv32, L.any_term ? L.inv_off : nullptr, L.x32, L.b32, L.t32};
+    const LV<T> v = lv<T>(s, L);
+    d.lv[k] = TailLevel<T>{L.d_sys_start, L.d_nz_start, L.rowptr, L.col, L.agg, L.mptr, L.mem, v.val, v.sinv,
+                           v.inv, L.any_term ? L.inv_off : nullptr, v.x, v.b};
   }
-  k_vcycle_tail32<<<s->seg.n_sys, 1024, 0, st>>>(d);
+  const size_t smem = A.tail_smem[sizeof(T) == 4 ? 1 : 0];
+  d.smem = (unsigned)smem;
+  launch_pdl(k_vcycle_tail<T>, s->seg.n_sys, kTailThreads, smem, st, d, s->status);
   note_launches(1);
 }
 
+// x = V(b): one V(2,2) cycle from a zero initial guess.  Systems that end at
+// this level are solved exactly; the others are smoothed, restricted,
+// corrected from the next level and smoothed again.  On coarse levels the
+// first sweep t = omega D_l1^-1 b has already been made by the restriction
+// that produced b.
 template <class T>
 static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
   Amg &A = s->amg;
   AmgLevel &L = A.levels[lvl];
-  if (sizeof(T) == 4 && lvl > 0 && lvl == A.tail_start) {   // b, x are this level's b32, x32
-    tail32(s, lvl, st);
+  if (lvl > 0 && lvl == A.tail_start) {   // b, x are this level's own b, x
+    tail<T>(s, lvl, st);
     return;
   }
   const LV<T> v = lv<T>(s, L);
   const int n = L.n;
   const int g = grid_for(n, TB);
   if (L.any_term) {
-    k_dense_apply<T><<<s->seg.n_sys, 64, 0, st>>>(L.d_sys_start, L.inv_off, v.inv, b, x);
+    launch_pdl(k_dense_apply<T>, s->seg.n_sys, 64, 0, st, (const int *)L.d_sys_start, (const long long *)L.inv_off,
+               v.inv, b, x);
     note_launches(1);
   }
   if (L.all_term) return;
   AmgLevel &C = A.levels[lvl + 1];
   const LV<T> c = lv<T>(s, C);
-  // level 0: sliced ELL, one thread per row; coarser levels: CSR, 8 lanes per row
-  const int g8 = grid_for(n, 32);
-  auto sweep = [&](const T *xin, T *xout) {
-    if (lvl == 0)
-      k_jac_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, v.sinv, b, xin, xout, L.skip);
-    else
-      k_jac_csr8<T><<<g8, 256, 0, st>>>(n, L.rowptr, L.col, v.val, v.sinv, b, xin, xout, L.skip);
-  };
-  // pre-smoothing: two damped Jacobi sweeps from x = 0
-  k_jac_first<T><<<g, TB, 0, st>>>(n, b, v.sinv, v.t);
-  sweep(v.t, x);
-  // residual, restricted to the coarse level (t is free again)
-  if (lvl == 0)
-    k_resid_sell<T><<<g, TB, 0, st>>>(n, L.rowptr, L.slice_ptr, L.scol, v.sval, b, x, v.t);
-  else
-    k_resid_csr8<T><<<g8, 256, 0, st>>>(n, L.rowptr, L.col, v.val, b, x, v.t);
-  k_restrict<T><<<grid_for(C.n, TB), TB, 0, st>>>(C.n, L.mptr, L.mem, v.t, c.b);
-  note_launches(4);
+  constexpr int LN = row_lanes<T>();
+  const int gL = grid_for(n, 256 / LN);   // LN lanes per row
+  if (lvl == 0) {
+    // level 0: sliced ELL, one thread per row
+    launch_pdl(k_jac_first<T>, g, TB, 0, st, n, b, v.sinv, v.t);
+    launch_pdl(k_jac_sell<T>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+               v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
+    launch_pdl(k_resid_sell<T>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
+               (const int *)L.scol, v.sval, b, (const T *)x, v.t);
+    launch_pdl(k_restrict_first<T>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
+               (const T *)v.t, c.sinv, c.b, c.t);
+    note_launches(4);
+  } else {
+    // coarse levels: CSR, 8 lanes per row; residual and restriction fused
+    launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
+               (const T *)v.t, x, (const uint8_t *)L.skip);
+    launch_pdl(k_resid_restrict8<T>, grid_for(C.n, 8), 256, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
+               (const int *)L.rowptr, (const int *)L.col, v.val, b, (const T *)x, c.sinv, c.b, c.t);
+    note_launches(2);
+  }
   vcycle<T>(s, lvl + 1, c.b, c.x, st);
-  k_prolong<T><<<g, TB, 0, st>>>(n, L.agg, c.x, x);
-  // post-smoothing: two sweeps
-  sweep(x, v.t);
-  sweep(v.t, x);
-  note_launches(3);
+  // post-smoothing: two sweeps (on coarse levels the first one applies the
+  // coarse correction as it reads x)
+  if (lvl == 0) {
+    launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, x);
+    launch_pdl(k_jac_sell<T>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+               v.sval, v.sinv, b, (const T *)x, v.t, (const uint8_t *)L.skip);
+    launch_pdl(k_jac_sell<T>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+               v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
+    note_launches(3);
+  } else {
+    launch_pdl(k_prolong_jac8<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
+               (const T *)x, (const int *)L.agg, (const T *)c.x, v.t, (const uint8_t *)L.skip);
+    launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
+               (const T *)v.t, x, (const uint8_t *)L.skip);
+    note_launches(2);
+  }
 }
 
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st) {
@@ -867,9 +1232,9 @@ void amg_apply(System *s, const double *r, double *z, cudaStream_t st) {
   }
   AmgLevel &L0 = A.levels[0];
   const int n = L0.n;
-  k_to_f32<<<grid_for(n, TB), TB, 0, st>>>(n, r, L0.b32);
+  launch_pdl(k_to_f32, grid_for(n, TB), TB, 0, st, (int64_t)n, r, L0.b32);
   vcycle<float>(s, 0, L0.b32, L0.x32, st);
-  k_to_f64<<<grid_for(n, TB), TB, 0, st>>>(n, L0.x32, z);
+  launch_pdl(k_to_f64, grid_for(n, TB), TB, 0, st, n, (const float *)L0.x32, z);
   note_launches(2);
 }
 

@@ -201,6 +201,7 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
     s->mu = props->mu;
     VAG_CUDA(cudaEventCreate(&s->ev0));
     VAG_CUDA(cudaEventCreate(&s->ev1));
+    trace_mark(s->ctx->stream, "start");
     s->status = sys_alloc<int>(s, 4);
     s->xyz = upload(s, mesh->xyz, 3 * (size_t)s->nv, mem, "xyz");
     s->cell_nodes = upload(s, mesh->cell_nodes, 8 * (size_t)s->nc, mem, "cell_nodes");
@@ -217,10 +218,15 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
     g.cell_start = {0, s->nc};
     g.dir_start = {0, s->nd};
     upload_segments(s);
+    trace_mark(s->ctx->stream, "upload");
     symbolic_phase(s);
+    trace_mark(s->ctx->stream, "symbolic phase");
     build_tiles(s);
     build_sell(s);
+    trace_mark(s->ctx->stream, "row tiles + SELL structure");
     numeric_phase(s);
+    trace_mark(s->ctx->stream, "numeric phase");
+    trace_report("vag_assemble");
   });
   if (st != VAG_OK) {
     destroy_system(sys.release());
@@ -404,12 +410,15 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_AMG)
       fail(VAG_EINVAL, "preconditioner not available in this build");
     use_device(s->ctx);
+    trace_mark(s->ctx->stream, "start");
     // VAG_MIXED: Jacobi -> FP64 refinement around FP32 CG; AMG -> FP64 CG
     // preconditioned by an FP32 copy of the AMG hierarchy
     if (opts->precision == VAG_MIXED && opts->precond == VAG_PC_JACOBI) mixed_solve(s, opts, inf);
     else pcg_solve(s, opts, inf);
     copy_out(s, u_out, s->u, (size_t)s->n_cv, opts->mem);
+    trace_mark(s->ctx->stream, "copy out");
     VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+    trace_report("vag_solve");
     if (inf->status == VAG_EBREAKDOWN) fail(VAG_EBREAKDOWN, "CG breakdown: p^T A p <= 0 or NaN");
     if (inf->status == VAG_ENOTCONVERGED)
       fail(VAG_ENOTCONVERGED, "CG reached maxit above rtol (last iterate written)");
@@ -457,6 +466,7 @@ vag_status vag_transport(vag_system *sys, const vag_transport_opts *o, double *c
     if (!(o->cfl > 0.0) && !(o->dt > 0.0)) fail(VAG_EINVAL, "give cfl > 0 or dt > 0");
     use_device(s->ctx);
     cudaStream_t st = s->ctx->stream;
+    trace_mark(st, "start");
     const size_t n = s->n_cv;
     // stage porosities, cbar and c
     if (!o->phi_m || (s->nf && !o->phi_f) || !o->cbar) fail(VAG_EINVAL, "null porosity or cbar");
@@ -481,7 +491,9 @@ vag_status vag_transport(vag_system *sys, const vag_transport_opts *o, double *c
     if (o->mem == VAG_MEM_HOST)
       VAG_CUDA(cudaMemcpyAsync(c_inout, cdev, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     VAG_CUDA(cudaFreeAsync(stage, st));
+    trace_mark(st, "copy out");
     VAG_CUDA(cudaStreamSynchronize(st));
+    trace_report("vag_transport");
   });
 }
 

@@ -1,5 +1,9 @@
 // Shared device utilities: budget-checked allocation, exclusive scan, status.
 #include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
 
 #include "vag_internal.cuh"
 
@@ -12,6 +16,49 @@ void note_launches(unsigned long long n) {
   if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------ trace ---
+// With the environment variable VAG_TRACE set, the phases of each API call
+// are marked with a device event and a host clock reading on the call's
+// stream, and printed to stderr when the call ends (device time between
+// consecutive marks, and host time spent issuing them).  Off by default;
+// marks are skipped while a graph is being captured.
+namespace {
+struct TraceMark {
+  const char *label;
+  cudaEvent_t ev;
+  std::chrono::steady_clock::time_point host;
+};
+thread_local std::vector<TraceMark> t_marks;
+bool trace_on() {
+  static const bool on = std::getenv("VAG_TRACE") != nullptr;
+  return on;
+}
+}  // namespace
+
+bool trace_enabled() { return trace_on(); }
+
+void trace_mark(cudaStream_t st, const char *label) {
+  if (!trace_on() || t_capturing) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, st);
+  t_marks.push_back({label, e, std::chrono::steady_clock::now()});
+}
+
+void trace_report(const char *call) {
+  if (!trace_on() || t_marks.empty()) return;
+  cudaEventSynchronize(t_marks.back().ev);
+  std::fprintf(stderr, "[vag trace] %s\n", call);
+  for (size_t i = 1; i < t_marks.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t_marks[i - 1].ev, t_marks[i].ev);
+    const double host = std::chrono::duration<double, std::milli>(t_marks[i].host - t_marks[i - 1].host).count();
+    std::fprintf(stderr, "  %-34s device %9.3f ms   host %9.3f ms\n", t_marks[i].label, ms, host);
+  }
+  for (auto &m : t_marks) cudaEventDestroy(m.ev);
+  t_marks.clear();
+}
 
 void *ctx_alloc(Ctx *c, size_t bytes) {
   void *p = nullptr;

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <functional>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "vag.h"
@@ -46,6 +47,7 @@ enum : int {
   ST_NONPOSITIVE = 256,    // a non-positive diagonal / porous volume
   ST_ISOLATED = 512,       // an unknown coupled to nothing (no diagonal)
   ST_NO_SLOT = 1024,       // a contribution without a CSR slot
+  ST_TAIL_SMEM = 2048,     // a system's tail levels exceed the shared-memory plan
 };
 
 constexpr int kMaxRowWidth = 160;   // unique columns of one eliminated row
@@ -88,6 +90,8 @@ struct AmgLevel {
   double *sinv = nullptr;          // [n] smoother scaling 1 / sum_j |a_ij| (l1-Jacobi)
   std::vector<int> sys_start;      // host, n_sys+1: first row of each system
   int *d_sys_start = nullptr;
+  std::vector<int> nz_start;       // host, n_sys+1: first nonzero of each system
+  int *d_nz_start = nullptr;
   int *agg = nullptr;              // [n] aggregate (row of the next level) or -1
   // systems that end their hierarchy at this level (at most kDenseMax rows)
   // are solved densely here: per-row skip mask and dense inverses
@@ -99,7 +103,7 @@ struct AmgLevel {
   int nc = 0;
   int *mptr = nullptr, *mem = nullptr;   // members of each aggregate, sorted
   double *x = nullptr, *b = nullptr, *t = nullptr;   // V-cycle work vectors
-  // sliced-ELL copy of the level (coarse levels; level 0 uses the system's)
+  // sliced-ELL copy of level 0 (the system's own); coarse levels use CSR
   int *slice_ptr = nullptr, *scol = nullptr;
   double *sval = nullptr;
   float *sval32 = nullptr;
@@ -114,7 +118,8 @@ struct Amg {
   size_t bytes = 0;
   bool built = false;
   bool f32 = false;                // V-cycle in FP32
-  int tail_start = -1;             // FP32: first level run by the one-kernel tail
+  int tail_start = -1;             // first level run by the one-kernel tail
+  size_t tail_smem[2] = {0, 0};    // its dynamic shared memory (FP64, FP32)
   float *sval32 = nullptr;         // FP32 sliced-ELL values of A (finest level)
 };
 
@@ -256,6 +261,34 @@ T *sys_alloc(System *s, size_t n) {
 void sys_free_all(System *s);
 
 // ----------------------------------------------------------- utilities ----
+// Programmatic dependent launch (sm_90 and later): a kernel launched with
+// launch_pdl may be scheduled while its predecessor in the stream finishes.
+// It may read data that no kernel of the current sequence writes (matrix
+// entries, index arrays) at once, and must call pdl_wait() before touching
+// anything a predecessor produces; pdl_wait() returns when the predecessor
+// has completed and its writes are visible.  pdl_trigger() (always after
+// pdl_wait()) lets the next kernel be scheduled early.  Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                       Args &&...args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  if (e != cudaSuccess) fail(VAG_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
 // Exclusive scan of n int32 values: out[0..n] (out[n] = total).  Returns the
 // total (synchronises the stream).
 int scan_exclusive(const int *in, int *out, int n, cudaStream_t st, bool want_total = true);
@@ -269,6 +302,11 @@ void note_launches(unsigned long long n);
 // graph launch counts its nodes instead)
 void set_capturing(bool on);
 unsigned long long launches_so_far();
+// phase trace, active only with the environment variable VAG_TRACE set
+// (labels must be string literals)
+bool trace_enabled();
+void trace_mark(cudaStream_t st, const char *label);
+void trace_report(const char *call);
 
 // ------------------------------------------------------------- phases -----
 void symbolic_phase(System *s);
@@ -290,9 +328,6 @@ void sell_values_scaled_f32(System *s, const double *scale, float *out);
 void sell_values_f32(System *s, float *out);
 int64_t sell_structure(cudaStream_t st, int n, const int *rowptr, const int *col, int **slice_ptr_out,
                        int **scol_out, const std::function<void *(size_t)> &alloc);
-template <class T>
-void sell_fill(cudaStream_t st, int n, const int *rowptr, const int *col, const double *val, const int *slice_ptr,
-               T *sval);
 void solve_infos(const System *s, vag_solve_info *infos);
 void recover_cells_and_fluxes(System *s);
 void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_transport_info *info,

@@ -33,8 +33,10 @@ __global__ void __launch_bounds__(NT) k_spmv(const int *__restrict__ rowptr, con
                                              int with_dot) {
   const int t = blockIdx.x;
   const int sys = tl.sys[t];
-  if (with_dot && ks[sys].done) return;
   const int r0 = tl.row0[t], r1 = tl.row1[t];
+  pdl_wait();
+  pdl_trigger();
+  if (with_dot && ks[sys].done) return;
   double dp = 0.0;
   for (int row = r0 + threadIdx.x; row < r1; row += NT) {
     const int len = rowptr[row + 1] - rowptr[row];
@@ -233,9 +235,11 @@ __global__ void __launch_bounds__(NT) k_update_m(double *__restrict__ x, double 
                                                  double *partials, unsigned *counter, KrylovScalars *ks, int *n_done) {
   const int t = blockIdx.x;
   const int sys = tl.sys[t];
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  pdl_wait();
+  pdl_trigger();
   if (ks[sys].done) return;
   const double alpha = ks[sys].alpha;
-  const int r0 = tl.row0[t], r1 = tl.row1[t];
   double rr = 0.0;
   for (int i = r0 + threadIdx.x; i < r1; i += NT) {
     x[i] = fma(alpha, p[i], x[i]);
@@ -261,8 +265,10 @@ __global__ void __launch_bounds__(NT) k_rz(const double *__restrict__ r, const d
                                            double *partials, unsigned *counter, KrylovScalars *ks, int *n_done) {
   const int t = blockIdx.x;
   const int sys = tl.sys[t];
-  if (ks[sys].done) return;
   const int r0 = tl.row0[t], r1 = tl.row1[t];
+  pdl_wait();
+  pdl_trigger();
+  if (ks[sys].done) return;
   double rz = 0.0;
   for (int i = r0 + threadIdx.x; i < r1; i += NT) rz = fma(r[i], z[i], rz);
   double v[1] = {rz}, out[1];
@@ -278,9 +284,11 @@ __global__ void __launch_bounds__(NT) k_pdir_z(double *__restrict__ p, const dou
                                                const KrylovScalars *ks) {
   const int t = blockIdx.x;
   const int sys = tl.sys[t];
+  const int r0 = tl.row0[t], r1 = tl.row1[t];
+  pdl_wait();
+  pdl_trigger();
   if (ks[sys].done) return;
   const double beta = ks[sys].beta;
-  const int r0 = tl.row0[t], r1 = tl.row1[t];
   for (int i = r0 + threadIdx.x; i < r1; i += NT) p[i] = fma(beta, p[i], z[i]);
 }
 
@@ -372,8 +380,9 @@ void build_tiles(System *s) {
 }
 
 static void launch_spmv(System *s, const double *x, double *y, int with_dot, cudaStream_t st) {
-  k_spmv<<<s->seg.n_tiles, NT, 0, st>>>(s->rowptr, s->slice_ptr, s->scol, s->sval, x, y, tiles_of(s), s->partials,
-                                        s->counter, s->ks, s->n_done, with_dot);
+  launch_pdl(k_spmv, s->seg.n_tiles, NT, 0, st, (const int *)s->rowptr, (const int *)s->slice_ptr,
+             (const int *)s->scol, (const double *)s->sval, x, y, tiles_of(s), s->partials, s->counter, s->ks,
+             s->n_done, with_dot);
   note_launches(1);
 }
 
@@ -405,10 +414,12 @@ static void pcg_iteration_amg(System *s, cudaStream_t st) {
   const Tiles tl = tiles_of(s);
   const int nt = s->seg.n_tiles;
   launch_spmv(s, s->kp, s->kq, 1, st);
-  k_update_m<<<nt, NT, 0, st>>>(s->kx, s->kr, s->kp, s->kq, tl, s->partials, s->counter, s->ks, s->n_done);
+  launch_pdl(k_update_m, nt, NT, 0, st, s->kx, s->kr, (const double *)s->kp, (const double *)s->kq, tl, s->partials,
+             s->counter, s->ks, s->n_done);
   amg_apply(s, s->kr, s->kz, st);
-  k_rz<<<nt, NT, 0, st>>>(s->kr, s->kz, tl, s->partials, s->counter, s->ks, s->n_done);
-  k_pdir_z<<<nt, NT, 0, st>>>(s->kp, s->kz, tl, s->ks);
+  launch_pdl(k_rz, nt, NT, 0, st, (const double *)s->kr, (const double *)s->kz, tl, s->partials, s->counter, s->ks,
+             s->n_done);
+  launch_pdl(k_pdir_z, nt, NT, 0, st, s->kp, (const double *)s->kz, tl, (const KrylovScalars *)s->ks);
   note_launches(3);
 }
 
@@ -434,6 +445,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   if (amg) {
     if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
     amg_setup(s, o->precision == VAG_MIXED);
+    trace_mark(st, "AMG setup");
     VAG_CUDA(cudaEventRecord(s->ev1, st));
     VAG_CUDA(cudaEventSynchronize(s->ev1));
     cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);
@@ -450,6 +462,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
     note_launches(1);
   }
   VAG_CHECK_LAUNCH();
+  trace_mark(st, "CG start (r0, z0)");
   const int chunk = 16;
   cudaGraphExec_t &gexec = amg ? s->pcg_graph_amg : s->pcg_graph;
   if (amg && gexec) {   // the hierarchy (and its pointers) is rebuilt every solve
@@ -471,6 +484,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
     VAG_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
     cudaGraphDestroy(graph);
     if (amg) s->amg_graph_nodes = nodes;
+    trace_mark(st, "graph capture + instantiate");
   }
   const unsigned long long per_launch = amg ? s->amg_graph_nodes : 3ull * chunk;
   const int max_chunks = (o->maxit + chunk - 1) / chunk;
@@ -487,10 +501,12 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
       VAG_CUDA(cudaGraphLaunch(gexec, st));
       note_launches(per_launch);
     }
+    trace_mark(st, "CG iterations (graph chunks)");
     launch_spmv(s, s->kx, s->kq, 0, st);
     k_resid2<<<nt, NT, 0, st>>>(s->rhs, s->kq, tl, s->partials, s->counter, s->ks);
     note_launches(1);
     VAG_CHECK_LAUNCH();
+    trace_mark(st, "true residual");
     if (attempt == 3) break;
     VAG_CUDA(cudaMemcpyAsync(s->ks_host, s->ks, sizeof(KrylovScalars) * ns, cudaMemcpyDeviceToHost, st));
     VAG_CUDA(cudaStreamSynchronize(st));
@@ -541,6 +557,7 @@ void finish_solve(System *s, vag_solve_info *info, bool mixed) {
   note_launches(1);
   VAG_CHECK_LAUNCH();
   recover_cells_and_fluxes(s);
+  trace_mark(st, "scatter + cell recovery + fluxes");
   VAG_CUDA(cudaEventRecord(s->ev1, st));
   VAG_CUDA(cudaMemcpyAsync(s->ks_host, s->ks, sizeof(KrylovScalars) * ns, cudaMemcpyDeviceToHost, st));
   VAG_CUDA(cudaStreamSynchronize(st));

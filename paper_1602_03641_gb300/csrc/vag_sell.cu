@@ -87,35 +87,11 @@ int64_t sell_structure(cudaStream_t st, int n, const int *rowptr, const int *col
   return total;
 }
 
-template <class T>
-void sell_fill(cudaStream_t st, int n, const int *rowptr, const int *col, const double *val, const int *slice_ptr,
-               T *sval) {
-  if (n <= 0) return;
-  k_sell_vals<T><<<grid_for(n, TB), TB, 0, st>>>(n, rowptr, val, nullptr, col, slice_ptr, sval);
-  note_launches(1);
-  VAG_CHECK_LAUNCH();
-}
-template void sell_fill<double>(cudaStream_t, int, const int *, const int *, const double *, const int *, double *);
-template void sell_fill<float>(cudaStream_t, int, const int *, const int *, const double *, const int *, float *);
-
 void build_sell(System *s) {
-  cudaStream_t st = s->ctx->stream;
-  const int n = s->n_rows;
-  s->n_slices = (n + 31) / 32;
-  s->slice_ptr = sys_alloc<int>(s, (size_t)s->n_slices + 1);
-  int *width;
-  VAG_CUDA(cudaMallocAsync(&width, sizeof(int) * ((size_t)s->n_slices + 1), st));
-  k_slice_width<<<grid_for(s->n_slices, TB), TB, 0, st>>>(n, s->n_slices, s->rowptr, width);
-  note_launches(1);
-  VAG_CHECK_LAUNCH();
-  s->sell_nnz = scan_exclusive(width, s->slice_ptr, s->n_slices, st);
-  VAG_CUDA(cudaFreeAsync(width, st));
-  s->scol = sys_alloc<int>(s, (size_t)s->sell_nnz);
-  s->sval = sys_alloc<double>(s, (size_t)s->sell_nnz);
-  k_sell_cols<<<grid_for(n, TB), TB, 0, st>>>(n, s->rowptr, s->col, s->slice_ptr, s->scol);
-  k_sell_pad<<<grid_for((int64_t)s->n_slices * 32, TB), TB, 0, st>>>(n, s->rowptr, s->slice_ptr, s->scol);
-  note_launches(2);
-  VAG_CHECK_LAUNCH();
+  s->n_slices = (s->n_rows + 31) / 32;
+  s->sell_nnz = sell_structure(s->ctx->stream, s->n_rows, s->rowptr, s->col, &s->slice_ptr, &s->scol,
+                               [s](size_t bytes) { return sys_alloc_bytes(s, bytes); });
+  s->sval = sys_alloc<double>(s, (size_t)std::max<int64_t>(s->sell_nnz, 1));
 }
 
 void sell_values(System *s) {

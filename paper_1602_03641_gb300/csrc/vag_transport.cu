@@ -360,6 +360,7 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
   k_set_dir<<<grid_for(s->nd, TB), TB, 0, st>>>(s->nd, s->dir_nodes, cbar, c0);
   note_launches(1);
   VAG_CHECK_LAUNCH();
+  trace_mark(st, "porous volumes + CFL + upwind map");
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   const int gs = grid_for(n, TB);
   // steps in CUDA graphs of kStepChunk launches (an even count: the chunk
@@ -395,6 +396,7 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     std::swap(c0, c1);
   }
   VAG_CHECK_LAUNCH();
+  trace_mark(st, "explicit steps");
   VAG_CUDA(cudaEventRecord(s->ev1, st));
   VAG_CUDA(cudaMemcpyAsync(c_dev, c0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   s->dts_host.resize(2 * (size_t)ns);
