@@ -20,6 +20,7 @@
 //             hierarchy therefore depends on that system alone.
 // Apply: a V(2,2) cycle with l1-Jacobi sweeps before and after the coarse
 // correction; it is a fixed symmetric linear operator, as CG needs.
+#include <climits>
 #include <cstdio>
 
 #include "vag_internal.cuh"
@@ -113,8 +114,9 @@ __device__ __forceinline__ unsigned long long node_key(int i, int8_t st, const i
 
 __global__ void k_mis_max1(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
                            const uint8_t *__restrict__ strong, const int8_t *__restrict__ state,
-                           const int *__restrict__ sys_start, int n_sys, unsigned long long *m1) {
+                           const int *__restrict__ sys_start, int n_sys, unsigned long long *m1, int *undecided) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *undecided = 0;   // counted by this round's k_mis_max2_decide
   if (i >= n) return;
   unsigned long long m = node_key(i, state[i], sys_start, n_sys);
   for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
@@ -214,53 +216,133 @@ __global__ void k_sort_members(int nc, const int *__restrict__ mptr, int *mem) {
   }
 }
 
-// One coarse row of A_c = P^T A P: the entries of the members' rows (members
-// in row order, entries in CSR order) are summed per coarse column in a
-// thread-local open-addressing table; columns are emitted in order of first
-// appearance, so the sums and their order are deterministic.
+// One coarse row of A_c = P^T A P per warp.  The entries of the members'
+// rows (members in row order, entries in CSR order: the sequence p) are read
+// 32 at a time; each entry finds its coarse column's slot in the warp's
+// shared-memory hash table, lanes that hit the same slot are grouped
+// (__match_any_sync) and the lowest of them adds their values to the slot in
+// lane order.  Every coarse entry is therefore the sum of its contributions
+// in sequence order, whatever the scheduling; the row is emitted sorted by
+// coarse column.
 constexpr int kHash = 256;
-__global__ void __launch_bounds__(64) k_coarse_build(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
-                                                     const int *__restrict__ rowptr, const int *__restrict__ col,
-                                                     const double *__restrict__ val, const int *__restrict__ agg,
-                                                     int *tcol, double *tval, int *cnt, double *cdinv, int *status) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I >= nc) return;
-  int keys[kHash];
-  double sums[kHash];
-  unsigned char slot_of[kCoarseWidth];
-  for (int h = 0; h < kHash; ++h) keys[h] = -1;
-  int n = 0;
+constexpr int kBuildWarps = 8;
+__global__ void __launch_bounds__(32 * kBuildWarps) k_coarse_build(int nc, const int *__restrict__ mptr,
+                                                                   const int *__restrict__ mem,
+                                                                   const int *__restrict__ rowptr,
+                                                                   const int *__restrict__ col,
+                                                                   const double *__restrict__ val,
+                                                                   const int *__restrict__ agg, int *tcol,
+                                                                   double *tval, int *cnt, double *cdinv,
+                                                                   int *status) {
+  __shared__ int keys[kBuildWarps][kHash];
+  __shared__ double sums[kBuildWarps][kHash];
+  __shared__ double vals[kBuildWarps][32];
+  __shared__ int nuniq[kBuildWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int I = blockIdx.x * kBuildWarps + w;
+  if (I >= nc) return;   // whole warps leave together
+  int *K = keys[w];
+  double *S = sums[w];
+  for (int h = lane; h < kHash; h += 32) {
+    K[h] = -1;
+    S[h] = 0.0;
+  }
+  if (lane == 0) nuniq[w] = 0;
+  __syncwarp();
   bool overflow = false;
   for (int p = mptr[I]; p < mptr[I + 1]; ++p) {
     const int i = mem[p];
-    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-      const int J = agg[col[k]];
-      if (J < 0) continue;
-      unsigned h = ((unsigned)J * 2654435761u) & (kHash - 1);
-      while (keys[h] != -1 && keys[h] != J) h = (h + 1) & (kHash - 1);
-      if (keys[h] == J) {
-        sums[h] += val[k];
-      } else if (n < kCoarseWidth) {
-        keys[h] = J;
-        sums[h] = val[k];
-        slot_of[n++] = (unsigned char)h;
-      } else {
-        overflow = true;
+    const int kb = rowptr[i], ke = rowptr[i + 1];
+    for (int c = kb; c < ke; c += 32) {
+      const int k = c + lane;
+      const int J = k < ke ? agg[col[k]] : -1;
+      const double v = k < ke ? val[k] : 0.0;
+      int slot = -1;
+      if (J >= 0) {
+        unsigned h = ((unsigned)J * 2654435761u) & (kHash - 1);
+        for (int probe = 0; probe < kHash; ++probe, h = (h + 1) & (kHash - 1)) {
+          const int cur = ((volatile int *)K)[h];
+          if (cur == J) { slot = (int)h; break; }
+          if (cur == -1) {
+            const int old = atomicCAS(&K[h], -1, J);
+            if (old == -1) { atomicAdd(&nuniq[w], 1); slot = (int)h; break; }
+            if (old == J) { slot = (int)h; break; }
+          }
+        }
+        if (slot < 0) overflow = true;
       }
+      vals[w][lane] = v;
+      __syncwarp();
+      const unsigned grp = __match_any_sync(0xffffffffu, slot >= 0 ? slot : -1 - lane);
+      if (slot >= 0 && lane == __ffs(grp) - 1) {
+        double acc = S[slot];
+        for (unsigned m = grp; m; m &= m - 1) acc += vals[w][__ffs(m) - 1];
+        S[slot] = acc;
+      }
+      __syncwarp();
     }
   }
-  if (overflow) atomicOr(status, ST_ROW_OVERFLOW);
-  double d = 0.0;
-  const size_t base = (size_t)I * kCoarseWidth;
-  for (int q = 0; q < n; ++q) {
-    const int h = slot_of[q];
-    tcol[base + q] = keys[h];
-    tval[base + q] = sums[h];
-    if (keys[h] == I) d = sums[h];
+  const int nu = nuniq[w];
+  if (__any_sync(0xffffffffu, overflow) || nu > kCoarseWidth) {
+    if (lane == 0) {
+      atomicOr(status, ST_ROW_OVERFLOW);
+      cnt[I] = 0;
+    }
+    return;
   }
-  cnt[I] = n;
-  if (!(d > 0.0)) atomicOr(status, ST_NONPOSITIVE);
-  cdinv[I] = 1.0 / d;
+  // the distinct columns in ascending order: compact the (column, sum) pairs
+  // to the front of the table in place (a pair only moves left, past pairs
+  // already read), pad to a power of two and sort them (bitonic, by column)
+  int pos = 0;
+  for (int h0 = 0; h0 < kHash; h0 += 32) {
+    const int key = K[h0 + lane];
+    const double sum = S[h0 + lane];
+    const unsigned b = __ballot_sync(0xffffffffu, key >= 0);
+    __syncwarp();
+    if (key >= 0) {
+      const int q = pos + __popc(b & ((1u << lane) - 1u));
+      K[q] = key;
+      S[q] = sum;
+    }
+    pos += __popc(b);
+    __syncwarp();
+  }
+  int n2 = 32;
+  while (n2 < nu) n2 <<= 1;
+  for (int q = nu + lane; q < n2; q += 32) K[q] = INT_MAX;
+  __syncwarp();
+  for (int size = 2; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = lane; q < n2; q += 32) {
+        const int o = q ^ stride;
+        if (o > q) {
+          const bool up = (q & size) == 0;
+          const int a = K[q], b = K[o];
+          if ((a > b) == up) {
+            K[q] = b; K[o] = a;
+            const double t = S[q]; S[q] = S[o]; S[o] = t;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  const size_t base = (size_t)I * kCoarseWidth;
+  bool diag = false;
+  for (int q = lane; q < nu; q += 32) {
+    tcol[base + q] = K[q];
+    tval[base + q] = S[q];
+    if (K[q] == I) {
+      diag = true;
+      if (!(S[q] > 0.0)) atomicOr(status, ST_NONPOSITIVE);
+      cdinv[I] = 1.0 / S[q];
+    }
+  }
+  if (!__any_sync(0xffffffffu, diag) && lane == 0) {
+    atomicOr(status, ST_NONPOSITIVE);
+    cdinv[I] = 1.0 / 0.0;
+  }
+  if (lane == 0) cnt[I] = nu;
 }
 
 __global__ void k_coarse_compact(int nc, const int *__restrict__ tcol, const double *__restrict__ tval,
@@ -896,6 +978,7 @@ void amg_setup(System *s, bool f32) {
   L0.sell_nnz = s->sell_nnz;
   A.levels.push_back(L0);
   int *undecided = static_cast<int *>(alloc(sizeof(int)));
+  if (!s->amg_pin) VAG_CUDA(cudaMallocHost(&s->amg_pin, 4 * sizeof(int)));
   int *und_host = s->n_done_host;   // pinned int
   std::vector<uint8_t> term(ns);
   std::vector<long long> off(ns + 1);
@@ -946,20 +1029,20 @@ void amg_setup(System *s, bool f32) {
     k_strength<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, L.val, sd, L.skip, strong, state);
     note_launches(2);
     trace_mark(st, "level: terminal blocks + strength");
-    // MIS(2) rounds, three between polls (a round after the last decision
-    // changes nothing)
-    for (int it = 0; it < 64; it += 3) {
-      for (int r = 0; r < 3; ++r) {
-        VAG_CUDA(cudaMemsetAsync(undecided, 0, sizeof(int), st));
-        k_mis_max1<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, L.d_sys_start, ns, m1);
-        k_mis_max2_decide<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, m1, L.d_sys_start,
-                                                           ns, next, undecided);
-        note_launches(2);
-        VAG_CUDA(cudaMemcpyAsync(state, next, n, cudaMemcpyDeviceToDevice, st));
-      }
+    // MIS(2) rounds (state and next alternate), polled after 8 rounds and
+    // then every 4 (a round after the last decision changes nothing)
+    for (int r = 0, poll = 8; r < 64;) {
+      k_mis_max1<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, L.d_sys_start, ns, m1,
+                                                 undecided);
+      k_mis_max2_decide<<<grid_for(n, TB), TB, 0, st>>>(n, L.rowptr, L.col, strong, state, m1, L.d_sys_start,
+                                                         ns, next, undecided);
+      note_launches(2);
+      std::swap(state, next);
+      if (++r < poll && r < 64) continue;
       VAG_CUDA(cudaMemcpyAsync(und_host, undecided, sizeof(int), cudaMemcpyDeviceToHost, st));
       VAG_CUDA(cudaStreamSynchronize(st));
       if (*und_host == 0) break;
+      poll += 4;
     }
     if (*und_host != 0) fail(VAG_ECUDA, "AMG: MIS(2) did not finish in 64 rounds");
     trace_mark(st, "level: MIS(2)");
@@ -982,8 +1065,8 @@ void amg_setup(System *s, bool f32) {
     VAG_CUDA(cudaMemsetAsync(cursor, 0, 4 * ((size_t)nc + 1), st));
     k_member_count<<<grid_for(n, TB), TB, 0, st>>>(n, L.agg, cnt);
     note_launches(1);
-    const int nmem = scan_exclusive(cnt, L.mptr, nc, st);
-    L.mem = static_cast<int *>(alloc(4 * (size_t)std::max(nmem, 1)));
+    scan_exclusive(cnt, L.mptr, nc, st, false);   // at most n members: no need to wait for the total
+    L.mem = static_cast<int *>(alloc(4 * (size_t)std::max(n, 1)));
     k_member_fill<<<grid_for(n, TB), TB, 0, st>>>(n, L.agg, L.mptr, cursor, L.mem);
     k_sort_members<<<grid_for(nc, TB), TB, 0, st>>>(nc, L.mptr, L.mem);
     note_launches(2);
@@ -998,11 +1081,21 @@ void amg_setup(System *s, bool f32) {
     VAG_CUDA(cudaMallocAsync(&tcol, 4 * (size_t)std::max(nc, 1) * kCoarseWidth, st));
     VAG_CUDA(cudaMallocAsync(&tval, 8 * (size_t)std::max(nc, 1) * kCoarseWidth, st));
     VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
-    k_coarse_build<<<grid_for(nc, 64), 64, 0, st>>>(nc, L.mptr, L.mem, L.rowptr, L.col, L.val, L.agg, tcol, tval, cnt,
-                                                     C.dinv, s->status);
+    k_coarse_build<<<grid_for(nc, kBuildWarps), 32 * kBuildWarps, 0, st>>>(nc, L.mptr, L.mem, L.rowptr, L.col, L.val,
+                                                                            L.agg, tcol, tval, cnt, C.dinv, s->status);
     note_launches(1);
-    C.nnz = scan_exclusive(cnt, C.rowptr, nc, st);
-    const int cst = read_status(s);
+    scan_exclusive(cnt, C.rowptr, nc, st, false);
+    C.d_sys_start = static_cast<int *>(alloc(4 * ((size_t)ns + 1)));
+    k_coarse_starts<<<grid_for(ns + 1, TB), TB, 0, st>>>(ns, L.d_sys_start, rscan, C.d_sys_start);
+    note_launches(1);
+    // one wait for the coarse nonzero count, the status and the row starts
+    C.sys_start.assign(ns + 1, 0);
+    VAG_CUDA(cudaMemcpyAsync(&s->amg_pin[0], C.rowptr + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VAG_CUDA(cudaMemcpyAsync(&s->amg_pin[1], s->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VAG_CUDA(cudaMemcpyAsync(C.sys_start.data(), C.d_sys_start, 4 * (ns + 1), cudaMemcpyDeviceToHost, st));
+    VAG_CUDA(cudaStreamSynchronize(st));
+    C.nnz = s->amg_pin[0];
+    const int cst = s->amg_pin[1];
     if (cst & ST_ROW_OVERFLOW) fail(VAG_EMESH, "AMG: a coarse row couples too many aggregates");
     if (cst & ST_NONPOSITIVE) fail(VAG_EINVAL, "AMG: non-positive coarse diagonal");
     C.col = static_cast<int *>(alloc(4 * (size_t)std::max<int64_t>(C.nnz, 1)));
@@ -1012,14 +1105,7 @@ void amg_setup(System *s, bool f32) {
     VAG_CUDA(cudaFreeAsync(tcol, st));
     VAG_CUDA(cudaFreeAsync(tval, st));
     trace_mark(st, "level: Galerkin product");
-    C.d_sys_start = static_cast<int *>(alloc(4 * ((size_t)ns + 1)));
-    k_coarse_starts<<<grid_for(ns + 1, TB), TB, 0, st>>>(ns, L.d_sys_start, rscan, C.d_sys_start);
-    note_launches(1);
-    C.sys_start.assign(ns + 1, 0);
-    VAG_CUDA(cudaMemcpyAsync(C.sys_start.data(), C.d_sys_start, 4 * (ns + 1), cudaMemcpyDeviceToHost, st));
-    VAG_CUDA(cudaStreamSynchronize(st));
     A.levels.push_back(C);   // invalidates L
-    trace_mark(st, "level: coarse row starts");
   }
   // work vectors per level (x, b, t) and the l1 smoother scaling
   for (auto &L : A.levels) {

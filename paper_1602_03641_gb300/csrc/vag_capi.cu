@@ -96,6 +96,7 @@ void destroy_system(vag_system *sys) {
   amg_free(s);
   if (s->ks_host) cudaFreeHost(s->ks_host);
   if (s->n_done_host) cudaFreeHost(s->n_done_host);
+  if (s->amg_pin) cudaFreeHost(s->amg_pin);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
   sys_free_all(s);

@@ -217,6 +217,7 @@ struct System {
   KrylovScalars *ks_host = nullptr;    // pinned mirror [n_sys]
   int *n_done = nullptr;               // systems converged (device)
   int *n_done_host = nullptr;          // pinned mirror
+  int *amg_pin = nullptr;              // pinned, 4 ints: AMG setup read-backs
   Segments seg;
   cudaGraphExec_t pcg_graph = nullptr;
   int pcg_graph_chunk = 0;
