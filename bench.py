@@ -57,8 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=N_CELLS_EDGE, help="mesh edge (profiling cases only)")
-    ap.add_argument("--workload", default="scale64", choices=["scale64", "batch", "serve"],
-                    help="scale64: the headline line; batch / serve: the batched and served workloads")
+    ap.add_argument("--workload", default="scale64", choices=["scale64", "batch", "serve", "mixed128"],
+                    help="scale64: the headline line; batch / serve / mixed128: the batched, served and "
+                         "mixed-precision workloads")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--requests", type=int, default=400)
     return ap.parse_args()
@@ -73,6 +74,18 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def fp64_peak_gflops():
+    """FP64 FMA peak of the GB300 from its unit counts and clock: 2 DFMA per
+    clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+    .avg.peak_sustained = 2) x 152 SMs x the maximum SM clock x 2 flops."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return 2 * 2 * 152 * mhz / 1e3
 
 
 class ClockSampler:
@@ -361,6 +374,96 @@ def serve_arm(args):
                       "results": lines}))
 
 
+def mixed128_arm(args):
+    """The mixed-precision workload: 128^3 jittered hex with a DFN of 50 seeded
+    rectangles at fracture/matrix ratios 1e2, 1e4, 1e6.  Per ratio: the FP64
+    and mixed solvers to a 1e-8 relative residual (FP64 residual in all of
+    them), each pressure compared with the FP64 AMG solve to 1e-12, then 1000
+    explicit transport steps; the hot kernels timed at this size (the CSR
+    and the transport map no longer fit the 129 MB L2)."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_1602_03641_gb300 as pkg
+    import vag_inputs as vi
+    torch.cuda.set_device(0)
+    n = 128 if args.n == N_CELLS_EDGE else args.n
+    ctx = pkg.Context(0)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    peak, peak_kind = measured_peaks()
+    fp64_peak = fp64_peak_gflops()
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for ratio in (1e2, 1e4, 1e6):
+        pb = vi.config_mixed128(n, ratio)
+        a = pkg.problem_arrays(pb, device=True)
+        s = ctx.assemble(a["xyz"], a["cell_nodes"], a["ff_nodes"], a["lambda_m"], a["lambda_f"], a["d_f"], a["mu"],
+                         a["dir_nodes"], a["dir_values"])
+        inf = s.info()
+        u_ref = torch.empty(inf.n_cv, dtype=torch.float64, device="cuda")
+        _, iref = s.solve(out=u_ref, precond=pkg.VAG_PC_AMG, rtol=1e-12, maxit=20000, raise_on_error=False)
+        nref = float(torch.linalg.vector_norm(u_ref))
+        res = {"n_rows": inf.n_rows, "nnz": inf.nnz, "n_ff": pb.n_ff, "reference_rel_residual": iref.rel_residual}
+        u = torch.empty_like(u_ref)
+        for name, prec, pc in (("fp64_amg", pkg.VAG_FP64, pkg.VAG_PC_AMG), ("mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG),
+                               ("fp64_jacobi", pkg.VAG_FP64, pkg.VAG_PC_JACOBI),
+                               ("mixed_jacobi", pkg.VAG_MIXED, pkg.VAG_PC_JACOBI)):
+            times = []
+            for rep in range(3):
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                _, info = s.solve(out=u, precision=prec, precond=pc, rtol=1e-8, maxit=50000, raise_on_error=False)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            err = float(torch.linalg.vector_norm(u - u_ref)) / nref
+            res[name] = {"ms": float(np.median(times)), "iterations": info.iterations, "refinements": info.outer,
+                         "rel_residual": info.rel_residual, "status": info.status, "rel_l2_vs_fp64_1e-12": err}
+        res["mixed_amg_over_fp64_amg"] = res["fp64_amg"]["ms"] / res["mixed_amg"]["ms"]
+        res["mixed_amg_over_fp64_jacobi"] = res["fp64_jacobi"]["ms"] / res["mixed_amg"]["ms"]
+        # 1000 transport steps on the mixed solve's fluxes
+        s.solve(out=u, precision=pkg.VAG_MIXED, precond=pkg.VAG_PC_AMG, rtol=1e-8, maxit=50000, raise_on_error=False)
+        c = torch.from_numpy(pb.c0()).cuda()
+        phm, phf, cb = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (pb.phi_m, pb.phi_f, pb.cbar))
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        tinf = s.transport(c, phm, phf, cb, n_steps=1000, cfl=0.9)
+        e1.record(stream)
+        e1.synchronize()
+        res["transport_1000_ms"] = e0.elapsed_time(e1)
+        res["transport_steps_ms"] = tinf.ms
+        inf = s.info()
+        nr, nz, ncv, nzt = inf.n_rows, inf.nnz, inf.n_cv, inf.nnz_transport
+        ks = {}
+        for key, kid, nbytes, flops in (
+                ("k_spmv", pkg.VAG_KERNEL_SPMV, nz * 12 + (nr + 1) * 4 + nr * 16, 2 * nz),
+                ("k_step", pkg.VAG_KERNEL_TRANSPORT_STEP, ncv * 28 + nzt * 12, 2 * nzt + ncv)):
+            ms = s.kernel_time(kid, 100)
+            ks[key] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6, "frac_hbm": nbytes / ms / 1e6 / peak,
+                       "frac_fp64": flops / ms / 1e6 / fp64_peak}
+        s.solve(out=u, precond=pkg.VAG_PC_AMG, rtol=1e-8, maxit=50000, raise_on_error=False)
+        ms = s.kernel_time(pkg.VAG_KERNEL_SMOOTH, 100)
+        nbytes = nz * 12 + (nr + 1) * 4 + nr * 32
+        ks["k_jac_sell<double>"] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6,
+                                    "frac_hbm": nbytes / ms / 1e6 / peak,
+                                    "frac_fp64": (2 * nz + 4 * nr) / ms / 1e6 / fp64_peak}
+        res["kernels"] = ks
+        out[f"{ratio:g}"] = res
+        s.close()
+        torch.cuda.empty_cache()
+    mid = out["10000"]
+    print(json.dumps({"metric": "mixed vs FP64 at 1e-8 relative residual (Darcy solve), 128^3 DFN",
+                      "value": mid["mixed_amg_over_fp64_amg"], "unit": "x (FP64 AMG time / mixed AMG time, ratio 1e4)",
+                      "n_gpus": 1, "higher_is_better": True, "dtype": "f64 outer / f32 inner", "data": "synthetic",
+                      "config": {"workload": f"mixed128: {n}^3 jittered hex, 50 seeded rectangles, ratios 1e2/1e4/1e6, "
+                                             "rtol 1e-8, 1000 transport steps", "hbm_peak_gbs": peak,
+                                 "hbm_peak_kind": peak_kind, "fp64_peak_tflops": fp64_peak / 1e3},
+                      "results": out}))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -371,6 +474,9 @@ def main():
         return
     if args.workload == "serve":
         serve_arm(args)
+        return
+    if args.workload == "mixed128":
+        mixed128_arm(args)
         return
     import torch
     import torch.distributed as dist
@@ -523,56 +629,53 @@ def main():
     cmp["mixed_over_fp64_jacobi"] = cmp["mixed_jacobi"]["solves_per_s"] / cmp["fp64_jacobi"]["solves_per_s"]
     cmp["mixed_over_fp64_amg"] = cmp["mixed_amg"]["solves_per_s"] / cmp["fp64_amg"]["solves_per_s"]
 
-    # kernel rooflines: SpMV of the eliminated system and one transport step,
-    # CUDA events on the stream the library launches on
+    # Hot kernels timed live on the workload's own data through the library's
+    # measurement hook (CUDA events on the library's stream): the CG product,
+    # one finest-level smoother sweep of the AMG V-cycle, one transport step.
+    # Share of the step = launches per step x mean launch time / step time.
     peak, peak_kind = measured_peaks()
+    fp64_peak = fp64_peak_gflops()
     s = ctx.assemble(d["xyz"], d["cn"], d["ffn"], d["lam"], d["lamf"], d["df"], pb.mu, d["dn"], d["dv"])
+    _, sinf = s.solve(out=u_dev, precond=precond, rtol=RTOL, maxit=100000)
+    with torch.cuda.stream(stream):
+        c_dev.copy_(d["c0"])
+    s.transport(c_dev, d["phm"], d["phf"], d["cb"], n_steps=TRANSPORT_STEPS, cfl=0.9)
     inf = s.info()
-    x = torch.rand(inf.n_rows, dtype=torch.float64, device=dev)
-    y = torch.empty_like(x)
-    L = pkg.lib()
-    for _ in range(20):
-        L.vag_spmv(s.h, x.data_ptr(), y.data_ptr(), pkg.VAG_MEM_DEVICE)
-    R = 400
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stream.synchronize()
-    e0.record(stream)
-    for _ in range(R):
-        L.vag_spmv(s.h, x.data_ptr(), y.data_ptr(), pkg.VAG_MEM_DEVICE)
-    e1.record(stream)
-    stream.synchronize()
-    spmv_ms = e0.elapsed_time(e1) / R
-    spmv_bytes = inf.nnz * 12 + (inf.n_rows + 1) * 4 + inf.n_rows * 16
-    s.solve(out=u_dev, precond=precond, rtol=RTOL, maxit=100000)
-    tms = {}
-    for nst in (20, 420):
-        with torch.cuda.stream(stream):
-            c_dev.copy_(d["c0"])
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ea.record(stream)
-        tinf = s.transport(c_dev, d["phm"], d["phf"], d["cb"], n_steps=nst, cfl=0.9)
-        eb.record(stream)
-        stream.synchronize()
-        tms[nst] = ea.elapsed_time(eb)
-    inf = s.info()
-    tstep_ms = (tms[420] - tms[20]) / 400
-    tstep_bytes = inf.n_cv * (8 + 8 + 8 + 4) + inf.nnz_transport * 12
+    reps = 400
+    its = sinf.iterations
+    n, nnz, ncv, nnzt = inf.n_rows, inf.nnz, inf.n_cv, inf.nnz_transport
+    kern = {}
+    def add(name, ms, per_step, nbytes, flops):
+        kern[name] = {"ms": ms, "launches_per_step": per_step, "share_of_step": per_step * ms / (tot / args.steps),
+                      "bytes": nbytes, "gbs": nbytes / ms / 1e6, "fp64_gflops": flops / ms / 1e6,
+                      "frac_hbm": nbytes / ms / 1e6 / peak, "frac_fp64": flops / ms / 1e6 / fp64_peak}
+    add("k_spmv (FP64 SELL q = A p)", s.kernel_time(pkg.VAG_KERNEL_SPMV, reps), its + 2,
+        nnz * 12 + (n + 1) * 4 + n * 16, 2 * nnz)
+    if args.precond == "amg":
+        add("k_jac_sell<double> (finest-level l1-Jacobi sweep)", s.kernel_time(pkg.VAG_KERNEL_SMOOTH, reps),
+            3 * (its + 1), nnz * 12 + (n + 1) * 4 + n * 32, 2 * nnz + 4 * n)
+    add("k_step (upwind transport step)", s.kernel_time(pkg.VAG_KERNEL_TRANSPORT_STEP, reps), TRANSPORT_STEPS,
+        ncv * 28 + nnzt * 12, 2 * nnzt + ncv)
     s.close()
-
+    dom = max(kern, key=lambda k: kern[k]["share_of_step"])
+    kd = kern[dom]
+    # the binding resource is the one the kernel uses the larger fraction of
+    if kd["frac_fp64"] >= kd["frac_hbm"]:
+        roof = {"kernel": dom, "bound": "alu", "achieved": kd["fp64_gflops"] / 1e3, "peak": fp64_peak / 1e3,
+                "unit": "TFLOP/s (FP64)", "frac": kd["frac_fp64"], "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x "
+                "max SM clock (ncu sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained)",
+                "secondary": {"bound": "hbm", "achieved": kd["gbs"], "peak": peak, "unit": "GB/s",
+                              "frac": kd["frac_hbm"], "peak_kind": peak_kind}}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": kd["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kd["frac_hbm"], "peak_kind": peak_kind,
+                "secondary": {"bound": "alu", "achieved": kd["fp64_gflops"] / 1e3, "peak": fp64_peak / 1e3,
+                              "unit": "TFLOP/s (FP64)", "frac": kd["frac_fp64"]}}
+    roof["traffic"] = ncu_traffic(dom)
+    roof["bytes_per_launch"] = kd["bytes"]
+    roof["launch_ms"] = kd["ms"]
+    spmv_gbs = kern["k_spmv (FP64 SELL q = A p)"]["gbs"]
     iters = [i[0].iterations for i in infos]
-    spmv_share = (statistics.mean(iters) + 1) * spmv_ms / (tot / args.steps)
-    trans_share = TRANSPORT_STEPS * tstep_ms / (tot / args.steps)
-    kern = {
-        "spmv_csr_f64": {"ms": spmv_ms, "bytes": spmv_bytes, "gbs": spmv_bytes / spmv_ms / 1e6,
-                         "share_of_step": spmv_share},
-        "transport_step": {"ms": tstep_ms, "bytes": tstep_bytes, "gbs": tstep_bytes / tstep_ms / 1e6,
-                           "share_of_step": trans_share},
-    }
-    dom = "spmv_csr_f64" if spmv_share >= trans_share else "transport_step"
-    ach = kern[dom]["gbs"]
-    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "peak_kind": peak_kind, "traffic": ncu_traffic(dom),
-            "bytes_per_launch": kern[dom]["bytes"]}
 
     if rank == 0:
         line = {
@@ -590,7 +693,7 @@ def main():
                           "of_which_precond_setup": infos[-1][0].ms_setup,
                           "of_which_krylov_and_recovery": infos[-1][0].ms_solve,
                           "of_which_transport_steps": infos[-1][1].ms},
-            "spmv_gbs": kern["spmv_csr_f64"]["gbs"], "kernels": kern,
+            "spmv_gbs": spmv_gbs, "kernels": kern,
             "roofline": roof, "gpu_launches": int(lc1 - lc0), "clocks": clocks, "e2e": e2e,
             "solvers_at_1e-8": cmp,
         }

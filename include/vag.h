@@ -275,6 +275,28 @@ vag_status vag_set_fluxes(vag_system *sys, const double *F_cell_nodes, const dou
 /* Porous volumes phi_mu [n_cv] of the last vag_transport (0 at Dirichlet nodes). */
 vag_status vag_export_porous_volumes(const vag_system *sys, double *phi, int mem);
 
+/* ------------------------------------------------------------ measurement */
+
+/* Hot kernels that vag_kernel_time can time. */
+enum {
+  VAG_KERNEL_SPMV = 0,            /* q = A p, FP64 sliced ELL (the CG product)      */
+  VAG_KERNEL_SMOOTH = 1,          /* one FP64 l1-Jacobi sweep on the finest level    */
+  VAG_KERNEL_TRANSPORT_STEP = 2   /* one explicit upwind step c' = d c + W c          */
+};
+
+/*
+ * Measurement hook (the paper has no counterpart): time `reps` back-to-back
+ * launches of one hot kernel on this system's own data with CUDA events on the
+ * context's stream and return the mean duration of a launch in *ms_per_launch.
+ * VAG_KERNEL_SMOOTH needs the AMG hierarchy of a previous vag_solve with
+ * VAG_PC_AMG and VAG_FP64; VAG_KERNEL_TRANSPORT_STEP needs the upwind map of a
+ * previous vag_transport; VAG_EINVAL otherwise, or for reps < 1.  The kernels
+ * run on the system's Krylov and transport work vectors, whose contents are
+ * overwritten (the solution and the concentrations already returned are not
+ * touched).  Synchronises the stream.
+ */
+vag_status vag_kernel_time(vag_system *sys, int kernel, int32_t reps, double *ms_per_launch);
+
 /* ---------------------------------------------------------------- server */
 
 /*

@@ -419,20 +419,6 @@ __global__ void k_dense_inverse(const int *__restrict__ sys_start, const int *__
 // Templated on the value type: T = double (FP64 hierarchy) or float (FP32
 // copy of the hierarchy, for the mixed-precision path).
 
-template <class T>
-__device__ __forceinline__ T row_sell(int i, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
-                                      const int *__restrict__ scol, const T *__restrict__ sval,
-                                      const T *__restrict__ x) {
-  const int len = rowptr[i + 1] - rowptr[i];
-  const int base = slice_ptr[i >> 5] + (i & 31);
-  T s = 0;
-#pragma unroll 4
-  for (int k = 0; k < len; ++k) {
-    const int idx = base + 32 * k;
-    s = fma(sval[idx], x[scol[idx]], s);
-  }
-  return s;
-}
 
 // Row product of a coarse level: LN lanes per CSR row, lane l takes entries
 // l, l+LN, ... and the partial sums meet in a fixed shuffle tree.  All 32
@@ -539,7 +525,7 @@ __global__ void k_jac_sell(int n, const int *__restrict__ rowptr, const int *__r
   pdl_wait();
   pdl_trigger();
   if (i >= n || skip[i]) return;
-  xout[i] = jac_row(xin[i], sinv[i], b[i], row_sell(i, rowptr, slice_ptr, scol, sval, xin));
+  xout[i] = jac_row(xin[i], sinv[i], b[i], sell_row(i, rowptr, slice_ptr, scol, sval, xin));
 }
 
 template <class T>
@@ -550,7 +536,7 @@ __global__ void k_resid_sell(int n, const int *__restrict__ rowptr, const int *_
   pdl_wait();
   pdl_trigger();
   if (i >= n) return;
-  r[i] = b[i] - row_sell(i, rowptr, slice_ptr, scol, sval, x);
+  r[i] = b[i] - sell_row(i, rowptr, slice_ptr, scol, sval, x);
 }
 
 // b_c[I] = sum of r over the members of aggregate I (row order)
@@ -1322,6 +1308,34 @@ void amg_apply(System *s, const double *r, double *z, cudaStream_t st) {
   vcycle<float>(s, 0, L0.b32, L0.x32, st);
   launch_pdl(k_to_f64, grid_for(n, TB), TB, 0, st, n, (const float *)L0.x32, z);
   note_launches(2);
+}
+
+// Mean duration of one FP64 finest-level sweep (x_out = x_in + omega
+// D_l1^-1 (b - A x_in)), launched as in the V-cycle.
+double time_smoother(System *s, int reps) {
+  Amg &A = s->amg;
+  if (!A.built || A.f32 || A.levels.empty() || !s->kz) fail(VAG_EINVAL, "no FP64 AMG hierarchy: solve with AMG first");
+  AmgLevel &L = A.levels[0];
+  cudaStream_t st = s->ctx->stream;
+  const int n = L.n, g = grid_for(n, TB);
+  auto sweep = [&](const double *xin, double *xout) {
+    launch_pdl(k_jac_sell<double>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
+               (const int *)L.scol, (const double *)L.sval, (const double *)L.sinv, (const double *)s->kr, xin, xout,
+               (const uint8_t *)L.skip);
+    note_launches(1);
+  };
+  VAG_CUDA(cudaMemsetAsync(s->kz, 0, sizeof(double) * n, st));
+  sweep(s->kz, s->kp);   // warm-up
+  VAG_CUDA(cudaEventRecord(s->ev0, st));
+  for (int r = 0; r < reps; ++r) {
+    if (r & 1) sweep(s->kp, s->kz);
+    else sweep(s->kz, s->kp);
+  }
+  VAG_CUDA(cudaEventRecord(s->ev1, st));
+  VAG_CUDA(cudaEventSynchronize(s->ev1));
+  float ms = 0.f;
+  VAG_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  return (double)ms / reps;
 }
 
 void amg_free(System *s) {

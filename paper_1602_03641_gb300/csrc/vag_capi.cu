@@ -427,6 +427,22 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
   return st;
 }
 
+vag_status vag_kernel_time(vag_system *sys, int kernel, int32_t reps, double *ms_per_launch) {
+  if (!sys) return VAG_EINVAL;
+  System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    if (!ms_per_launch || reps < 1) fail(VAG_EINVAL, "null output or reps < 1");
+    use_device(s->ctx);
+    switch (kernel) {
+      case VAG_KERNEL_SPMV: *ms_per_launch = time_spmv(s, reps); break;
+      case VAG_KERNEL_SMOOTH: *ms_per_launch = time_smoother(s, reps); break;
+      case VAG_KERNEL_TRANSPORT_STEP: *ms_per_launch = time_transport_step(s, reps); break;
+      default: fail(VAG_EINVAL, "unknown kernel");
+    }
+    VAG_CHECK_LAUNCH();
+  });
+}
+
 vag_status vag_spmv(vag_system *sys, const double *x, double *y, int mem) {
   if (!sys) return VAG_EINVAL;
   System *s = &sys->s;

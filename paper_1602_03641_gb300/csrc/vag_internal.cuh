@@ -261,6 +261,25 @@ T *sys_alloc(System *s, size_t n) {
 }
 void sys_free_all(System *s);
 
+// Product of one row of a sliced-ELL matrix (32-row slices, column-major,
+// see vag_sell.cu): one FMA per stored entry of the row, in CSR order, four
+// entries in flight.  (A loop over the uniform slice width with eight in
+// flight, padding included, measured 10-20 % slower on GB300.)
+template <class T>
+__device__ __forceinline__ T sell_row(int row, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
+                                      const int *__restrict__ scol, const T *__restrict__ sval,
+                                      const T *__restrict__ x) {
+  const int len = rowptr[row + 1] - rowptr[row];
+  const int base = slice_ptr[row >> 5] + (row & 31);
+  T s = 0;
+#pragma unroll 4
+  for (int k = 0; k < len; ++k) {
+    const int idx = base + 32 * k;
+    s = fma(sval[idx], x[scol[idx]], s);
+  }
+  return s;
+}
+
 // ----------------------------------------------------------- utilities ----
 // Programmatic dependent launch (sm_90 and later): a kernel launched with
 // launch_pdl may be scheduled while its predecessor in the stream finishes.
@@ -316,6 +335,10 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void amg_setup(System *s, bool f32);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
 void amg_free(System *s);
+// measurement hooks: mean ms of one launch over `reps`
+double time_spmv(System *s, int reps);
+double time_smoother(System *s, int reps);
+double time_transport_step(System *s, int reps);
 void mixed_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void ensure_krylov_buffers(System *s);
 // Krylov result in s->kx and per-system scalars in s->ks: scatter into u,

@@ -12,8 +12,8 @@
 //               the last tile computes beta and the convergence flag;
 //   k_pdir      p = z + beta p.
 // A converged system's tiles return at entry.  Reductions are deterministic
-// and depend only on the system itself (tile sizes come from its own row
-// count), so a system gives bitwise the same iterates alone or in a batch.
+// and depend only on the system itself (its tiles cover its own rows only),
+// so a system gives bitwise the same iterates alone or in a batch.
 // Iterations are captured in a CUDA graph of `chunk` iterations; the host
 // polls one counter (systems done) between graph launches.
 #include "vag_internal.cuh"
@@ -39,14 +39,7 @@ __global__ void __launch_bounds__(NT) k_spmv(const int *__restrict__ rowptr, con
   if (with_dot && ks[sys].done) return;
   double dp = 0.0;
   for (int row = r0 + threadIdx.x; row < r1; row += NT) {
-    const int len = rowptr[row + 1] - rowptr[row];
-    const int base = slice_ptr[row >> 5] + (row & 31);
-    double s = 0.0;
-#pragma unroll 4
-    for (int k = 0; k < len; ++k) {
-      const int idx = base + 32 * k;
-      s = fma(sval[idx], __ldg(&x[scol[idx]]), s);
-    }
+    const double s = sell_row(row, rowptr, slice_ptr, scol, sval, x);
     y[row] = s;
     dp = fma(x[row], s, dp);
   }
@@ -340,14 +333,13 @@ Tiles tiles_of(const System *s) {
 
 }  // namespace
 
-// Rows per tile of a system with n rows: about n / 1216 (enough tiles to fill
-// every SM several times), a power of two between 256 (one row per thread)
-// and 2048.  It depends on the system alone.
-static int tile_rows(int n) {
-  int t = 256;
-  while (t < 2048 && t * 2 <= n / 1216) t *= 2;
-  return t;
-}
+// Rows per tile: 256, one row per thread.  (Tiles of up to 2048 rows, several
+// rows per thread, cost the SpMV a third of its bandwidth at 128^3 on GB300:
+// a thread's rows run one after the other, with fewer loads in flight; the
+// price of small tiles, a longer list of partial sums for the last tile of a
+// system to add, is a few microseconds.)  The tiling depends on the system
+// alone.
+static int tile_rows(int) { return 256; }
 
 void build_tiles(System *s) {
   Segments &g = s->seg;
@@ -408,6 +400,20 @@ void spmv_f64(System *s, const double *x, double *y) {
   ensure_krylov_buffers(s);
   launch_spmv(s, x, y, 0, s->ctx->stream);
   VAG_CHECK_LAUNCH();
+}
+
+double time_spmv(System *s, int reps) {
+  ensure_krylov_buffers(s);
+  cudaStream_t st = s->ctx->stream;
+  VAG_CUDA(cudaMemsetAsync(s->kp, 0, sizeof(double) * s->n_rows, st));
+  launch_spmv(s, s->kp, s->kq, 0, st);   // warm-up
+  VAG_CUDA(cudaEventRecord(s->ev0, st));
+  for (int r = 0; r < reps; ++r) launch_spmv(s, s->kp, s->kq, 0, st);
+  VAG_CUDA(cudaEventRecord(s->ev1, st));
+  VAG_CUDA(cudaEventSynchronize(s->ev1));
+  float ms = 0.f;
+  VAG_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  return (double)ms / reps;
 }
 
 static void pcg_iteration_amg(System *s, cudaStream_t st) {

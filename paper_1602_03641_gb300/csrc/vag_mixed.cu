@@ -40,14 +40,7 @@ __global__ void __launch_bounds__(NT) k_spmv32(const int *__restrict__ rowptr, c
   const int r0 = tl.row0[t], r1 = tl.row1[t];
   float dp = 0.f;
   for (int row = r0 + threadIdx.x; row < r1; row += NT) {
-    const int len = rowptr[row + 1] - rowptr[row];
-    const int base = slice_ptr[row >> 5] + (row & 31);
-    float s = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < len; ++k) {
-      const int idx = base + 32 * k;
-      s = fmaf(sval[idx], __ldg(&x[scol[idx]]), s);
-    }
+    const float s = sell_row(row, rowptr, slice_ptr, scol, sval, x);
     y[row] = s;
     dp = fmaf(x[row], s, dp);
   }

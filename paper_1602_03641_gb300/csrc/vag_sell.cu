@@ -32,7 +32,7 @@ __global__ void k_sell_cols(int n, const int *__restrict__ rowptr, const int *__
   for (int k = 0; k < e - b; ++k) scol[base + 32 * k] = col[b + k];
 }
 
-// padding slots point at the row itself (never read: rows stop at their length)
+// padding slots point at the row itself (their values are 0)
 __global__ void k_sell_pad(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                            int *__restrict__ scol) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,6 +57,9 @@ __global__ void k_sell_vals(int n, const int *__restrict__ rowptr, const double 
     const double v = scale ? sr * val[b + k] * scale[col[b + k]] : val[b + k];
     sval[base + 32 * k] = (T)v;
   }
+  // padding up to the slice width: value 0 (its column is the row itself)
+  const int w = (slice_ptr[(row >> 5) + 1] - slice_ptr[row >> 5]) >> 5;
+  for (int k = e - b; k < w; ++k) sval[base + 32 * k] = (T)0;
 }
 
 }  // namespace

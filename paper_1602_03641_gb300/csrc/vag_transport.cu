@@ -270,14 +270,31 @@ __global__ void k_cv_sys(int nv, int nf, int nc, int n_sys, const int *__restric
   cv_sys[mu] = lo;
 }
 
+// Launched with programmatic dependent launch: the map (written once per
+// solve) is read before the dependency wait, the previous step's c after it.
+constexpr int kStepPF = 4;
 __global__ void __launch_bounds__(TB) k_step(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
                                              const double *__restrict__ w, const double *__restrict__ diag,
                                              const double *__restrict__ c, double *__restrict__ cn) {
   const int mu = blockIdx.x * TB + threadIdx.x;
-  if (mu >= n) return;
-  double v = diag[mu] * c[mu];
-  const int b = rowptr[mu], e = rowptr[mu + 1];
-  for (int k = b; k < e; ++k) v = fma(w[k], __ldg(&c[col[k]]), v);
+  const bool valid = mu < n;
+  const int b = valid ? rowptr[mu] : 0, e = valid ? rowptr[mu + 1] : 0;
+  const double d = valid ? diag[mu] : 0.0;
+  int pc[kStepPF];
+  double pw[kStepPF];
+#pragma unroll
+  for (int u = 0; u < kStepPF; ++u) {
+    pc[u] = b + u < e ? col[b + u] : 0;
+    pw[u] = b + u < e ? w[b + u] : 0.0;
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (!valid) return;
+  double v = d * c[mu];
+#pragma unroll
+  for (int u = 0; u < kStepPF; ++u)
+    if (b + u < e) v = fma(pw[u], c[pc[u]], v);
+  for (int k = b + kStepPF; k < e; ++k) v = fma(w[k], c[col[k]], v);
   cn[mu] = v;
 }
 
@@ -287,6 +304,31 @@ __global__ void k_set_dir(int nd, const int *__restrict__ dn, const double *__re
 }
 
 }  // namespace
+
+// Mean duration of one explicit step on the current upwind map.
+double time_transport_step(System *s, int reps) {
+  if (!s->trowptr || !s->cbuf || !s->tdiag) fail(VAG_EINVAL, "no upwind map: run vag_transport first");
+  cudaStream_t st = s->ctx->stream;
+  const int n = s->n_cv;
+  const int gs = grid_for(n, TB);
+  double *a = s->cbuf, *b = s->cbuf + n;
+  auto step = [&](const double *c, double *cn) {
+    launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
+               (const double *)s->tdiag, c, cn);
+    note_launches(1);
+  };
+  step(a, b);   // warm-up
+  VAG_CUDA(cudaEventRecord(s->ev0, st));
+  for (int r = 0; r < reps; ++r) {
+    if (r & 1) step(b, a);
+    else step(a, b);
+  }
+  VAG_CUDA(cudaEventRecord(s->ev1, st));
+  VAG_CUDA(cudaEventSynchronize(s->ev1));
+  float ms = 0.f;
+  VAG_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  return (double)ms / reps;
+}
 
 void recover_cells_and_fluxes(System *s) {
   cudaStream_t st = s->ctx->stream;
@@ -376,7 +418,8 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
       set_capturing(true);
       double *a = s->cbuf, *b = s->cbuf + n;
       for (int k = 0; k < kStepChunk; ++k) {
-        k_step<<<gs, TB, 0, st>>>(n, s->trowptr, s->tcol, s->tval, s->tdiag, a, b);
+        launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
+                   (const double *)s->tdiag, (const double *)a, b);
         std::swap(a, b);
       }
       set_capturing(false);
@@ -391,7 +434,8 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     }
   }
   for (int k = chunks * kStepChunk; k < o->n_steps; ++k) {
-    k_step<<<gs, TB, 0, st>>>(n, s->trowptr, s->tcol, s->tval, s->tdiag, c0, c1);
+    launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
+               (const double *)s->tdiag, (const double *)c0, c1);
     note_launches(1);
     std::swap(c0, c1);
   }

@@ -23,6 +23,7 @@ VAG_EBREAKDOWN, VAG_ETIMEOUT, VAG_ECUDA, VAG_EMESH = 5, 6, 7, 8
 VAG_MEM_HOST, VAG_MEM_DEVICE = 0, 1
 VAG_FP64, VAG_MIXED = 0, 1
 VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG = 0, 1, 2
+VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP = 0, 1, 2
 
 STATUS_NAMES = {0: "VAG_OK", 1: "VAG_EINVAL", 2: "VAG_ENOMEM", 3: "VAG_EBUDGET", 4: "VAG_ENOTCONVERGED",
                 5: "VAG_EBREAKDOWN", 6: "VAG_ETIMEOUT", 7: "VAG_ECUDA", 8: "VAG_EMESH"}
@@ -117,6 +118,7 @@ _SIGS = {
     "vag_system_get_info": (C.c_int, [P, C.POINTER(vag_system_info)]),
     "vag_solve": (C.c_int, [P, C.POINTER(vag_solve_opts), P, C.POINTER(vag_solve_info)]),
     "vag_spmv": (C.c_int, [P, P, P, C.c_int]),
+    "vag_kernel_time": (C.c_int, [P, C.c_int, C.c_int32, C.POINTER(C.c_double)]),
     "vag_transport": (C.c_int, [P, C.POINTER(vag_transport_opts), P, C.POINTER(vag_transport_info)]),
     "vag_export_system": (C.c_int, [P, P, P, P, P, P, C.c_int]),
     "vag_export_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
@@ -339,6 +341,13 @@ class System:
         mem = _mem_of(x, y)
         self.ctx.check(self._L.vag_spmv(self.h, _ptr(x, np.float64), _ptr(y, np.float64), mem))
         return y
+
+    def kernel_time(self, kernel, reps=100):
+        """Mean ms of one launch of a hot kernel on this system's data
+        (VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP)."""
+        ms = C.c_double()
+        self.ctx.check(self._L.vag_kernel_time(self.h, int(kernel), int(reps), C.byref(ms)))
+        return ms.value
 
     def transport(self, c, phi_m, phi_f, cbar, n_steps, cfl=0.9, dt=0.0, omega=0.5):
         """c is updated in place (numpy or CUDA tensor, [n_cv])."""
