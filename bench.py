@@ -76,6 +76,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def replica_throughput(local_ms, steps, world, device="cpu"):
+    """Whole-job throughput of `world` independent replicas that each ran
+    `steps` steps in `local_ms`: the slowest rank's time bounds the job (the
+    maximum over ranks), and every rank processed `steps` units."""
+    tot = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([tot], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    return world * steps / (tot / 1e3), tot
+
+
 def fp64_peak_gflops():
     """FP64 FMA peak of the GB300 from its unit counts and clock: 2 DFMA per
     clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
@@ -590,12 +604,7 @@ def main():
     lc1 = pkg.launch_count()
     barrier()
     clocks = sampler.stop()
-    tot = sum(ms)
-    if world > 1:
-        t = torch.tensor([tot], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-    value = world * args.steps / (tot / 1e3)
+    value, tot = replica_throughput(sum(ms), args.steps, world, dev)
 
     # end to end from pinned host buffers
     e2e = None
@@ -603,11 +612,7 @@ def main():
         step_host()
         barrier()
         ms_h, _ = timed(step_host, args.steps)
-        tot_h = sum(ms_h)
-        if world > 1:
-            t = torch.tensor([tot_h], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot_h = float(t.item())
+        _, tot_h = replica_throughput(sum(ms_h), args.steps, world, dev)
         h2d = sum(pin[k].nbytes for k in ["xyz", "cn", "ffn", "lam", "lamf", "df", "dn", "dv", "phm", "phf", "cb",
                                          "c0"])
         e2e = {"value": world * args.steps / (tot_h / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
