@@ -251,6 +251,12 @@ typedef struct {
 vag_status vag_transport(vag_system *sys, const vag_transport_opts *opts, double *c_inout,
                          vag_transport_info *info);
 
+/* The same operation under the name of the problem statement's transport
+ * step (Eq. tracero1own applied n_steps times): *dt_used (may be NULL)
+ * receives the step used (a batch: its smallest); info may be NULL. */
+vag_status vag_transport_step(vag_system *sys, const vag_transport_opts *opts, double *c_inout, double *dt_used,
+                              vag_transport_info *info);
+
 /* Per-system CFL bound and step of the last vag_transport: [n_sys] each (a
  * system with no outflow anywhere has bound +inf and step 0 under cfl > 0). */
 vag_status vag_transport_get_dts(const vag_system *sys, double *dt_max, double *dt);

@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(256) k_jac_csr(int n, const int *__restrict__ 
 }
 
 // same sweep in the sliced-ELL layout (level 0), one thread per row
-template <class T>
+template <class T, int U>
 __global__ void k_jac_sell(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                            const int *__restrict__ scol, const T *__restrict__ sval, const T *__restrict__ sinv,
                            const T *__restrict__ b, const T *__restrict__ xin, T *__restrict__ xout,
@@ -525,10 +525,10 @@ __global__ void k_jac_sell(int n, const int *__restrict__ rowptr, const int *__r
   pdl_wait();
   pdl_trigger();
   if (i >= n || skip[i]) return;
-  xout[i] = jac_row(xin[i], sinv[i], b[i], sell_row(i, rowptr, slice_ptr, scol, sval, xin));
+  xout[i] = jac_row(xin[i], sinv[i], b[i], sell_row<T, U>(i, rowptr, slice_ptr, scol, sval, xin));
 }
 
-template <class T>
+template <class T, int U>
 __global__ void k_resid_sell(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                              const int *__restrict__ scol, const T *__restrict__ sval, const T *__restrict__ b,
                              const T *__restrict__ x, T *__restrict__ r) {
@@ -536,7 +536,7 @@ __global__ void k_resid_sell(int n, const int *__restrict__ rowptr, const int *_
   pdl_wait();
   pdl_trigger();
   if (i >= n) return;
-  r[i] = b[i] - sell_row(i, rowptr, slice_ptr, scol, sval, x);
+  r[i] = b[i] - sell_row<T, U>(i, rowptr, slice_ptr, scol, sval, x);
 }
 
 // b_c[I] = sum of r over the members of aggregate I (row order)
@@ -1259,12 +1259,15 @@ static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
   const LV<T> c = lv<T>(s, C);
   constexpr int LN = row_lanes<T>();
   const int gL = grid_for(n, 256 / LN);   // LN lanes per row
+  // finest level: the autotuned loads in flight of the sliced-ELL row loop
+  auto jac_sell = s->sell_u == 2 ? k_jac_sell<T, 2> : s->sell_u == 8 ? k_jac_sell<T, 8> : k_jac_sell<T, 4>;
+  auto resid_sell = s->sell_u == 2 ? k_resid_sell<T, 2> : s->sell_u == 8 ? k_resid_sell<T, 8> : k_resid_sell<T, 4>;
   if (lvl == 0) {
     // level 0: sliced ELL, one thread per row
     launch_pdl(k_jac_first<T>, g, TB, 0, st, n, b, v.sinv, v.t);
-    launch_pdl(k_jac_sell<T>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+    launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
-    launch_pdl(k_resid_sell<T>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
+    launch_pdl(resid_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
                (const int *)L.scol, v.sval, b, (const T *)x, v.t);
     launch_pdl(k_restrict_first<T>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
                (const T *)v.t, c.sinv, c.b, c.t);
@@ -1282,9 +1285,9 @@ static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
   // coarse correction as it reads x)
   if (lvl == 0) {
     launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, x);
-    launch_pdl(k_jac_sell<T>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+    launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)x, v.t, (const uint8_t *)L.skip);
-    launch_pdl(k_jac_sell<T>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+    launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
     note_launches(3);
   } else {
@@ -1319,7 +1322,8 @@ double time_smoother(System *s, int reps) {
   cudaStream_t st = s->ctx->stream;
   const int n = L.n, g = grid_for(n, TB);
   auto sweep = [&](const double *xin, double *xout) {
-    launch_pdl(k_jac_sell<double>, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
+    auto jac = s->sell_u == 2 ? k_jac_sell<double, 2> : s->sell_u == 8 ? k_jac_sell<double, 8> : k_jac_sell<double, 4>;
+    launch_pdl(jac, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
                (const int *)L.scol, (const double *)L.sval, (const double *)L.sinv, (const double *)s->kr, xin, xout,
                (const uint8_t *)L.skip);
     note_launches(1);

@@ -514,6 +514,15 @@ vag_status vag_transport(vag_system *sys, const vag_transport_opts *o, double *c
   });
 }
 
+vag_status vag_transport_step(vag_system *sys, const vag_transport_opts *opts, double *c_inout, double *dt_used,
+                              vag_transport_info *info) {
+  vag_transport_info local{};
+  vag_transport_info *inf = info ? info : &local;
+  const vag_status st = vag_transport(sys, opts, c_inout, inf);
+  if (st == VAG_OK && dt_used) *dt_used = inf->dt;
+  return st;
+}
+
 vag_status vag_export_system(const vag_system *sys, int32_t *rowptr, int32_t *col, double *val, double *rhs,
                              int32_t *row_dof, int mem) {
   if (!sys) return VAG_EINVAL;

@@ -65,6 +65,9 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   cudaMemPool_t pool = nullptr;   // stream-ordered pool for every device buffer of the context's systems
   std::string last_error;
+  // autotuned loads in flight of the sliced-ELL row loop, per matrix size
+  // class (floor(log2 rows)); see tune_sell
+  std::vector<int> sell_unroll = std::vector<int>(32, 0);
 };
 
 // One device allocation owned by a system.
@@ -202,6 +205,7 @@ struct System {
   // sliced-ELL copy (32-row slices, column-major inside a slice)
   int n_slices = 0;
   int64_t sell_nnz = 0;
+  int sell_u = 0;              // loads in flight of the SELL row loop (0: not tuned yet)
   int *slice_ptr = nullptr;    // [n_slices+1] element offsets
   int *scol = nullptr;         // [sell_nnz]
   double *sval = nullptr;      // [sell_nnz]
@@ -262,17 +266,19 @@ T *sys_alloc(System *s, size_t n) {
 void sys_free_all(System *s);
 
 // Product of one row of a sliced-ELL matrix (32-row slices, column-major,
-// see vag_sell.cu): one FMA per stored entry of the row, in CSR order, four
-// entries in flight.  (A loop over the uniform slice width with eight in
-// flight, padding included, measured 10-20 % slower on GB300.)
-template <class T>
+// see vag_sell.cu): one FMA per stored entry of the row, in CSR order, with
+// U entries in flight (U is chosen per matrix size by the autotuner in
+// vag_krylov.cu; the FMA sequence, hence the result, is the same for every
+// U).  (A loop over the uniform slice width with eight in flight, padding
+// included, measured 10-20 % slower on GB300.)
+template <class T, int U = 4>
 __device__ __forceinline__ T sell_row(int row, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                                       const int *__restrict__ scol, const T *__restrict__ sval,
                                       const T *__restrict__ x) {
   const int len = rowptr[row + 1] - rowptr[row];
   const int base = slice_ptr[row >> 5] + (row & 31);
   T s = 0;
-#pragma unroll 4
+#pragma unroll(U)
   for (int k = 0; k < len; ++k) {
     const int idx = base + 32 * k;
     s = fma(sval[idx], x[scol[idx]], s);
@@ -335,6 +341,10 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void amg_setup(System *s, bool f32);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
 void amg_free(System *s);
+// choose (once per context and matrix size class) the loads in flight of the
+// sliced-ELL row loop by timing the candidates on this system's matrix;
+// never call it while a stream capture is open
+void tune_sell(System *s);
 // measurement hooks: mean ms of one launch over `reps`
 double time_spmv(System *s, int reps);
 double time_smoother(System *s, int reps);

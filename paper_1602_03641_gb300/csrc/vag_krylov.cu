@@ -16,6 +16,8 @@
 // so a system gives bitwise the same iterates alone or in a batch.
 // Iterations are captured in a CUDA graph of `chunk` iterations; the host
 // polls one counter (systems done) between graph launches.
+#include <cstdio>
+
 #include "vag_internal.cuh"
 #include "vag_reduce.cuh"
 
@@ -26,6 +28,7 @@ constexpr int NT = 256;
 
 // q = A p in the sliced-ELL layout, one thread per row: exactly one FMA per
 // stored entry, in the row's CSR order.
+template <int U>
 __global__ void __launch_bounds__(NT) k_spmv(const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                                              const int *__restrict__ scol, const double *__restrict__ sval,
                                              const double *__restrict__ x, double *__restrict__ y, Tiles tl,
@@ -39,7 +42,7 @@ __global__ void __launch_bounds__(NT) k_spmv(const int *__restrict__ rowptr, con
   if (with_dot && ks[sys].done) return;
   double dp = 0.0;
   for (int row = r0 + threadIdx.x; row < r1; row += NT) {
-    const double s = sell_row(row, rowptr, slice_ptr, scol, sval, x);
+    const double s = sell_row<double, U>(row, rowptr, slice_ptr, scol, sval, x);
     y[row] = s;
     dp = fma(x[row], s, dp);
   }
@@ -371,11 +374,51 @@ void build_tiles(System *s) {
   VAG_CUDA(cudaStreamSynchronize(str));   // host vectors go out of scope
 }
 
-static void launch_spmv(System *s, const double *x, double *y, int with_dot, cudaStream_t st) {
-  launch_pdl(k_spmv, s->seg.n_tiles, NT, 0, st, (const int *)s->rowptr, (const int *)s->slice_ptr,
+static void launch_spmv_u(System *s, int u, const double *x, double *y, int with_dot, cudaStream_t st) {
+  auto kern = u == 2 ? k_spmv<2> : u == 8 ? k_spmv<8> : k_spmv<4>;
+  launch_pdl(kern, s->seg.n_tiles, NT, 0, st, (const int *)s->rowptr, (const int *)s->slice_ptr,
              (const int *)s->scol, (const double *)s->sval, x, y, tiles_of(s), s->partials, s->counter, s->ks,
              s->n_done, with_dot);
   note_launches(1);
+}
+
+static void launch_spmv(System *s, const double *x, double *y, int with_dot, cudaStream_t st) {
+  launch_spmv_u(s, s->sell_u ? s->sell_u : 4, x, y, with_dot, st);
+}
+
+// The autotuner of the sliced-ELL product: 2, 4 or 8 entries of a row in
+// flight per thread, timed (CUDA events, 5 launches each after a warm-up) on
+// the system's own matrix the first time the context meets a matrix of this
+// size class; later systems of the class reuse the choice.  Every candidate
+// performs the same FMAs in the same order, so the choice changes the time,
+// never the result (a system stays bitwise the same alone or in a batch).
+void tune_sell(System *s) {
+  if (s->sell_u) return;
+  int cls = 0;
+  while ((2 << cls) <= s->n_rows && cls < 31) ++cls;
+  int &slot = s->ctx->sell_unroll[cls];
+  if (!slot) {
+    ensure_krylov_buffers(s);
+    cudaStream_t st = s->ctx->stream;
+    VAG_CUDA(cudaMemsetAsync(s->kp, 0, sizeof(double) * s->n_rows, st));
+    const int cand[3] = {2, 4, 8};
+    float best = 0.f;
+    for (int u : cand) {
+      launch_spmv_u(s, u, s->kp, s->kq, 0, st);
+      VAG_CUDA(cudaEventRecord(s->ev0, st));
+      for (int r = 0; r < 5; ++r) launch_spmv_u(s, u, s->kp, s->kq, 0, st);
+      VAG_CUDA(cudaEventRecord(s->ev1, st));
+      VAG_CUDA(cudaEventSynchronize(s->ev1));
+      float ms = 0.f;
+      VAG_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+      if (!slot || ms < best) {
+        best = ms;
+        slot = u;
+      }
+    }
+    if (trace_enabled()) std::fprintf(stderr, "[vag trace] SELL autotune: %d rows -> %d in flight\n", s->n_rows, slot);
+  }
+  s->sell_u = slot;
 }
 
 void ensure_krylov_buffers(System *s) {
@@ -398,12 +441,14 @@ void ensure_krylov_buffers(System *s) {
 
 void spmv_f64(System *s, const double *x, double *y) {
   ensure_krylov_buffers(s);
+  tune_sell(s);
   launch_spmv(s, x, y, 0, s->ctx->stream);
   VAG_CHECK_LAUNCH();
 }
 
 double time_spmv(System *s, int reps) {
   ensure_krylov_buffers(s);
+  tune_sell(s);
   cudaStream_t st = s->ctx->stream;
   VAG_CUDA(cudaMemsetAsync(s->kp, 0, sizeof(double) * s->n_rows, st));
   launch_spmv(s, s->kp, s->kq, 0, st);   // warm-up
@@ -442,6 +487,7 @@ static void pcg_iteration(System *s, cudaStream_t st) {
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   cudaStream_t st = s->ctx->stream;
   ensure_krylov_buffers(s);
+  tune_sell(s);
   const bool amg = o->precond == VAG_PC_AMG;
   const int ns = s->seg.n_sys;
   const int nt = s->seg.n_tiles;

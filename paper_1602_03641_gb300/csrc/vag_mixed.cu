@@ -30,6 +30,7 @@ __global__ void k_dscale(int n, const double *__restrict__ dinv, double *__restr
   if (i < n) sc[i] = sqrt(dinv[i]);
 }
 
+template <int U>
 __global__ void __launch_bounds__(NT) k_spmv32(const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                                                const int *__restrict__ scol, const float *__restrict__ sval,
                                                const float *__restrict__ x, float *__restrict__ y, Tiles tl,
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(NT) k_spmv32(const int *__restrict__ rowptr, c
   const int r0 = tl.row0[t], r1 = tl.row1[t];
   float dp = 0.f;
   for (int row = r0 + threadIdx.x; row < r1; row += NT) {
-    const float s = sell_row(row, rowptr, slice_ptr, scol, sval, x);
+    const float s = sell_row<float, U>(row, rowptr, slice_ptr, scol, sval, x);
     y[row] = s;
     dp = fmaf(x[row], s, dp);
   }
@@ -221,6 +222,9 @@ static void ensure_mixed_buffers(System *s) {
 }
 
 void mixed_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
+  ensure_krylov_buffers(s);
+  tune_sell(s);
+  auto spmv32 = s->sell_u == 2 ? k_spmv32<2> : s->sell_u == 8 ? k_spmv32<8> : k_spmv32<4>;
   cudaStream_t st = s->ctx->stream;
   ensure_krylov_buffers(s);
   ensure_mixed_buffers(s);
@@ -245,8 +249,8 @@ void mixed_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
     VAG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
     for (int i = 0; i < chunk; ++i) {
-      k_spmv32<<<nt, NT, 0, st>>>(s->rowptr, s->slice_ptr, s->scol, m.sval32, m.p32, m.q32, tl, s->partials,
-                                  s->counter, m.ks_in, m.n_done_in);
+      spmv32<<<nt, NT, 0, st>>>(s->rowptr, s->slice_ptr, s->scol, m.sval32, m.p32, m.q32, tl, s->partials,
+                                s->counter, m.ks_in, m.n_done_in);
       k_upd32<<<nt, NT, 0, st>>>(m.x32, m.r32, m.p32, m.q32, tl, s->partials, s->counter, m.ks_in, m.n_done_in);
       k_pdir32<<<nt, NT, 0, st>>>(m.p32, m.r32, tl, m.ks_in);
     }

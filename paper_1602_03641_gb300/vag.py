@@ -120,6 +120,8 @@ _SIGS = {
     "vag_spmv": (C.c_int, [P, P, P, C.c_int]),
     "vag_kernel_time": (C.c_int, [P, C.c_int, C.c_int32, C.POINTER(C.c_double)]),
     "vag_transport": (C.c_int, [P, C.POINTER(vag_transport_opts), P, C.POINTER(vag_transport_info)]),
+    "vag_transport_step": (C.c_int, [P, C.POINTER(vag_transport_opts), P, C.POINTER(C.c_double),
+                                     C.POINTER(vag_transport_info)]),
     "vag_export_system": (C.c_int, [P, P, P, P, P, P, C.c_int]),
     "vag_export_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
     "vag_set_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
@@ -357,6 +359,17 @@ class System:
         inf = vag_transport_info()
         self.ctx.check(self._L.vag_transport(self.h, C.byref(o), _ptr(c, np.float64), C.byref(inf)))
         return inf
+
+    def transport_step(self, c, phi_m, phi_f, cbar, n_steps, cfl=0.9, dt=0.0, omega=0.5):
+        """vag_transport_step: as transport(), returning (info, step used)."""
+        mem = _mem_of(c, phi_m, phi_f, cbar)
+        o = vag_transport_opts(_ptr(phi_m, np.float64), _ptr(phi_f, np.float64), _ptr(cbar, np.float64),
+                               float(omega), float(cfl), float(dt), int(n_steps), mem)
+        inf = vag_transport_info()
+        used = C.c_double(-1.0)
+        self.ctx.check(self._L.vag_transport_step(self.h, C.byref(o), _ptr(c, np.float64), C.byref(used),
+                                                  C.byref(inf)))
+        return inf, used.value
 
     def export_system(self):
         i = self.info()

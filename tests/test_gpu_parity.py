@@ -162,6 +162,21 @@ def test_transport_ten_steps_end_to_end(ctx, name):
     assert c.min() >= -1e-14 and c.max() <= 1 + 1e-14
 
 
+def test_transport_step_entry_point(ctx):
+    """vag_transport_step is vag_transport with the step returned: same
+    concentrations bitwise, dt_used = info.dt."""
+    import paper_1602_03641_gb300 as pkg
+    pb = CASES["dfn12"]()
+    s = pkg.assemble_problem(ctx, pb)
+    s.solve(rtol=1e-12, maxit=20000, raise_on_error=False)
+    c1, c2 = pb.c0(), pb.c0()
+    i1 = s.transport(c1, pb.phi_m, pb.phi_f, pb.cbar, n_steps=7, cfl=0.9)
+    i2, used = s.transport_step(c2, pb.phi_m, pb.phi_f, pb.cbar, n_steps=7, cfl=0.9)
+    np.testing.assert_array_equal(c1, c2)
+    assert used == i2.dt == i1.dt and i2.steps == 7
+    s.close()
+
+
 def test_spmv_matches(runs):
     pb, ref, sysg, u, info = runs["dfn12"]
     S, b, R = vo.schur_system(pb, ref.A)
