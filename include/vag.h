@@ -50,6 +50,9 @@ enum {
 enum { VAG_MEM_HOST = 0, VAG_MEM_DEVICE = 1 };
 enum { VAG_FP64 = 0, VAG_MIXED = 1 };
 enum { VAG_PC_JACOBI = 0, VAG_PC_CHEBYSHEV = 1, VAG_PC_AMG = 2 };
+/* Krylov method: CG (the system is SPD) or BiCGStab, the method of the
+ * paper's solver experiments (§5.3), right-preconditioned. */
+enum { VAG_KRYLOV_CG = 0, VAG_KRYLOV_BICGSTAB = 1 };
 
 typedef struct vag_ctx vag_ctx;
 typedef struct vag_system vag_system;
@@ -187,6 +190,9 @@ typedef struct {
   double rtol;       /* stop at ||b - A x||_2 <= rtol ||b||_2 (> 0)           */
   int32_t maxit;     /* Krylov iteration cap (total over refinements)          */
   int mem;           /* location of u_out                                     */
+  int32_t krylov;    /* VAG_KRYLOV_CG (0, the default) or VAG_KRYLOV_BICGSTAB
+                        (FP64 iterations; with VAG_MIXED only for VAG_PC_AMG,
+                        whose V-cycle then runs on the FP32 hierarchy)     */
 } vag_solve_opts;
 
 typedef struct {

@@ -93,6 +93,7 @@ void destroy_system(vag_system *sys) {
   if (s->mx.graph) cudaGraphExecDestroy(s->mx.graph);
   if (s->pcg_graph_amg) cudaGraphExecDestroy(s->pcg_graph_amg);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
+  if (s->bicg_graph) cudaGraphExecDestroy(s->bicg_graph);
   amg_free(s);
   if (s->ks_host) cudaFreeHost(s->ks_host);
   if (s->n_done_host) cudaFreeHost(s->n_done_host);
@@ -414,8 +415,16 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     trace_mark(s->ctx->stream, "start");
     // VAG_MIXED: Jacobi -> FP64 refinement around FP32 CG; AMG -> FP64 CG
     // preconditioned by an FP32 copy of the AMG hierarchy
-    if (opts->precision == VAG_MIXED && opts->precond == VAG_PC_JACOBI) mixed_solve(s, opts, inf);
-    else pcg_solve(s, opts, inf);
+    if (opts->krylov != VAG_KRYLOV_CG && opts->krylov != VAG_KRYLOV_BICGSTAB) fail(VAG_EINVAL, "unknown Krylov method");
+    if (opts->krylov == VAG_KRYLOV_BICGSTAB) {
+      if (opts->precision == VAG_MIXED && opts->precond != VAG_PC_AMG)
+        fail(VAG_EINVAL, "BiCGStab with VAG_MIXED needs VAG_PC_AMG");
+      bicgstab_solve(s, opts, inf);
+    } else if (opts->precision == VAG_MIXED && opts->precond == VAG_PC_JACOBI) {
+      mixed_solve(s, opts, inf);
+    } else {
+      pcg_solve(s, opts, inf);
+    }
     copy_out(s, u_out, s->u, (size_t)s->n_cv, opts->mem);
     trace_mark(s->ctx->stream, "copy out");
     VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));

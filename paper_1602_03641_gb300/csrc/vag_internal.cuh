@@ -82,6 +82,8 @@ struct KrylovScalars {
   int iter, maxit, done, breakdown;
   int inner_total;             // mixed precision: inner iterations summed over refinements
   int stalled;                 // true residual stopped falling (rounding floor)
+  double omega;                // BiCGStab: omega; rz holds rho = r0^.r, pq holds r0^.v
+  int half;                    // BiCGStab: converged on s within the current iteration
 };
 
 // One level of the aggregation AMG hierarchy (level 0 aliases the system).
@@ -230,6 +232,9 @@ struct System {
   Mixed mx;
   Amg amg;
   double *kz = nullptr;                // preconditioned residual (AMG)
+  // BiCGStab: shadow residual r0^, s, s^ = M s, t = A s^, p^ = M p
+  double *b_r0 = nullptr, *b_s = nullptr, *b_sh = nullptr, *b_t = nullptr, *b_ph = nullptr;
+  cudaGraphExec_t bicg_graph = nullptr;
   cudaGraphExec_t pcg_graph_amg = nullptr;
   size_t amg_graph_nodes = 0;
 
@@ -338,6 +343,7 @@ void trace_report(const char *call);
 void symbolic_phase(System *s);
 void numeric_phase(System *s);
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
+void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void amg_setup(System *s, bool f32);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
 void amg_free(System *s);

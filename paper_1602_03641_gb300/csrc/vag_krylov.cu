@@ -334,6 +334,148 @@ Tiles tiles_of(const System *s) {
   return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0};
 }
 
+// ------------------------------------------------------------- BiCGStab ----
+// Right-preconditioned BiCGStab (van der Vorst 1992), the Krylov method the
+// paper's experiments use (§5.3), with the same per-system tiles and
+// deterministic reductions as CG.  Per iteration, with p^ = M p, s^ = M s:
+//   v = A p^, alpha = rho / (r0^.v), s = r - alpha v, t = A s^,
+//   omega = (t.s)/(t.t), x += alpha p^ + omega s^, r = s - omega t,
+//   rho' = r0^.r, beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v).
+
+// r0^ = p = r (after k_init_m: x = 0, r = b); rho = r.r = b.b
+__global__ void __launch_bounds__(NT) k_bi_start(const double *__restrict__ r, double *__restrict__ r0,
+                                                 double *__restrict__ p, Tiles tl, KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  const int r0i = tl.row0[t], r1 = tl.row1[t];
+  for (int i = r0i + threadIdx.x; i < r1; i += NT) {
+    r0[i] = r[i];
+    p[i] = r[i];
+  }
+  if (t == tl.sys_tile0[sys] && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.rz = k.bb;
+    k.omega = 1.0;
+    k.half = 0;
+    const bool fin = k.rr <= k.tol2 || k.maxit <= 0;
+    k.done = fin ? 1 : 0;
+    if (fin) atomicAdd(n_done, 1);
+  }
+}
+
+// z = D^-1 x (Jacobi preconditioner of BiCGStab)
+__global__ void __launch_bounds__(NT) k_bi_jacobi(const double *__restrict__ x, const double *__restrict__ dinv,
+                                                  double *__restrict__ z, Tiles tl, const KrylovScalars *ks) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  for (int i = tl.row0[t] + threadIdx.x; i < tl.row1[t]; i += NT) z[i] = dinv[i] * x[i];
+}
+
+// alpha = rho / (r0^.v)
+__global__ void __launch_bounds__(NT) k_bi_alpha(const double *__restrict__ r0, const double *__restrict__ v, Tiles tl,
+                                                 double *partials, unsigned *counter, KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  double d = 0.0;
+  for (int i = tl.row0[t] + threadIdx.x; i < tl.row1[t]; i += NT) d = fma(r0[i], v[i], d);
+  double in[1] = {d}, out[1];
+  if (seg_sum<NT, 1>(in, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.pq = out[0];
+    if (!(out[0] != 0.0) || !(k.rz == k.rz)) {
+      k.breakdown = 1;
+      k.done = 1;
+      atomicAdd(n_done, 1);
+    } else {
+      k.alpha = k.rz / out[0];
+    }
+  }
+}
+
+// s = r - alpha v, and s.s (a converged s ends the iteration with omega = 0)
+__global__ void __launch_bounds__(NT) k_bi_s(const double *__restrict__ r, const double *__restrict__ v,
+                                             double *__restrict__ sv, Tiles tl, double *partials, unsigned *counter,
+                                             KrylovScalars *ks) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  const double alpha = ks[sys].alpha;
+  double ss = 0.0;
+  for (int i = tl.row0[t] + threadIdx.x; i < tl.row1[t]; i += NT) {
+    const double si = fma(-alpha, v[i], r[i]);
+    sv[i] = si;
+    ss = fma(si, si, ss);
+  }
+  double in[1] = {ss}, out[1];
+  if (seg_sum<NT, 1>(in, partials, counter, tl, t, sys, out) && threadIdx.x == 0)
+    ks[sys].half = out[0] <= ks[sys].tol2 ? 1 : 0;
+}
+
+// omega = (t.s)/(t.t) (0 when s already met the tolerance)
+__global__ void __launch_bounds__(NT) k_bi_omega(const double *__restrict__ tv, const double *__restrict__ sv, Tiles tl,
+                                                 double *partials, unsigned *counter, KrylovScalars *ks) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  double ts = 0.0, tt = 0.0;
+  for (int i = tl.row0[t] + threadIdx.x; i < tl.row1[t]; i += NT) {
+    ts = fma(tv[i], sv[i], ts);
+    tt = fma(tv[i], tv[i], tt);
+  }
+  double in[2] = {ts, tt}, out[2];
+  if (seg_sum<NT, 2>(in, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.omega = (k.half || !(out[1] > 0.0)) ? 0.0 : out[0] / out[1];
+  }
+}
+
+// x += alpha p^ + omega s^, r = s - omega t, rho' = r0^.r and r.r; the last
+// tile counts the iteration, tests convergence and forms beta
+__global__ void __launch_bounds__(NT) k_bi_update(double *__restrict__ x, double *__restrict__ r,
+                                                  const double *__restrict__ ph, const double *__restrict__ sh,
+                                                  const double *__restrict__ sv, const double *__restrict__ tv,
+                                                  const double *__restrict__ r0, Tiles tl, double *partials,
+                                                  unsigned *counter, KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  const double alpha = ks[sys].alpha, omega = ks[sys].omega;
+  double rho = 0.0, rr = 0.0;
+  for (int i = tl.row0[t] + threadIdx.x; i < tl.row1[t]; i += NT) {
+    x[i] = fma(omega, sh[i], fma(alpha, ph[i], x[i]));
+    const double ri = fma(-omega, tv[i], sv[i]);
+    r[i] = ri;
+    rho = fma(r0[i], ri, rho);
+    rr = fma(ri, ri, rr);
+  }
+  double in[2] = {rho, rr}, out[2];
+  if (seg_sum<NT, 2>(in, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.iter += 1;
+    k.rr = out[1];
+    bool fin = out[1] <= k.tol2 || k.half || k.iter >= k.maxit;
+    if (!(out[1] == out[1])) { k.breakdown = 1; fin = true; }
+    if (!fin && (!(out[0] != 0.0) || !(k.omega != 0.0))) { k.breakdown = 1; fin = true; }
+    if (!fin) {
+      k.beta = (out[0] / k.rz) * (k.alpha / k.omega);
+      k.rz = out[0];
+    }
+    if (fin) { k.done = 1; atomicAdd(n_done, 1); }
+  }
+}
+
+// p = r + beta (p - omega v)
+__global__ void __launch_bounds__(NT) k_bi_pdir(double *__restrict__ p, const double *__restrict__ r,
+                                                const double *__restrict__ v, Tiles tl, const KrylovScalars *ks) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  if (ks[sys].done) return;
+  const double beta = ks[sys].beta, omega = ks[sys].omega;
+  for (int i = tl.row0[t] + threadIdx.x; i < tl.row1[t]; i += NT) p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+}
+
 }  // namespace
 
 // Rows per tile: 256, one row per thread.  (Tiles of up to 2048 rows, several
@@ -586,6 +728,90 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
       note_launches(1);
     }
   }
+  finish_solve(s, info, false);
+  info->ms_setup = setup_ms;
+  info->ms_solve -= setup_ms;
+}
+
+void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
+  cudaStream_t st = s->ctx->stream;
+  ensure_krylov_buffers(s);
+  tune_sell(s);
+  const bool amg = o->precond == VAG_PC_AMG;
+  const int nt = s->seg.n_tiles;
+  const Tiles tl = tiles_of(s);
+  if (!s->b_r0) {
+    s->b_r0 = sys_alloc<double>(s, s->n_rows);
+    s->b_s = sys_alloc<double>(s, s->n_rows);
+    s->b_sh = sys_alloc<double>(s, s->n_rows);
+    s->b_t = sys_alloc<double>(s, s->n_rows);
+    s->b_ph = sys_alloc<double>(s, s->n_rows);
+  }
+  float setup_ms = 0.f;
+  VAG_CUDA(cudaEventRecord(s->ev0, st));
+  if (amg) {
+    if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
+    amg_setup(s, o->precision == VAG_MIXED);
+    VAG_CUDA(cudaEventRecord(s->ev1, st));
+    VAG_CUDA(cudaEventSynchronize(s->ev1));
+    cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);
+  }
+  auto precond = [&](const double *in, double *out) {
+    if (amg) {
+      amg_apply(s, in, out, st);
+    } else {
+      k_bi_jacobi<<<nt, NT, 0, st>>>(in, s->dinv, out, tl, s->ks);
+      note_launches(1);
+    }
+  };
+  VAG_CUDA(cudaMemsetAsync(s->n_done, 0, sizeof(int), st));
+  k_init_m<<<nt, NT, 0, st>>>(s->rhs, s->kx, s->kr, tl, s->partials, s->counter, s->ks, o->rtol, o->maxit);
+  k_bi_start<<<nt, NT, 0, st>>>(s->kr, s->b_r0, s->kp, tl, s->ks, s->n_done);
+  note_launches(2);
+  VAG_CHECK_LAUNCH();
+  // iterations in a CUDA graph of `chunk` iterations, rebuilt every solve
+  // (the AMG hierarchy's buffers are new each time)
+  const int chunk = 8;
+  if (s->bicg_graph) {
+    cudaGraphExecDestroy(s->bicg_graph);
+    s->bicg_graph = nullptr;
+  }
+  cudaGraph_t graph;
+  VAG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  set_capturing(true);
+  for (int i = 0; i < chunk; ++i) {
+    precond(s->kp, s->b_ph);
+    launch_spmv(s, s->b_ph, s->kq, 0, st);   // v
+    k_bi_alpha<<<nt, NT, 0, st>>>(s->b_r0, s->kq, tl, s->partials, s->counter, s->ks, s->n_done);
+    k_bi_s<<<nt, NT, 0, st>>>(s->kr, s->kq, s->b_s, tl, s->partials, s->counter, s->ks);
+    precond(s->b_s, s->b_sh);
+    launch_spmv(s, s->b_sh, s->b_t, 0, st);  // t
+    k_bi_omega<<<nt, NT, 0, st>>>(s->b_t, s->b_s, tl, s->partials, s->counter, s->ks);
+    k_bi_update<<<nt, NT, 0, st>>>(s->kx, s->kr, s->b_ph, s->b_sh, s->b_s, s->b_t, s->b_r0, tl, s->partials,
+                                   s->counter, s->ks, s->n_done);
+    k_bi_pdir<<<nt, NT, 0, st>>>(s->kp, s->kr, s->kq, tl, s->ks);
+    note_launches(5);
+  }
+  set_capturing(false);
+  VAG_CUDA(cudaStreamEndCapture(st, &graph));
+  size_t nodes = 0;
+  cudaGraphGetNodes(graph, nullptr, &nodes);
+  VAG_CUDA(cudaGraphInstantiate(&s->bicg_graph, graph, 0));
+  cudaGraphDestroy(graph);
+  const int ns = s->seg.n_sys;
+  const int max_chunks = (o->maxit + chunk - 1) / chunk;
+  for (int c = 0; c < max_chunks + 1; ++c) {
+    VAG_CUDA(cudaMemcpyAsync(s->n_done_host, s->n_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VAG_CUDA(cudaStreamSynchronize(st));
+    if (*s->n_done_host >= ns) break;
+    VAG_CUDA(cudaGraphLaunch(s->bicg_graph, st));
+    note_launches(nodes);
+  }
+  // the true residual decides the status
+  launch_spmv(s, s->kx, s->kq, 0, st);
+  k_resid2<<<nt, NT, 0, st>>>(s->rhs, s->kq, tl, s->partials, s->counter, s->ks);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
   finish_solve(s, info, false);
   info->ms_setup = setup_ms;
   info->ms_solve -= setup_ms;

@@ -23,6 +23,7 @@ VAG_EBREAKDOWN, VAG_ETIMEOUT, VAG_ECUDA, VAG_EMESH = 5, 6, 7, 8
 VAG_MEM_HOST, VAG_MEM_DEVICE = 0, 1
 VAG_FP64, VAG_MIXED = 0, 1
 VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG = 0, 1, 2
+VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB = 0, 1
 VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP = 0, 1, 2
 
 STATUS_NAMES = {0: "VAG_OK", 1: "VAG_EINVAL", 2: "VAG_ENOMEM", 3: "VAG_EBUDGET", 4: "VAG_ENOTCONVERGED",
@@ -50,7 +51,7 @@ class vag_system_info(C.Structure):
 
 class vag_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int32),
-                ("mem", C.c_int)]
+                ("mem", C.c_int), ("krylov", C.c_int32)]
 
 
 class vag_solve_info(C.Structure):
@@ -323,13 +324,13 @@ class System:
         self.ctx.check(self._L.vag_update_props(self.h, C.byref(p), mem))
 
     def solve(self, out=None, precision=VAG_FP64, precond=VAG_PC_JACOBI, rtol=1e-12, maxit=20000,
-              raise_on_error=True):
+              raise_on_error=True, krylov=VAG_KRYLOV_CG):
         """Returns (u, info); u over [nodes | ffaces | cells]."""
         n = self.info().n_cv
         if out is None:
             out = np.empty(n)
         mem = _mem_of(out)
-        o = vag_solve_opts(precision, precond, float(rtol), int(maxit), mem)
+        o = vag_solve_opts(precision, precond, float(rtol), int(maxit), mem, int(krylov))
         inf = vag_solve_info()
         st = self._L.vag_solve(self.h, C.byref(o), _ptr(out, np.float64), C.byref(inf))
         if raise_on_error:
