@@ -57,9 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=N_CELLS_EDGE, help="mesh edge (profiling cases only)")
-    ap.add_argument("--workload", default="scale64", choices=["scale64", "batch", "serve", "mixed128"],
-                    help="scale64: the headline line; batch / serve / mixed128: the batched, served and "
-                         "mixed-precision workloads")
+    ap.add_argument("--workload", default="scale64", choices=["scale64", "batch", "serve", "mixed128", "solvers"],
+                    help="scale64: the headline line; batch / serve / mixed128 / solvers: the batched, "
+                         "served and mixed-precision workloads, and the solver comparison")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--requests", type=int, default=400)
     return ap.parse_args()
@@ -478,6 +478,63 @@ def mixed128_arm(args):
     ctx.close()
 
 
+# Iterations of the paper's Table solver_cpg_perm (n_x = 128, N_p = 2; GMRES
+# from PETSc, no restart; "-": no convergence in 1200 iterations), context only.
+PAPER_SOLVER_PERM = {"GMRES + Boomer AMG": {"20": 15, "100": 15, "1000": 16},
+                     "GMRES + Aggregation AMG (Trilinos)": {"20": 59, "100": None, "1000": None},
+                     "GMRES + ILU(0)": {"20": 751, "100": None, "1000": None}}
+
+
+def solvers_arm(args):
+    """The shape of the paper's solver experiment (iterations against the
+    fracture/matrix permeability ratio, §5.3) on the 128^3 DFN of 50
+    rectangles: CG and BiCGStab, each with Jacobi and with the aggregation
+    AMG, FP64, to a 1e-8 relative residual, at ratios 20, 100, 1000 (the
+    paper's) and 1e4, 1e6."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_1602_03641_gb300 as pkg
+    import vag_inputs as vi
+    torch.cuda.set_device(0)
+    n = 128 if args.n == N_CELLS_EDGE else args.n
+    ctx = pkg.Context(0)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    res = {}
+    for ratio in (20.0, 100.0, 1000.0, 1e4, 1e6):
+        pb = vi.config_mixed128(n, ratio)
+        a = pkg.problem_arrays(pb, device=True)
+        s = ctx.assemble(a["xyz"], a["cell_nodes"], a["ff_nodes"], a["lambda_m"], a["lambda_f"], a["d_f"], a["mu"],
+                         a["dir_nodes"], a["dir_values"])
+        u = torch.empty(s.info().n_cv, dtype=torch.float64, device="cuda")
+        row = {}
+        for name, kr, pc in (("CG + Jacobi", pkg.VAG_KRYLOV_CG, pkg.VAG_PC_JACOBI),
+                             ("CG + aggregation AMG", pkg.VAG_KRYLOV_CG, pkg.VAG_PC_AMG),
+                             ("BiCGStab + Jacobi", pkg.VAG_KRYLOV_BICGSTAB, pkg.VAG_PC_JACOBI),
+                             ("BiCGStab + aggregation AMG", pkg.VAG_KRYLOV_BICGSTAB, pkg.VAG_PC_AMG)):
+            s.solve(out=u, precond=pc, rtol=1e-8, maxit=50000, raise_on_error=False, krylov=kr)   # warm-up
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            _, info = s.solve(out=u, precond=pc, rtol=1e-8, maxit=50000, raise_on_error=False, krylov=kr)
+            e1.record(stream)
+            e1.synchronize()
+            row[name] = {"iterations": info.iterations, "ms": e0.elapsed_time(e1), "setup_ms": info.ms_setup,
+                         "rel_residual": info.rel_residual, "status": info.status}
+        res[f"{ratio:g}"] = row
+        s.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "linear solver iterations and time vs fracture/matrix permeability ratio (128^3 DFN)",
+                      "value": res["1000"]["CG + aggregation AMG"]["iterations"],
+                      "unit": "CG + AMG iterations at ratio 1000", "n_gpus": 1, "higher_is_better": False,
+                      "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"solvers: {n}^3 jittered hex, 50 seeded rectangles, rtol 1e-8, "
+                                             "ratios 20/100/1000/1e4/1e6"},
+                      "results": res, "paper_table_solver_cpg_perm_np2": PAPER_SOLVER_PERM}))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -491,6 +548,9 @@ def main():
         return
     if args.workload == "mixed128":
         mixed128_arm(args)
+        return
+    if args.workload == "solvers":
+        solvers_arm(args)
         return
     import torch
     import torch.distributed as dist
