@@ -40,7 +40,11 @@ constexpr double kTheta = 0.08;
 // rows where lambda_max(D^-1 A) > 3 (jittered, anisotropic cells), and the
 // V-cycle then stops being positive definite.
 constexpr double kOmega = 4.0 / 3.0;
-constexpr int kDenseMax = 48;       // two 48x48 FP64 blocks fit the static shared limit
+// A system whose level has at most kDenseMax rows is solved there with a dense
+// inverse: one coarse level less than with 48 (at 64^3 the 61-row level ends
+// the hierarchy), for an inversion of about 0.2 ms on one SM at setup
+constexpr int kDenseMax = 96;
+constexpr size_t kDenseSmem = 2 * sizeof(double) * kDenseMax * kDenseMax;   // [A | B] in dynamic shared memory
 constexpr int kMaxLevels = 16;
 constexpr int kCoarseWidth = 160;   // unique columns of one coarse row (< 256)
 
@@ -374,11 +378,11 @@ __global__ void k_coarse_starts(int n_sys, const int *__restrict__ sys_start, co
 __global__ void k_dense_inverse(const int *__restrict__ sys_start, const int *__restrict__ rowptr,
                                 const int *__restrict__ col, const double *__restrict__ val,
                                 const long long *__restrict__ off, double *inv, int *status) {
-  __shared__ double A[kDenseMax * kDenseMax];
-  __shared__ double B[kDenseMax * kDenseMax];
+  extern __shared__ double dense_sm[];   // kDenseSmem bytes
   const int g = blockIdx.x;
   const int r0 = sys_start[g], m = sys_start[g + 1] - r0;
-  if (m == 0 || off[g + 1] - off[g] != (long long)m * m) return;   // not terminal here
+  if (m == 0 || m > kDenseMax || off[g + 1] - off[g] != (long long)m * m) return;   // not terminal here
+  double *A = dense_sm, *B = dense_sm + m * m;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     A[e] = 0.0;
     B[e] = (e / m == e % m) ? 1.0 : 0.0;
@@ -537,6 +541,45 @@ __global__ void k_resid_sell(int n, const int *__restrict__ rowptr, const int *_
   pdl_trigger();
   if (i >= n) return;
   r[i] = b[i] - sell_row<T, U>(i, rowptr, slice_ptr, scol, sval, x);
+}
+
+// The last finest-level sweep of the V-cycle inside CG (FP64): z = the sweep,
+// and r.z per system formed on the way (r is the level's right-hand side),
+// exactly as the separate r.z kernel would: one row per thread of a 256-row
+// tile, the tile's block sum, the last tile of a system adding the tile
+// partials in order and setting beta = (r.z)' / (r.z) and rho = (r.z)'.
+template <int U>
+__global__ void __launch_bounds__(256) k_jac_sell_rz(const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
+                                                     const int *__restrict__ scol, const double *__restrict__ sval,
+                                                     const double *__restrict__ sinv, const double *__restrict__ r,
+                                                     const double *__restrict__ xin, double *__restrict__ z,
+                                                     const uint8_t *__restrict__ skip, Tiles tl, double *partials,
+                                                     unsigned *counter, KrylovScalars *ks, int *n_done) {
+  const int t = blockIdx.x;
+  const int sys = tl.sys[t];
+  const int i = tl.row0[t] + threadIdx.x;
+  const bool valid = i < tl.row1[t];
+  pdl_wait();
+  pdl_trigger();
+  double rz = 0.0;
+  if (valid) {
+    double zi;
+    if (skip[i]) {
+      zi = z[i];   // solved densely on this level
+    } else {
+      zi = jac_row(xin[i], sinv[i], r[i], sell_row<double, U>(i, rowptr, slice_ptr, scol, sval, xin));
+      z[i] = zi;
+    }
+    rz = fma(r[i], zi, 0.0);
+  }
+  if (ks[sys].done) return;   // uniform in the block: one system per tile
+  double v[1] = {rz}, out[1];
+  if (seg_sum<256, 1>(v, partials, counter, tl, t, sys, out) && threadIdx.x == 0) {
+    KrylovScalars &k = ks[sys];
+    k.beta = out[0] / k.rz;
+    k.rz = out[0];
+    if (!(out[0] > 0.0)) { k.breakdown = 1; k.done = 1; atomicAdd(n_done, 1); }
+  }
 }
 
 // b_c[I] = sum of r over the members of aggregate I (row order)
@@ -997,7 +1040,9 @@ void amg_setup(System *s, bool f32) {
         L.inv_off = static_cast<long long *>(alloc(8 * ((size_t)ns + 1)));
         VAG_CUDA(cudaMemcpyAsync(L.inv_off, off.data(), 8 * (ns + 1), cudaMemcpyHostToDevice, st));
         VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
-        k_dense_inverse<<<ns, TB, 0, st>>>(L.d_sys_start, L.rowptr, L.col, L.val, L.inv_off, L.inv, s->status);
+        VAG_CUDA(cudaFuncSetAttribute(k_dense_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem));
+        k_dense_inverse<<<ns, TB, kDenseSmem, st>>>(L.d_sys_start, L.rowptr, L.col, L.val, L.inv_off, L.inv,
+                                                   s->status);
         note_launches(1);
         VAG_CHECK_LAUNCH();
         if (read_status(s) & ST_NONPOSITIVE) fail(VAG_EINVAL, "AMG: a terminal block is not positive definite");
@@ -1238,13 +1283,16 @@ static void tail(System *s, int lvl, cudaStream_t st) {
 // corrected from the next level and smoothed again.  On coarse levels the
 // first sweep t = omega D_l1^-1 b has already been made by the restriction
 // that produced b.
+// cg: level 0 of the FP64 V-cycle inside CG: its first sweep t = omega
+// D_l1^-1 r was made by the CG update, and its last sweep also forms r.z
+// (returns true when it did)
 template <class T>
-static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
+static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool cg = false) {
   Amg &A = s->amg;
   AmgLevel &L = A.levels[lvl];
   if (lvl > 0 && lvl == A.tail_start) {   // b, x are this level's own b, x
     tail<T>(s, lvl, st);
-    return;
+    return false;
   }
   const LV<T> v = lv<T>(s, L);
   const int n = L.n;
@@ -1254,7 +1302,7 @@ static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
                v.inv, b, x);
     note_launches(1);
   }
-  if (L.all_term) return;
+  if (L.all_term) return false;
   AmgLevel &C = A.levels[lvl + 1];
   const LV<T> c = lv<T>(s, C);
   constexpr int LN = row_lanes<T>();
@@ -1264,14 +1312,14 @@ static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
   auto resid_sell = s->sell_u == 2 ? k_resid_sell<T, 2> : s->sell_u == 8 ? k_resid_sell<T, 8> : k_resid_sell<T, 4>;
   if (lvl == 0) {
     // level 0: sliced ELL, one thread per row
-    launch_pdl(k_jac_first<T>, g, TB, 0, st, n, b, v.sinv, v.t);
+    if (!cg) launch_pdl(k_jac_first<T>, g, TB, 0, st, n, b, v.sinv, v.t);
     launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
     launch_pdl(resid_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
                (const int *)L.scol, v.sval, b, (const T *)x, v.t);
     launch_pdl(k_restrict_first<T>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
                (const T *)v.t, c.sinv, c.b, c.t);
-    note_launches(4);
+    note_launches(cg ? 3 : 4);
   } else {
     // coarse levels: CSR, 8 lanes per row; residual and restriction fused
     launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
@@ -1287,6 +1335,18 @@ static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
     launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, x);
     launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)x, v.t, (const uint8_t *)L.skip);
+    if constexpr (sizeof(T) == 8) {
+      if (cg) {
+      auto jr = s->sell_u == 2 ? k_jac_sell_rz<2> : s->sell_u == 8 ? k_jac_sell_rz<8> : k_jac_sell_rz<4>;
+      const Tiles tl{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0};
+      launch_pdl(jr, s->seg.n_tiles, 256, 0, st, (const int *)L.rowptr, (const int *)L.slice_ptr,
+                 (const int *)L.scol, (const double *)v.sval, (const double *)v.sinv, (const double *)b,
+                 (const double *)v.t, (double *)x, (const uint8_t *)L.skip, tl, s->partials, s->counter, s->ks,
+                 s->n_done);
+      note_launches(3);
+      return true;
+      }
+    }
     launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
     note_launches(3);
@@ -1297,6 +1357,7 @@ static void vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st) {
                (const T *)v.t, x, (const uint8_t *)L.skip);
     note_launches(2);
   }
+  return false;
 }
 
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st) {
@@ -1311,6 +1372,18 @@ void amg_apply(System *s, const double *r, double *z, cudaStream_t st) {
   vcycle<float>(s, 0, L0.b32, L0.x32, st);
   launch_pdl(k_to_f64, grid_for(n, TB), TB, 0, st, n, (const float *)L0.x32, z);
   note_launches(2);
+}
+
+bool amg_apply_cg(System *s, const double *r, double *z, cudaStream_t st) {
+  if (s->amg.f32 || s->amg.levels.empty() || s->amg.levels[0].all_term) return false;
+  return vcycle<double>(s, 0, r, z, st, true);
+}
+
+const double *amg_first_sweep_scale(System *s, double *&t0, double &omega) {
+  if (s->amg.f32 || s->amg.levels.empty() || s->amg.levels[0].all_term) return nullptr;
+  t0 = s->amg.levels[0].t;
+  omega = kOmega;
+  return s->amg.levels[0].sinv;
 }
 
 // Mean duration of one FP64 finest-level sweep (x_out = x_in + omega

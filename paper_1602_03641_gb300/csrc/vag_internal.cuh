@@ -346,6 +346,13 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void amg_setup(System *s, bool f32);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
+// The FP64 V-cycle inside CG: amg_first_sweep_scale gives the finest level's
+// l1 scaling, its first-sweep buffer t0 and omega (null for the FP32
+// hierarchy or a hierarchy without coarse levels) so that the CG update can
+// make the first sweep t0 = omega D_l1^-1 r; amg_apply_cg then runs the rest of
+// the cycle and forms r.z (beta, rho) in its last sweep.
+const double *amg_first_sweep_scale(System *s, double *&t0, double &omega);
+bool amg_apply_cg(System *s, const double *r, double *z, cudaStream_t st);
 void amg_free(System *s);
 // choose (once per context and matrix size class) the loads in flight of the
 // sliced-ELL row loop by timing the candidates on this system's matrix;

@@ -226,9 +226,13 @@ __global__ void __launch_bounds__(NT) k_rz_start(const double *__restrict__ r, c
 
 // x += alpha p, r -= alpha q, partial r.r; the last tile counts the iteration
 // and tests convergence
+// With sinv0 set, also the first sweep of the AMG V-cycle from zero,
+// t0 = omega D_l1^-1 r (the same product the V-cycle would form).
 __global__ void __launch_bounds__(NT) k_update_m(double *__restrict__ x, double *__restrict__ r,
                                                  const double *__restrict__ p, const double *__restrict__ q, Tiles tl,
-                                                 double *partials, unsigned *counter, KrylovScalars *ks, int *n_done) {
+                                                 double *partials, unsigned *counter, KrylovScalars *ks, int *n_done,
+                                                 const double *__restrict__ sinv0, double *__restrict__ t0,
+                                                 double omega) {
   const int t = blockIdx.x;
   const int sys = tl.sys[t];
   const int r0 = tl.row0[t], r1 = tl.row1[t];
@@ -241,6 +245,7 @@ __global__ void __launch_bounds__(NT) k_update_m(double *__restrict__ x, double 
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
+    if (sinv0) t0[i] = omega * sinv0[i] * ri;
     rr = fma(ri, ri, rr);
   }
   double v[1] = {rr}, out[1];
@@ -607,13 +612,19 @@ static void pcg_iteration_amg(System *s, cudaStream_t st) {
   const Tiles tl = tiles_of(s);
   const int nt = s->seg.n_tiles;
   launch_spmv(s, s->kp, s->kq, 1, st);
+  double *t0 = nullptr;
+  double omega = 0.0;
+  const double *sinv0 = amg_first_sweep_scale(s, t0, omega);
   launch_pdl(k_update_m, nt, NT, 0, st, s->kx, s->kr, (const double *)s->kp, (const double *)s->kq, tl, s->partials,
-             s->counter, s->ks, s->n_done);
-  amg_apply(s, s->kr, s->kz, st);
-  launch_pdl(k_rz, nt, NT, 0, st, (const double *)s->kr, (const double *)s->kz, tl, s->partials, s->counter, s->ks,
-             s->n_done);
+             s->counter, s->ks, s->n_done, sinv0, t0, omega);
+  const bool rz_done = sinv0 ? amg_apply_cg(s, s->kr, s->kz, st) : (amg_apply(s, s->kr, s->kz, st), false);
+  if (!rz_done) {
+    launch_pdl(k_rz, nt, NT, 0, st, (const double *)s->kr, (const double *)s->kz, tl, s->partials, s->counter, s->ks,
+               s->n_done);
+    note_launches(1);
+  }
   launch_pdl(k_pdir_z, nt, NT, 0, st, s->kp, (const double *)s->kz, tl, (const KrylovScalars *)s->ks);
-  note_launches(3);
+  note_launches(2);
 }
 
 static void pcg_iteration(System *s, cudaStream_t st) {
