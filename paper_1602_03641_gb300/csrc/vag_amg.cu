@@ -508,6 +508,25 @@ __global__ void k_jac_first(int n, const T *__restrict__ b, const T *__restrict_
   if (i < n) x[i] = jac_first_row(b[i], sinv[i]);
 }
 
+// r = b - A x on a coarse level, row_lanes<T>() lanes per row (used with the
+// restriction as a separate kernel where aggregates are large: the fused
+// kernel walks an aggregate's members four at a time)
+template <class T>
+__global__ void __launch_bounds__(256) k_resid_csr(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                                   const T *__restrict__ val, const T *__restrict__ b,
+                                                   const T *__restrict__ x, T *__restrict__ r) {
+  constexpr int LN = row_lanes<T>();
+  const int lane = threadIdx.x & (LN - 1);
+  const int i = blockIdx.x * (256 / LN) + threadIdx.x / LN;
+  const bool valid = i < n;
+  RowPF<T> f;
+  row_prefetch<LN>(f, i, valid, lane, rowptr, col, val);
+  pdl_wait();
+  pdl_trigger();
+  const T s = row_finish<LN>(f, col, val, x);
+  if (valid && lane == 0) r[i] = b[i] - s;
+}
+
 // x_out = x_in + omega D_l1^-1 (b - A x_in) on a coarse level, row_lanes<T>()
 // lanes per row (256 / LN rows per block); rows of systems solved densely here
 // are skipped
@@ -1336,9 +1355,17 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
     // coarse levels: CSR, 8 lanes per row; residual and restriction fused
     launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
                (const T *)v.t, x, (const uint8_t *)L.skip);
-    launch_pdl(k_resid_restrict8<T>, grid_for(C.n, 8), 256, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
-               (const int *)L.rowptr, (const int *)L.col, v.val, b, (const T *)x, c.sinv, c.b, c.t);
-    note_launches(2);
+    if (n > 6 * C.n) {   // large aggregates: residual over all rows, then restriction
+      launch_pdl(k_resid_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, b,
+                 (const T *)x, v.t);
+      launch_pdl(k_restrict_first<T>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
+                 (const T *)v.t, c.sinv, c.b, c.t);
+      note_launches(3);
+    } else {
+      launch_pdl(k_resid_restrict8<T>, grid_for(C.n, 8), 256, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
+                 (const int *)L.rowptr, (const int *)L.col, v.val, b, (const T *)x, c.sinv, c.b, c.t);
+      note_launches(2);
+    }
   }
   vcycle<T>(s, lvl + 1, c.b, c.x, st);
   // post-smoothing: two sweeps (on coarse levels the first one applies the
