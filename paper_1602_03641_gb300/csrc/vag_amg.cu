@@ -637,13 +637,25 @@ template <class T>
 __global__ void k_restrict_first(int nc, const int *__restrict__ mptr, const int *__restrict__ mem,
                                  const T *__restrict__ r, const T *__restrict__ sinv_c, T *__restrict__ bc,
                                  T *__restrict__ tc) {
+  // the aggregate's first members and the scaling (written by no kernel of
+  // the cycle) before the dependency wait; the sum keeps the member order
+  constexpr int PF = 12;
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p0 = I < nc ? mptr[I] : 0, p1 = I < nc ? mptr[I + 1] : 0;
+  int m[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) m[u] = p0 + u < p1 ? mem[p0 + u] : 0;
+  const T si = I < nc ? sinv_c[I] : (T)0;
   pdl_wait();
   pdl_trigger();
   if (I >= nc) return;
-  const T v = restrict_row(I, mptr, mem, r);
+  T v = 0;
+#pragma unroll
+  for (int u = 0; u < PF; ++u)
+    if (p0 + u < p1) v += r[m[u]];
+  for (int p = p0 + PF; p < p1; ++p) v += r[mem[p]];
   bc[I] = v;
-  tc[I] = jac_first_row(v, sinv_c[I]);
+  tc[I] = jac_first_row(v, si);
 }
 
 // Residual of a coarse level, restricted and turned into the next level's
