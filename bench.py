@@ -421,6 +421,7 @@ def mixed128_arm(args):
         res = {"n_rows": inf.n_rows, "nnz": inf.nnz, "n_ff": pb.n_ff, "reference_rel_residual": iref.rel_residual}
         u = torch.empty_like(u_ref)
         for name, prec, pc in (("fp64_amg", pkg.VAG_FP64, pkg.VAG_PC_AMG), ("mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG),
+                               ("mixed16_amg", pkg.VAG_MIXED_F16, pkg.VAG_PC_AMG),
                                ("fp64_jacobi", pkg.VAG_FP64, pkg.VAG_PC_JACOBI),
                                ("mixed_jacobi", pkg.VAG_MIXED, pkg.VAG_PC_JACOBI)):
             times = []
@@ -684,7 +685,8 @@ def main():
     # preconditioned by the FP32 copy of the AMG hierarchy.
     cmp = {}
     for name, prec, pc in (("fp64_jacobi", pkg.VAG_FP64, pkg.VAG_PC_JACOBI), ("mixed_jacobi", pkg.VAG_MIXED, pkg.VAG_PC_JACOBI),
-                           ("fp64_amg", pkg.VAG_FP64, pkg.VAG_PC_AMG), ("mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG)):
+                           ("fp64_amg", pkg.VAG_FP64, pkg.VAG_PC_AMG), ("mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG),
+                           ("mixed16_amg", pkg.VAG_MIXED_F16, pkg.VAG_PC_AMG)):
         step_device_prec(prec, pc, 1e-8)
         ms_c, inf_c = timed(lambda: step_device_prec(prec, pc, 1e-8), max(3, args.steps // 2))
         cmp[name] = {"solves_per_s": len(ms_c) / (sum(ms_c) / 1e3), "ms_per_step": sum(ms_c) / len(ms_c),

@@ -48,7 +48,10 @@ enum {
 };
 
 enum { VAG_MEM_HOST = 0, VAG_MEM_DEVICE = 1 };
-enum { VAG_FP64 = 0, VAG_MIXED = 1 };
+/* VAG_MIXED_F16: VAG_MIXED with the AMG V-cycle's finest-level matrix stored
+ * in FP16 after symmetric diagonal scaling (D^-1/2 A D^-1/2, entries in
+ * [-1, 1]); VAG_PC_AMG only. */
+enum { VAG_FP64 = 0, VAG_MIXED = 1, VAG_MIXED_F16 = 2 };
 enum { VAG_PC_JACOBI = 0, VAG_PC_CHEBYSHEV = 1, VAG_PC_AMG = 2 };
 /* Krylov method: CG (the system is SPD) or BiCGStab, the method of the
  * paper's solver experiments (§5.3), right-preconditioned. */

@@ -992,6 +992,109 @@ __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailDesc<T> d, int
   }
 }
 
+// ---- the finest level in scaled variables, matrix in FP16 (VAG_MIXED_F16) ----
+// With S = D^-1/2 and h = S A S (FP16), the level works on x~ = S^-1 x and
+// b~ = S b: a sweep is x~ += omega D_h^-1 (b~ - h x~) with the l1 scaling of h,
+// the residual handed to the restriction is S^-1 (b~ - h x~) = b - A x, the
+// coarse correction enters as x~ += S^-1 P x_c, and z = S x~ on the way out.
+
+__global__ void k_scale_setup(int n, const double *__restrict__ dinv, double *__restrict__ s0d,
+                              float *__restrict__ s0f, double *__restrict__ sm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = sqrt(1.0 / dinv[i]);   // sqrt(a_ii)
+  s0d[i] = d;
+  s0f[i] = (float)d;
+  sm[i] = 1.0 / d;                        // the D^-1/2 of the FP16 copy
+}
+
+// l1 scaling of the stored FP16 rows: 1 / sum_j |h_ij|
+__global__ void k_l1_inv_h(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
+                           const __half *__restrict__ sval, float *__restrict__ sinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int len = rowptr[i + 1] - rowptr[i];
+  const int base = slice_ptr[i >> 5] + (i & 31);
+  float a = 0.f;
+  for (int k = 0; k < len; ++k) a += fabsf(__half2float(sval[base + 32 * k]));
+  sinv[i] = 1.f / a;
+}
+
+// b~ = S r (FP64 in, FP32 out)
+__global__ void k_to_f32_scaled(int n, const double *__restrict__ r, const double *__restrict__ s0d,
+                                float *__restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double si = i < n ? s0d[i] : 1.0;
+  pdl_wait();
+  pdl_trigger();
+  if (i < n) b[i] = (float)(r[i] / si);
+}
+
+// z = S x~ (FP32 in, FP64 out)
+__global__ void k_to_f64_scaled(int n, const float *__restrict__ x, const double *__restrict__ s0d,
+                                double *__restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double si = i < n ? s0d[i] : 1.0;
+  pdl_wait();
+  pdl_trigger();
+  if (i < n) z[i] = (double)x[i] / si;
+}
+
+template <int U>
+__global__ void k_jac_sell_h(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
+                             const int *__restrict__ scol, const __half *__restrict__ sval,
+                             const float *__restrict__ sinv, const float *__restrict__ b,
+                             const float *__restrict__ xin, float *__restrict__ xout, const uint8_t *__restrict__ skip) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
+  if (i >= n || skip[i]) return;
+  xout[i] = jac_row(xin[i], sinv[i], b[i], sell_row<float, U, __half>(i, rowptr, slice_ptr, scol, sval, xin));
+}
+
+// unscaled residual b - A x = S^-1 (b~ - h x~) for the restriction
+template <int U>
+__global__ void k_resid_sell_h(int n, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
+                               const int *__restrict__ scol, const __half *__restrict__ sval,
+                               const float *__restrict__ s0f, const float *__restrict__ b,
+                               const float *__restrict__ x, float *__restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
+  if (i >= n) return;
+  r[i] = s0f[i] * (b[i] - sell_row<float, U, __half>(i, rowptr, slice_ptr, scol, sval, x));
+}
+
+// a system solved densely on the finest level, in scaled variables:
+// x~ = S^-1 A^-1 S^-1 b~ (S^-1 = diag(s0f))
+__global__ void k_dense_apply_scaled(const int *__restrict__ sys_start, const long long *__restrict__ off,
+                                     const float *__restrict__ inv, const float *__restrict__ s0f,
+                                     const float *__restrict__ b, float *x) {
+  const int g = blockIdx.x;
+  const int r0 = sys_start[g], m = sys_start[g + 1] - r0;
+  const bool term = m > 0 && off[g + 1] - off[g] == (long long)m * m;
+  pdl_wait();
+  pdl_trigger();
+  if (!term) return;
+  const float *M = inv + off[g];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    float acc = 0.f;
+    for (int j = 0; j < m; ++j) acc = fmaf(M[i * m + j], s0f[r0 + j] * b[r0 + j], acc);
+    x[r0 + i] = s0f[r0 + i] * acc;
+  }
+}
+
+// x~ += S^-1 P x_c
+__global__ void k_prolong_scaled(int n, const int *__restrict__ agg, const float *__restrict__ s0f,
+                                 const float *__restrict__ xc, float *x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = i < n ? agg[i] : -1;
+  const float si = i < n ? s0f[i] : 0.f;
+  pdl_wait();
+  pdl_trigger();
+  if (J >= 0) x[i] += si * xc[J];
+}
+
 __global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   pdl_wait();
@@ -1011,7 +1114,7 @@ __global__ void k_to_f64(int n, const float *__restrict__ a, double *__restrict_
 
 // Build the hierarchy for the current matrix values (called before every
 // AMG solve: the numeric phase may have changed them).
-void amg_setup(System *s, bool f32) {
+void amg_setup(System *s, bool f32, bool f16) {
   cudaStream_t st = s->ctx->stream;
   Amg &A = s->amg;
   const int ns = s->seg.n_sys;
@@ -1194,6 +1297,7 @@ void amg_setup(System *s, bool f32) {
   }
   // FP32 copy of the hierarchy (the mixed-precision path)
   A.f32 = f32;
+  A.f16 = false;
   if (f32) {
     auto cast = [&](const double *src, int64_t n) -> float * {
       float *d = static_cast<float *>(alloc(4 * (size_t)std::max<int64_t>(n, 1)));
@@ -1205,6 +1309,20 @@ void amg_setup(System *s, bool f32) {
     };
     A.sval32 = static_cast<float *>(alloc(4 * (size_t)std::max<int64_t>(s->sell_nnz, 1)));
     sell_values_f32(s, A.sval32);
+    A.f16 = f16;
+    if (A.f16) {
+      const int n0 = s->n_rows;
+      A.s0d = static_cast<double *>(alloc(8 * (size_t)std::max(n0, 1)));
+      A.s0f = static_cast<float *>(alloc(4 * (size_t)std::max(n0, 1)));
+      double *sm = static_cast<double *>(alloc(8 * (size_t)std::max(n0, 1)));
+      A.sval16 = static_cast<__half *>(alloc(2 * (size_t)std::max<int64_t>(s->sell_nnz, 1)));
+      A.sinv16 = static_cast<float *>(alloc(4 * (size_t)std::max(n0, 1)));
+      k_scale_setup<<<grid_for(n0, TB), TB, 0, st>>>(n0, s->dinv, A.s0d, A.s0f, sm);
+      note_launches(1);
+      sell_values_scaled_f16(s, sm, A.sval16);
+      k_l1_inv_h<<<grid_for(n0, TB), TB, 0, st>>>(n0, s->rowptr, s->slice_ptr, A.sval16, A.sinv16);
+      note_launches(1);
+    }
     for (size_t l = 0; l < A.levels.size(); ++l) {
       AmgLevel &L = A.levels[l];
       if (l == 0) {
@@ -1341,8 +1459,13 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
   const int n = L.n;
   const int g = grid_for(n, TB);
   if (L.any_term) {
-    launch_pdl(k_dense_apply<T>, s->seg.n_sys, 64, 0, st, (const int *)L.d_sys_start, (const long long *)L.inv_off,
-               v.inv, b, x);
+    if (sizeof(T) == 4 && lvl == 0 && A.f16)
+      launch_pdl(k_dense_apply_scaled, s->seg.n_sys, 64, 0, st, (const int *)L.d_sys_start,
+                 (const long long *)L.inv_off, (const float *)L.inv32, (const float *)A.s0f, (const float *)b,
+                 (float *)x);
+    else
+      launch_pdl(k_dense_apply<T>, s->seg.n_sys, 64, 0, st, (const int *)L.d_sys_start,
+                 (const long long *)L.inv_off, v.inv, b, x);
     note_launches(1);
   }
   if (L.all_term) return false;
@@ -1353,7 +1476,22 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
   // finest level: the autotuned loads in flight of the sliced-ELL row loop
   auto jac_sell = s->sell_u == 2 ? k_jac_sell<T, 2> : s->sell_u == 8 ? k_jac_sell<T, 8> : k_jac_sell<T, 4>;
   auto resid_sell = s->sell_u == 2 ? k_resid_sell<T, 2> : s->sell_u == 8 ? k_resid_sell<T, 8> : k_resid_sell<T, 4>;
-  if (lvl == 0) {
+  const bool h16 = sizeof(T) == 4 && lvl == 0 && A.f16;   // scaled FP16 finest level
+  auto jac_h = s->sell_u == 2 ? k_jac_sell_h<2> : s->sell_u == 8 ? k_jac_sell_h<8> : k_jac_sell_h<4>;
+  if (h16) {
+    const float *bb = (const float *)b;
+    float *xx = (float *)x, *tt = A.levels[0].t32;
+    const LV<float> c32 = lv<float>(s, C);
+    auto resid_h = s->sell_u == 2 ? k_resid_sell_h<2> : s->sell_u == 8 ? k_resid_sell_h<8> : k_resid_sell_h<4>;
+    launch_pdl(k_jac_first<float>, g, TB, 0, st, n, bb, (const float *)A.sinv16, tt);
+    launch_pdl(jac_h, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+               (const __half *)A.sval16, (const float *)A.sinv16, bb, (const float *)tt, xx, (const uint8_t *)L.skip);
+    launch_pdl(resid_h, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+               (const __half *)A.sval16, (const float *)A.s0f, bb, (const float *)xx, tt);
+    launch_pdl(k_restrict_first<float>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
+               (const float *)tt, c32.sinv, c32.b, c32.t);
+    note_launches(4);
+  } else if (lvl == 0) {
     // level 0: sliced ELL, one thread per row
     if (!cg) launch_pdl(k_jac_first<T>, g, TB, 0, st, n, b, v.sinv, v.t);
     launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
@@ -1382,7 +1520,17 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
   vcycle<T>(s, lvl + 1, c.b, c.x, st);
   // post-smoothing: two sweeps (on coarse levels the first one applies the
   // coarse correction as it reads x)
-  if (lvl == 0) {
+  if (h16) {
+    const float *bb = (const float *)b;
+    float *xx = (float *)x, *tt = A.levels[0].t32;
+    launch_pdl(k_prolong_scaled, g, TB, 0, st, n, (const int *)L.agg, (const float *)A.s0f,
+               (const float *)A.levels[1].x32, xx);
+    launch_pdl(jac_h, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+               (const __half *)A.sval16, (const float *)A.sinv16, bb, (const float *)xx, tt, (const uint8_t *)L.skip);
+    launch_pdl(jac_h, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+               (const __half *)A.sval16, (const float *)A.sinv16, bb, (const float *)tt, xx, (const uint8_t *)L.skip);
+    note_launches(3);
+  } else if (lvl == 0) {
     launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, x);
     launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)x, v.t, (const uint8_t *)L.skip);
@@ -1419,6 +1567,13 @@ void amg_apply(System *s, const double *r, double *z, cudaStream_t st) {
   }
   AmgLevel &L0 = A.levels[0];
   const int n = L0.n;
+  if (A.f16) {   // scaled variables on the finest level
+    launch_pdl(k_to_f32_scaled, grid_for(n, TB), TB, 0, st, n, r, (const double *)A.s0d, L0.b32);
+    vcycle<float>(s, 0, L0.b32, L0.x32, st);
+    launch_pdl(k_to_f64_scaled, grid_for(n, TB), TB, 0, st, n, (const float *)L0.x32, (const double *)A.s0d, z);
+    note_launches(2);
+    return;
+  }
   launch_pdl(k_to_f32, grid_for(n, TB), TB, 0, st, (int64_t)n, r, L0.b32);
   vcycle<float>(s, 0, L0.b32, L0.x32, st);
   launch_pdl(k_to_f64, grid_for(n, TB), TB, 0, st, n, (const float *)L0.x32, z);

@@ -408,7 +408,10 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     if (!opts) fail(VAG_EINVAL, "null options");
     check_mem(opts->mem);
     if (!(opts->rtol > 0.0) || opts->maxit <= 0) fail(VAG_EINVAL, "rtol must be > 0 and maxit > 0");
-    if (opts->precision != VAG_FP64 && opts->precision != VAG_MIXED) fail(VAG_EINVAL, "unknown precision");
+    if (opts->precision != VAG_FP64 && opts->precision != VAG_MIXED && opts->precision != VAG_MIXED_F16)
+      fail(VAG_EINVAL, "unknown precision");
+    if (opts->precision == VAG_MIXED_F16 && opts->precond != VAG_PC_AMG)
+      fail(VAG_EINVAL, "VAG_MIXED_F16 stores the AMG finest level in FP16: it needs VAG_PC_AMG");
     if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_AMG)
       fail(VAG_EINVAL, "preconditioner not available in this build");
     use_device(s->ctx);

@@ -1,6 +1,7 @@
 // Internal declarations of the VAG CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -126,6 +127,12 @@ struct Amg {
   int tail_start = -1;             // first level run by the one-kernel tail
   size_t tail_smem[2] = {0, 0};    // its dynamic shared memory (FP64, FP32)
   float *sval32 = nullptr;         // FP32 sliced-ELL values of A (finest level)
+  // VAG_MIXED_F16: the finest level in scaled variables (x~ = D^1/2 x),
+  // h = D^-1/2 A D^-1/2 in FP16 (sliced ELL), its l1 scaling, and D^1/2
+  bool f16 = false;
+  __half *sval16 = nullptr;
+  float *sinv16 = nullptr, *s0f = nullptr;
+  double *s0d = nullptr;
 };
 
 // State of the mixed-precision solve (FP32 inner CG inside FP64 refinement).
@@ -276,9 +283,12 @@ void sys_free_all(System *s);
 // vag_krylov.cu; the FMA sequence, hence the result, is the same for every
 // U).  (A loop over the uniform slice width with eight in flight, padding
 // included, measured 10-20 % slower on GB300.)
-template <class T, int U = 4>
+__device__ __forceinline__ float sell_val(__half v) { return __half2float(v); }
+__device__ __forceinline__ float sell_val(float v) { return v; }
+__device__ __forceinline__ double sell_val(double v) { return v; }
+template <class T, int U = 4, class V = T>
 __device__ __forceinline__ T sell_row(int row, const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
-                                      const int *__restrict__ scol, const T *__restrict__ sval,
+                                      const int *__restrict__ scol, const V *__restrict__ sval,
                                       const T *__restrict__ x) {
   const int len = rowptr[row + 1] - rowptr[row];
   const int base = slice_ptr[row >> 5] + (row & 31);
@@ -286,7 +296,7 @@ __device__ __forceinline__ T sell_row(int row, const int *__restrict__ rowptr, c
 #pragma unroll(U)
   for (int k = 0; k < len; ++k) {
     const int idx = base + 32 * k;
-    s = fma(sval[idx], x[scol[idx]], s);
+    s = fma((T)sell_val(sval[idx]), x[scol[idx]], s);
   }
   return s;
 }
@@ -344,7 +354,7 @@ void symbolic_phase(System *s);
 void numeric_phase(System *s);
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
-void amg_setup(System *s, bool f32);
+void amg_setup(System *s, bool f32, bool f16 = false);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
 // The FP64 V-cycle inside CG: amg_first_sweep_scale gives the finest level's
 // l1 scaling, its first-sweep buffer t0 and omega (null for the FP32
@@ -373,6 +383,7 @@ void build_sell(System *s);
 void sell_values(System *s);
 void sell_values_scaled_f32(System *s, const double *scale, float *out);
 void sell_values_f32(System *s, float *out);
+void sell_values_scaled_f16(System *s, const double *scale, __half *out);
 int64_t sell_structure(cudaStream_t st, int n, const int *rowptr, const int *col, int **slice_ptr_out,
                        int **scol_out, const std::function<void *(size_t)> &alloc);
 void solve_infos(const System *s, vag_solve_info *infos);

@@ -649,7 +649,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   if (amg) {
     if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
-    amg_setup(s, o->precision == VAG_MIXED);
+    amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16);
     trace_mark(st, "AMG setup");
     VAG_CUDA(cudaEventRecord(s->ev1, st));
     VAG_CUDA(cudaEventSynchronize(s->ev1));
@@ -762,7 +762,7 @@ void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   if (amg) {
     if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
-    amg_setup(s, o->precision == VAG_MIXED);
+    amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16);
     VAG_CUDA(cudaEventRecord(s->ev1, st));
     VAG_CUDA(cudaEventSynchronize(s->ev1));
     cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);

@@ -45,6 +45,11 @@ __global__ void k_sell_pad(int n, const int *__restrict__ rowptr, const int *__r
 }
 
 template <class T>
+__device__ __forceinline__ T to_store(double v) { return (T)v; }
+template <>
+__device__ __forceinline__ __half to_store<__half>(double v) { return __double2half(v); }
+
+template <class T>
 __global__ void k_sell_vals(int n, const int *__restrict__ rowptr, const double *__restrict__ val,
                             const double *__restrict__ scale, const int *__restrict__ col,
                             const int *__restrict__ slice_ptr, T *__restrict__ sval) {
@@ -55,11 +60,11 @@ __global__ void k_sell_vals(int n, const int *__restrict__ rowptr, const double 
   const double sr = scale ? scale[row] : 1.0;
   for (int k = 0; k < e - b; ++k) {
     const double v = scale ? sr * val[b + k] * scale[col[b + k]] : val[b + k];
-    sval[base + 32 * k] = (T)v;
+    sval[base + 32 * k] = to_store<T>(v);
   }
   // padding up to the slice width: value 0 (its column is the row itself)
   const int w = (slice_ptr[(row >> 5) + 1] - slice_ptr[row >> 5]) >> 5;
-  for (int k = e - b; k < w; ++k) sval[base + 32 * k] = (T)0;
+  for (int k = e - b; k < w; ++k) sval[base + 32 * k] = to_store<T>(0.0);
 }
 
 }  // namespace
@@ -116,5 +121,15 @@ void sell_values_scaled_f32(System *s, const double *scale, float *out) {
 }
 
 void sell_values_f32(System *s, float *out) { sell_values_scaled_f32(s, nullptr, out); }
+
+// FP16 copy of D^{-1/2} A D^{-1/2} (scale = D^{-1/2}, FP64): unit diagonal,
+// off-diagonal entries in [-1, 1], so FP16 keeps about three digits of each.
+void sell_values_scaled_f16(System *s, const double *scale, __half *out) {
+  cudaStream_t st = s->ctx->stream;
+  k_sell_vals<__half><<<grid_for(s->n_rows, TB), TB, 0, st>>>(s->n_rows, s->rowptr, s->val, scale, s->col,
+                                                               s->slice_ptr, out);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
+}
 
 }  // namespace vag

@@ -143,3 +143,52 @@ def test_amg_on_rows_where_damped_jacobi_diverges(ctx, index):
         assert info.rel_residual <= 1e-11, (info.status, info.rel_residual)
         ref = vo.DarcyTransport(pb)
         assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["scale_14x11x12", "dfn16_1e6", "fourfrac24"])
+def test_fp16_finest_level_preconditions_fp64_cg(ctx, name):
+    """VAG_MIXED_F16: the V-cycle's finest level in FP16 after symmetric
+    diagonal scaling, inside FP64 CG: FP64 accuracy, a few more iterations at
+    most."""
+    import paper_1602_03641_gb300 as pkg
+    pb = CASES[name]()
+    ref = vo.DarcyTransport(pb)
+    s = pkg.assemble_problem(ctx, pb)
+    u, info = s.solve(precision=pkg.VAG_MIXED_F16, precond=pkg.VAG_PC_AMG, rtol=1e-12, maxit=2000,
+                      raise_on_error=False)
+    assert info.rel_residual <= 1e-11, (info.rel_residual, info.iterations)
+    assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-10
+    _, i32 = s.solve(precision=pkg.VAG_MIXED, precond=pkg.VAG_PC_AMG, rtol=1e-12, maxit=2000, raise_on_error=False)
+    assert info.iterations <= i32.iterations + 20, (info.iterations, i32.iterations)
+    s.close()
+
+
+def test_fp16_finest_level_batch_equals_alone_bitwise(ctx):
+    """Including a system solved densely on its finest level (one cell)."""
+    import paper_1602_03641_gb300 as pkg
+    pbs = [vi.random_dfn_problem(14, 7, 1e4, seed=13), vi.build_problem((1, 1, 1), []), vi.config_plain16(7)]
+    bs = ctx.assemble_batch([pkg.problem_arrays(p) for p in pbs])
+    lay = bs.batch_layout()
+    nv, nf = lay["node_start"][-1], lay["ff_start"][-1]
+    ub, _ = bs.solve(precision=pkg.VAG_MIXED_F16, precond=pkg.VAG_PC_AMG, rtol=1e-10, maxit=2000,
+                     raise_on_error=False)
+    infos = bs.solve_infos()
+    ns, fs, cs = lay["node_start"], lay["ff_start"], lay["cell_start"]
+    for i, pb in enumerate(pbs):
+        s1 = pkg.assemble_problem(ctx, pb)
+        u1, inf1 = s1.solve(precision=pkg.VAG_MIXED_F16, precond=pkg.VAG_PC_AMG, rtol=1e-10, maxit=2000,
+                            raise_on_error=False)
+        ui = np.concatenate([ub[ns[i]:ns[i + 1]], ub[nv + fs[i]:nv + fs[i + 1]], ub[nv + nf + cs[i]:nv + nf + cs[i + 1]]])
+        np.testing.assert_array_equal(ui, u1)
+        assert infos[i].iterations == inf1.iterations
+        assert inf1.rel_residual <= 1e-10
+        s1.close()
+    bs.close()
+
+
+def test_fp16_needs_amg(ctx):
+    import paper_1602_03641_gb300 as pkg
+    s = pkg.assemble_problem(ctx, vi.config_plain16(6))
+    _, info = s.solve(precision=pkg.VAG_MIXED_F16, precond=pkg.VAG_PC_JACOBI, raise_on_error=False)
+    assert info.ret == pkg.VAG_EINVAL
+    s.close()
