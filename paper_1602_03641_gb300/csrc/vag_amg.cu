@@ -1,10 +1,11 @@
 // Aggregation algebraic multigrid preconditioner for the eliminated VAG
 // system (the paper's §5 compares Trilinos aggregation AMG and Hypre's
 // classical AMG as GMRES/BiCGStab preconditioners; this is the library's own
-// aggregation AMG, used inside CG).
+// aggregation AMG, used inside CG or BiCGStab).
 //
 // Setup, level by level, all on the device:
-//  strength   j is a strong neighbour of i if |a_ij| >= theta sqrt(a_ii a_jj);
+//  strength   j is a strong neighbour of i if |a_ij| >= theta sqrt(a_ii a_jj)
+//             (theta per level and system, see kTheta);
 //  MIS(2)     roots: undecided nodes whose key is the largest within two
 //             strong hops (keys hash the system-local row index, so a system's
 //             hierarchy does not depend on the rest of a batch); nodes within
@@ -12,14 +13,17 @@
 //  aggregates a root and its strong neighbours, then every remaining node
 //             joins the aggregate of its strongest aggregated neighbour; nodes
 //             without a strong neighbour stay out of the coarse space;
-//  Galerkin   A_c = P^T A P for the piecewise-constant P, one thread per
-//             coarse row summing its members' rows in row order;
+//  Galerkin   A_c = P^T A P for the piecewise-constant P, one warp per
+//             coarse row summing its members' rows in row order (entries of a
+//             coarse column added in that order; columns sorted);
 //  terminal   a system whose level has at most kDenseMax rows leaves the
 //             hierarchy there: its block is inverted densely (Gauss-Jordan,
 //             SPD) and applied exactly in the cycle.  The depth of a system's
 //             hierarchy therefore depends on that system alone.
 // Apply: a V(2,2) cycle with l1-Jacobi sweeps before and after the coarse
-// correction; it is a fixed symmetric linear operator, as CG needs.
+// correction; it is a fixed symmetric linear operator, as CG needs.  FP64, or
+// on an FP32 copy of the hierarchy (VAG_MIXED; VAG_MIXED_F16 also keeps the
+// finest level in FP16 after symmetric diagonal scaling).
 #include <climits>
 #include <cstdio>
 
@@ -49,8 +53,8 @@ constexpr int kSmallLevel = 50000;
 // V-cycle then stops being positive definite.
 constexpr double kOmega = 4.0 / 3.0;
 // A system whose level has at most kDenseMax rows is solved there with a dense
-// inverse: one coarse level less than with 48 (at 64^3 the 61-row level ends
-// the hierarchy), for an inversion of about 0.2 ms on one SM at setup
+// inverse (an inversion of at most about 0.2 ms on one SM at setup, against
+// four latency-bound launches per V-cycle for every level it saves)
 constexpr int kDenseMax = 96;
 constexpr size_t kDenseSmem = 2 * sizeof(double) * kDenseMax * kDenseMax;   // [A | B] in dynamic shared memory
 constexpr int kMaxLevels = 16;
