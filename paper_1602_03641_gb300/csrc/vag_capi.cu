@@ -1,6 +1,8 @@
 // extern "C" entry points of libvag (declared in include/vag.h): argument
 // checks, host/device staging, and the mapping of internal errors to status
 // codes.  No exception crosses this boundary.
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstring>
 #include <memory>
 
@@ -27,6 +29,14 @@ vag_status guarded(Ctx *c, F &&f) {
     return VAG_ECUDA;
   }
 }
+
+// NVTX range around an API call (visible to Nsight tools; a no-op without one)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 void check_mem(int mem) {
   if (mem != VAG_MEM_HOST && mem != VAG_MEM_DEVICE) fail(VAG_EINVAL, "mem must be VAG_MEM_HOST or VAG_MEM_DEVICE");
@@ -178,6 +188,7 @@ unsigned long long vag_launch_count(void) { return launches_so_far(); }
 
 vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *props, const vag_dirichlet *bc,
                         int mem, vag_system **out) {
+  NvtxRange nvtx_range("vag_assemble");
   if (!ctx) return VAG_EINVAL;
   if (out) *out = nullptr;
   std::unique_ptr<vag_system> sys;
@@ -240,6 +251,7 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
 
 vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshes, const vag_props *props,
                               const vag_dirichlet *bcs, int mem, vag_system **out) {
+  NvtxRange nvtx_range("vag_assemble_batch");
   if (!ctx) return VAG_EINVAL;
   if (out) *out = nullptr;
   std::unique_ptr<vag_system> sys;
@@ -364,6 +376,7 @@ vag_status vag_transport_get_dts(const vag_system *sys, double *dt_max, double *
 }
 
 vag_status vag_update_props(vag_system *sys, const vag_props *props, int mem) {
+  NvtxRange nvtx_range("vag_update_props");
   if (!sys) return VAG_EINVAL;
   System *s = &sys->s;
   return guarded(s->ctx, [&] {
@@ -400,6 +413,7 @@ vag_status vag_system_get_info(const vag_system *sys, vag_system_info *info) {
 }
 
 vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out, vag_solve_info *info) {
+  NvtxRange nvtx_range("vag_solve");
   if (!sys) return VAG_EINVAL;
   System *s = &sys->s;
   vag_solve_info local{};
@@ -456,6 +470,7 @@ vag_status vag_kernel_time(vag_system *sys, int kernel, int32_t reps, double *ms
 }
 
 vag_status vag_spmv(vag_system *sys, const double *x, double *y, int mem) {
+  NvtxRange nvtx_range("vag_spmv");
   if (!sys) return VAG_EINVAL;
   System *s = &sys->s;
   return guarded(s->ctx, [&] {
@@ -482,6 +497,7 @@ vag_status vag_spmv(vag_system *sys, const double *x, double *y, int mem) {
 }
 
 vag_status vag_transport(vag_system *sys, const vag_transport_opts *o, double *c_inout, vag_transport_info *info) {
+  NvtxRange nvtx_range("vag_transport");
   if (!sys) return VAG_EINVAL;
   System *s = &sys->s;
   vag_transport_info local{};

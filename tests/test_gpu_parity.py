@@ -248,6 +248,55 @@ def test_error_paths(ctx):
     small.close()
 
 
+def test_invalid_inputs_are_reported(ctx):
+    """Bad physical inputs end in a status code, never a crash or a silent
+    result: negative or NaN permeabilities and NaN coordinates at assembly, a
+    non-positive porosity at transport, an indefinite permeability tensor at
+    the solve."""
+    import paper_1602_03641_gb300 as pkg
+    neg = vi.config_plain16(4)
+    neg.lambda_m = -np.asarray(neg.lambda_m)
+    with pytest.raises(pkg.VagError) as e:
+        pkg.assemble_problem(ctx, neg)
+    assert e.value.code == pkg.VAG_EINVAL
+    nanf = vi.config_plain16(4)
+    nanf.lambda_f = np.asarray(nanf.lambda_f, float).copy()
+    nanf.lambda_f[3] = np.nan
+    with pytest.raises(pkg.VagError) as e:
+        pkg.assemble_problem(ctx, nanf)
+    assert e.value.code == pkg.VAG_EINVAL
+    nanx = vi.config_plain16(4)
+    nanx.xyz = np.asarray(nanx.xyz, float).copy()
+    nanx.xyz[30, 1] = np.nan
+    with pytest.raises(pkg.VagError) as e:
+        pkg.assemble_problem(ctx, nanx)
+    assert e.value.code in (pkg.VAG_EMESH, pkg.VAG_EINVAL)
+    pb = vi.config_plain16(4)
+    s = pkg.assemble_problem(ctx, pb)
+    s.solve(rtol=1e-10, maxit=1000)
+    phi = np.asarray(pb.phi_m, float).copy()
+    phi[5] = -0.1
+    with pytest.raises(pkg.VagError) as e:
+        s.transport(pb.c0(), phi, pb.phi_f, pb.cbar, 1)
+    assert e.value.code == pkg.VAG_EINVAL
+    s.close()
+    # an indefinite tensor with a positive diagonal: Lambda = [[1, 3, 0], [3, 1, 0], [0, 0, 1]]
+    ind = vi.build_problem((4, 4, 4), [], jitter=0.0, seed=1)
+    lam = np.zeros((ind.n_cells, 6))
+    lam[:, 0] = lam[:, 1] = lam[:, 2] = 1.0
+    lam[:, 3] = 3.0
+    ind.lambda_m = lam
+    try:
+        s = pkg.assemble_problem(ctx, ind)
+    except pkg.VagError as err:        # caught at assembly: a non-positive diagonal
+        assert err.code == pkg.VAG_EINVAL
+    else:
+        for pc in (pkg.VAG_PC_JACOBI, pkg.VAG_PC_AMG):
+            _, info = s.solve(precond=pc, rtol=1e-10, maxit=500, raise_on_error=False)
+            assert info.ret != pkg.VAG_OK, (pc, info.ret, info.rel_residual)
+        s.close()
+
+
 def test_deterministic_bitwise(ctx):
     import paper_1602_03641_gb300 as pkg
     pb = vi.random_dfn_problem(14, 10, 1e4, seed=3)
