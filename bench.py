@@ -512,6 +512,7 @@ def solvers_arm(args):
         u = torch.empty(s.info().n_cv, dtype=torch.float64, device="cuda")
         row = {}
         for name, kr, pc in (("CG + Jacobi", pkg.VAG_KRYLOV_CG, pkg.VAG_PC_JACOBI),
+                             ("CG + Chebyshev-Jacobi", pkg.VAG_KRYLOV_CG, pkg.VAG_PC_CHEBYSHEV),
                              ("CG + aggregation AMG", pkg.VAG_KRYLOV_CG, pkg.VAG_PC_AMG),
                              ("BiCGStab + Jacobi", pkg.VAG_KRYLOV_BICGSTAB, pkg.VAG_PC_JACOBI),
                              ("BiCGStab + aggregation AMG", pkg.VAG_KRYLOV_BICGSTAB, pkg.VAG_PC_AMG)):
@@ -685,6 +686,7 @@ def main():
     # preconditioned by the FP32 copy of the AMG hierarchy.
     cmp = {}
     for name, prec, pc in (("fp64_jacobi", pkg.VAG_FP64, pkg.VAG_PC_JACOBI), ("mixed_jacobi", pkg.VAG_MIXED, pkg.VAG_PC_JACOBI),
+                           ("fp64_chebyshev", pkg.VAG_FP64, pkg.VAG_PC_CHEBYSHEV),
                            ("fp64_amg", pkg.VAG_FP64, pkg.VAG_PC_AMG), ("mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG),
                            ("mixed16_amg", pkg.VAG_MIXED_F16, pkg.VAG_PC_AMG)):
         step_device_prec(prec, pc, 1e-8)

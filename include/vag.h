@@ -52,6 +52,11 @@ enum { VAG_MEM_HOST = 0, VAG_MEM_DEVICE = 1 };
  * in FP16 after symmetric diagonal scaling (D^-1/2 A D^-1/2, entries in
  * [-1, 1]); VAG_PC_AMG only. */
 enum { VAG_FP64 = 0, VAG_MIXED = 1, VAG_MIXED_F16 = 2 };
+/* Preconditioners: Jacobi D^-1; VAG_PC_CHEBYSHEV, four steps of Chebyshev
+ * acceleration of Jacobi (a degree-3 polynomial in D^-1 A times D^-1) on
+ * [b/100, b], b = 1.2 x the largest Ritz value of D^-1 A after ten Lanczos
+ * (Jacobi-CG) steps from a pseudo-random vector, FP64 only; VAG_PC_AMG, the
+ * library's aggregation AMG V-cycle (FP64, or FP32 under VAG_MIXED). */
 enum { VAG_PC_JACOBI = 0, VAG_PC_CHEBYSHEV = 1, VAG_PC_AMG = 2 };
 /* Krylov method: CG (the system is SPD) or BiCGStab, the method of the
  * paper's solver experiments (§5.3), right-preconditioned. */
@@ -189,7 +194,8 @@ vag_status vag_system_get_info(const vag_system *sys, vag_system_info *info);
 typedef struct {
   int precision;     /* VAG_FP64, or VAG_MIXED: FP32 inner Krylov inside FP64
                         iterative refinement (residual and update in FP64)   */
-  int precond;       /* VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG          */
+  int precond;       /* VAG_PC_JACOBI, VAG_PC_CHEBYSHEV (VAG_FP64 only;
+                        VAG_EINVAL otherwise), VAG_PC_AMG                     */
   double rtol;       /* stop at ||b - A x||_2 <= rtol ||b||_2 (> 0)           */
   int32_t maxit;     /* Krylov iteration cap (total over refinements)          */
   int mem;           /* location of u_out                                     */

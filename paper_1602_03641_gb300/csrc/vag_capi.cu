@@ -104,6 +104,7 @@ void destroy_system(vag_system *sys) {
   if (s->pcg_graph_amg) cudaGraphExecDestroy(s->pcg_graph_amg);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   if (s->bicg_graph) cudaGraphExecDestroy(s->bicg_graph);
+  if (s->pcg_graph_cheb) cudaGraphExecDestroy(s->pcg_graph_cheb);
   amg_free(s);
   if (s->ks_host) cudaFreeHost(s->ks_host);
   if (s->n_done_host) cudaFreeHost(s->n_done_host);
@@ -426,8 +427,10 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
       fail(VAG_EINVAL, "unknown precision");
     if (opts->precision == VAG_MIXED_F16 && opts->precond != VAG_PC_AMG)
       fail(VAG_EINVAL, "VAG_MIXED_F16 stores the AMG finest level in FP16: it needs VAG_PC_AMG");
-    if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_AMG)
-      fail(VAG_EINVAL, "preconditioner not available in this build");
+    if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_CHEBYSHEV && opts->precond != VAG_PC_AMG)
+      fail(VAG_EINVAL, "unknown preconditioner");
+    if (opts->precond == VAG_PC_CHEBYSHEV && opts->precision != VAG_FP64)
+      fail(VAG_EINVAL, "VAG_PC_CHEBYSHEV runs in FP64 only");
     use_device(s->ctx);
     trace_mark(s->ctx->stream, "start");
     // VAG_MIXED: Jacobi -> FP64 refinement around FP32 CG; AMG -> FP64 CG

@@ -244,6 +244,13 @@ struct System {
   cudaGraphExec_t bicg_graph = nullptr;
   cudaGraphExec_t pcg_graph_amg = nullptr;
   size_t amg_graph_nodes = 0;
+  // Chebyshev preconditioner: coefficient table [2 kChebDegree per system],
+  // work vectors, and the intervals [a, b] (host, per system)
+  double *cheb_coef = nullptr;
+  double *cw = nullptr, *cd = nullptr, *cy = nullptr;
+  std::vector<double> cheb_bounds;
+  cudaGraphExec_t pcg_graph_cheb = nullptr;
+  size_t cheb_graph_nodes = 0;
 
   // transport (device)
   double *Fcn = nullptr;       // [8 nc]
@@ -364,6 +371,18 @@ void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
 const double *amg_first_sweep_scale(System *s, double *&t0, double &omega);
 bool amg_apply_cg(System *s, const double *r, double *z, cudaStream_t st);
 void amg_free(System *s);
+// Chebyshev preconditioner (FP64): cheb_setup estimates each system's interval
+// from Jacobi-CG Lanczos coefficients and fills the coefficient table;
+// cheb_apply forms z = M r (in_iter: systems already done are skipped;
+// w_ready: s->cw already holds D^-1 r; rz: the last step also sets beta and
+// r.z in s->ks, as the r.z reduction of CG does).
+void cheb_setup(System *s);
+void cheb_apply(System *s, const double *r, double *z, cudaStream_t st, bool in_iter, bool w_ready, bool rz);
+// m Jacobi-CG iterations from x = 0 on A x = v (v on the device, per system
+// rows): alpha[sys*m + j], beta[sys*m + j] for j < steps[sys], the iterations
+// that ran without breakdown.  Overwrites the Krylov work vectors.
+void jacobi_cg_coefficients(System *s, const double *v, int m, std::vector<double> &alpha,
+                            std::vector<double> &beta, std::vector<int> &steps);
 // choose (once per context and matrix size class) the loads in flight of the
 // sliced-ELL row loop by timing the candidates on this system's matrix;
 // never call it while a stream capture is open

@@ -2,7 +2,8 @@
 //
 // The system is the Galerkin form restricted to the non-Dirichlet unknowns,
 // hence symmetric positive definite: conjugate gradients with a Jacobi
-// preconditioner.  A solve handles a batch of independent systems at once
+// preconditioner (or a general one, z = M r: Chebyshev-Jacobi or aggregation
+// AMG, further below).  A solve handles a batch of independent systems at once
 // (a single system is a batch of one): every kernel runs one thread block per
 // row tile of some system, and each system keeps its own CG scalars.  Per
 // iteration three kernels:
@@ -16,7 +17,9 @@
 // so a system gives bitwise the same iterates alone or in a batch.
 // Iterations are captured in a CUDA graph of `chunk` iterations; the host
 // polls one counter (systems done) between graph launches.
+#include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "vag_internal.cuh"
 #include "vag_reduce.cuh"
@@ -637,28 +640,78 @@ static void pcg_iteration(System *s, cudaStream_t st) {
   note_launches(1);
 }
 
+// Chebyshev: the CG update also forms w = D^-1 r (the polynomial's first
+// step), the remaining steps follow, the last one forming r.z and beta
+static void pcg_iteration_cheb(System *s, cudaStream_t st) {
+  const Tiles tl = tiles_of(s);
+  const int nt = s->seg.n_tiles;
+  launch_spmv(s, s->kp, s->kq, 1, st);
+  launch_pdl(k_update_m, nt, NT, 0, st, s->kx, s->kr, (const double *)s->kp, (const double *)s->kq, tl, s->partials,
+             s->counter, s->ks, s->n_done, (const double *)s->dinv, s->cw, 1.0);
+  cheb_apply(s, s->kr, s->kz, st, true, true, true);
+  launch_pdl(k_pdir_z, nt, NT, 0, st, s->kp, (const double *)s->kz, tl, (const KrylovScalars *)s->ks);
+  note_launches(2);
+}
+
+void jacobi_cg_coefficients(System *s, const double *v, int m, std::vector<double> &alpha,
+                            std::vector<double> &beta, std::vector<int> &steps) {
+  ensure_krylov_buffers(s);
+  tune_sell(s);
+  cudaStream_t st = s->ctx->stream;
+  const int ns = s->seg.n_sys;
+  VAG_CUDA(cudaMemsetAsync(s->n_done, 0, sizeof(int), st));
+  // rtol 0: a system stops only on an exact zero residual, a breakdown or m
+  k_init<<<s->seg.n_tiles, NT, 0, st>>>(v, s->dinv, s->kx, s->kr, s->kp, tiles_of(s), s->partials, s->counter, s->ks,
+                                        s->n_done, 0.0, m);
+  note_launches(1);
+  alpha.assign((size_t)ns * m, 0.0);
+  beta.assign((size_t)ns * m, 0.0);
+  steps.assign(ns, 0);
+  for (int j = 0; j < m; ++j) {
+    pcg_iteration(s, st);
+    VAG_CHECK_LAUNCH();
+    VAG_CUDA(cudaMemcpyAsync(s->ks_host, s->ks, sizeof(KrylovScalars) * ns, cudaMemcpyDeviceToHost, st));
+    VAG_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < ns; ++i) {
+      const KrylovScalars &k = s->ks_host[i];
+      if (steps[i] != j || k.iter != j + 1 || k.breakdown) continue;
+      if (!(k.alpha > 0.0) || !std::isfinite(k.alpha) || !(k.beta >= 0.0) || !std::isfinite(k.beta)) continue;
+      alpha[(size_t)i * m + j] = k.alpha;
+      beta[(size_t)i * m + j] = k.beta;
+      steps[i] = j + 1;
+    }
+  }
+}
+
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   cudaStream_t st = s->ctx->stream;
   ensure_krylov_buffers(s);
   tune_sell(s);
   const bool amg = o->precond == VAG_PC_AMG;
+  const bool cheb = o->precond == VAG_PC_CHEBYSHEV;
+  const bool general = amg || cheb;   // z = M r by a general operator
   const int ns = s->seg.n_sys;
   const int nt = s->seg.n_tiles;
   const Tiles tl = tiles_of(s);
   float setup_ms = 0.f;
   VAG_CUDA(cudaEventRecord(s->ev0, st));
-  if (amg) {
+  if (general) {
     if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
-    amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16);
-    trace_mark(st, "AMG setup");
+    if (amg) amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16);
+    else cheb_setup(s);
+    trace_mark(st, amg ? "AMG setup" : "Chebyshev setup (Lanczos bounds)");
     VAG_CUDA(cudaEventRecord(s->ev1, st));
     VAG_CUDA(cudaEventSynchronize(s->ev1));
     cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);
   }
+  auto apply_m = [&](const double *r, double *z) {
+    if (amg) amg_apply(s, r, z, st);
+    else cheb_apply(s, r, z, st, false, false, false);
+  };
   VAG_CUDA(cudaMemsetAsync(s->n_done, 0, sizeof(int), st));
-  if (amg) {
+  if (general) {
     k_init_m<<<nt, NT, 0, st>>>(s->rhs, s->kx, s->kr, tl, s->partials, s->counter, s->ks, o->rtol, o->maxit);
-    amg_apply(s, s->kr, s->kz, st);
+    apply_m(s->kr, s->kz);
     k_rz_start<<<nt, NT, 0, st>>>(s->kr, s->kz, s->kp, tl, s->partials, s->counter, s->ks, s->n_done);
     note_launches(2);
   } else {
@@ -669,7 +722,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   VAG_CHECK_LAUNCH();
   trace_mark(st, "CG start (r0, z0)");
   const int chunk = 16;
-  cudaGraphExec_t &gexec = amg ? s->pcg_graph_amg : s->pcg_graph;
+  cudaGraphExec_t &gexec = amg ? s->pcg_graph_amg : cheb ? s->pcg_graph_cheb : s->pcg_graph;
   if (amg && gexec) {   // the hierarchy (and its pointers) is rebuilt every solve
     cudaGraphExecDestroy(gexec);
     gexec = nullptr;
@@ -680,6 +733,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
     set_capturing(true);
     for (int i = 0; i < chunk; ++i) {
       if (amg) pcg_iteration_amg(s, st);
+      else if (cheb) pcg_iteration_cheb(s, st);
       else pcg_iteration(s, st);
     }
     set_capturing(false);
@@ -689,9 +743,10 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
     VAG_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
     cudaGraphDestroy(graph);
     if (amg) s->amg_graph_nodes = nodes;
+    if (cheb) s->cheb_graph_nodes = nodes;
     trace_mark(st, "graph capture + instantiate");
   }
-  const unsigned long long per_launch = amg ? s->amg_graph_nodes : 3ull * chunk;
+  const unsigned long long per_launch = amg ? s->amg_graph_nodes : cheb ? s->cheb_graph_nodes : 3ull * chunk;
   const int max_chunks = (o->maxit + chunk - 1) / chunk;
   // The recursive residual can drift below the true one; after convergence
   // the true residual is recomputed and CG restarts from the current iterate
@@ -728,9 +783,9 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
     // push the stall flags back before the restart kernels read them
     VAG_CUDA(cudaMemcpyAsync(s->ks, s->ks_host, sizeof(KrylovScalars) * ns, cudaMemcpyHostToDevice, st));
     VAG_CUDA(cudaMemsetAsync(s->n_done, 0, sizeof(int), st));
-    if (amg) {
+    if (general) {
       k_restart_m<<<nt, NT, 0, st>>>(s->rhs, s->kq, s->kr, tl, s->partials, s->counter, s->ks);
-      amg_apply(s, s->kr, s->kz, st);
+      apply_m(s->kr, s->kz);
       k_rz_start<<<nt, NT, 0, st>>>(s->kr, s->kz, s->kp, tl, s->partials, s->counter, s->ks, s->n_done);
       note_launches(2);
     } else {
@@ -749,6 +804,7 @@ void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   ensure_krylov_buffers(s);
   tune_sell(s);
   const bool amg = o->precond == VAG_PC_AMG;
+  const bool cheb = o->precond == VAG_PC_CHEBYSHEV;
   const int nt = s->seg.n_tiles;
   const Tiles tl = tiles_of(s);
   if (!s->b_r0) {
@@ -766,10 +822,17 @@ void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
     VAG_CUDA(cudaEventRecord(s->ev1, st));
     VAG_CUDA(cudaEventSynchronize(s->ev1));
     cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);
+  } else if (cheb) {
+    cheb_setup(s);
+    VAG_CUDA(cudaEventRecord(s->ev1, st));
+    VAG_CUDA(cudaEventSynchronize(s->ev1));
+    cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);
   }
   auto precond = [&](const double *in, double *out) {
     if (amg) {
       amg_apply(s, in, out, st);
+    } else if (cheb) {
+      cheb_apply(s, in, out, st, true, false, false);
     } else {
       k_bi_jacobi<<<nt, NT, 0, st>>>(in, s->dinv, out, tl, s->ks);
       note_launches(1);
