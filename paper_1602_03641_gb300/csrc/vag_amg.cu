@@ -20,8 +20,10 @@
 //             hierarchy there: its block is inverted densely (Gauss-Jordan,
 //             SPD) and applied exactly in the cycle.  The depth of a system's
 //             hierarchy therefore depends on that system alone.
-// Apply: a V(2,2) cycle with l1-Jacobi sweeps before and after the coarse
-// correction; it is a fixed symmetric linear operator, as CG needs.  FP64, or
+// Apply: a V-cycle with l1-Jacobi sweeps before and after the coarse
+// correction, one each on the finest level and two each on the coarse levels
+// (V(1,1) / V(2,2)); as many sweeps after as before on every level, so it is
+// a fixed symmetric linear operator, as CG needs.  FP64, or
 // on an FP32 copy of the hierarchy (VAG_MIXED; VAG_MIXED_F16 also keeps the
 // finest level in FP16 after symmetric diagonal scaling).
 #include <climits>
@@ -1299,6 +1301,7 @@ void amg_setup(System *s, bool f32, bool f16) {
     L.b = static_cast<double *>(alloc(8 * (size_t)std::max(L.n, 1)));
     L.t = static_cast<double *>(alloc(8 * (size_t)std::max(L.n, 1)));
   }
+  if (!A.levels.empty()) A.levels[0].r = static_cast<double *>(alloc(8 * (size_t)std::max(A.levels[0].n, 1)));
   // FP32 copy of the hierarchy (the mixed-precision path)
   A.f32 = f32;
   A.f16 = false;
@@ -1340,6 +1343,7 @@ void amg_setup(System *s, bool f32, bool f16) {
       L.b32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
       L.t32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
     }
+    if (!A.levels.empty()) A.levels[0].r32 = static_cast<float *>(alloc(4 * (size_t)std::max(A.levels[0].n, 1)));
   }
   // first nonzero of each system on every coarse level (the tail's layout)
   for (size_t l = 1; l < A.levels.size(); ++l) {
@@ -1409,22 +1413,22 @@ void amg_setup(System *s, bool f32, bool f16) {
 template <class T>
 struct LV {
   const T *val, *sinv, *inv, *sval;
-  T *x, *b, *t;
+  T *x, *b, *t, *r;
 };
 template <class T>
 static LV<T> lv(System *s, AmgLevel &L);
 template <>
 LV<double> lv<double>(System *, AmgLevel &L) {
-  return {L.val, L.sinv, L.inv, L.sval, L.x, L.b, L.t};
+  return {L.val, L.sinv, L.inv, L.sval, L.x, L.b, L.t, L.r};
 }
 template <>
 LV<float> lv<float>(System *, AmgLevel &L) {
-  return {L.val32, L.sinv32, L.inv32, L.sval32, L.x32, L.b32, L.t32};
+  return {L.val32, L.sinv32, L.inv32, L.sval32, L.x32, L.b32, L.t32, L.r32};
 }   // val32 on coarse levels, sval32 on level 0
 
-// x = V(b): one V(2,2) cycle from a zero initial guess.  Systems that end at
-// this level are solved exactly; the others are smoothed, restricted,
-// corrected from the next level and smoothed again.
+// The levels from lvl down, V(2,2) from a zero initial guess, in one kernel.
+// Systems that end at a level are solved exactly there; the others are
+// smoothed, restricted, corrected from the next level and smoothed again.
 template <class T>
 static void tail(System *s, int lvl, cudaStream_t st) {
   Amg &A = s->amg;
@@ -1443,8 +1447,9 @@ static void tail(System *s, int lvl, cudaStream_t st) {
   note_launches(1);
 }
 
-// x = V(b): one V(2,2) cycle from a zero initial guess.  Systems that end at
-// this level are solved exactly; the others are smoothed, restricted,
+// x = V(b): one V-cycle from a zero initial guess, one sweep before and after
+// the coarse correction on level 0 and two on coarse levels.  Systems that
+// end at this level are solved exactly; the others are smoothed, restricted,
 // corrected from the next level and smoothed again.  On coarse levels the
 // first sweep t = omega D_l1^-1 b has already been made by the restriction
 // that produced b.
@@ -1488,23 +1493,20 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
     const LV<float> c32 = lv<float>(s, C);
     auto resid_h = s->sell_u == 2 ? k_resid_sell_h<2> : s->sell_u == 8 ? k_resid_sell_h<8> : k_resid_sell_h<4>;
     launch_pdl(k_jac_first<float>, g, TB, 0, st, n, bb, (const float *)A.sinv16, tt);
-    launch_pdl(jac_h, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
-               (const __half *)A.sval16, (const float *)A.sinv16, bb, (const float *)tt, xx, (const uint8_t *)L.skip);
     launch_pdl(resid_h, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
-               (const __half *)A.sval16, (const float *)A.s0f, bb, (const float *)xx, tt);
+               (const __half *)A.sval16, (const float *)A.s0f, bb, (const float *)tt, L.r32);
     launch_pdl(k_restrict_first<float>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
-               (const float *)tt, c32.sinv, c32.b, c32.t);
-    note_launches(4);
+               (const float *)L.r32, c32.sinv, c32.b, c32.t);
+    note_launches(3);
   } else if (lvl == 0) {
-    // level 0: sliced ELL, one thread per row
+    // level 0: sliced ELL, one thread per row; one sweep from zero, t =
+    // omega D_l1^-1 b, then the residual b - A t for the restriction
     if (!cg) launch_pdl(k_jac_first<T>, g, TB, 0, st, n, b, v.sinv, v.t);
-    launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
-               v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
     launch_pdl(resid_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
-               (const int *)L.scol, v.sval, b, (const T *)x, v.t);
+               (const int *)L.scol, v.sval, b, (const T *)v.t, v.r);
     launch_pdl(k_restrict_first<T>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
-               (const T *)v.t, c.sinv, c.b, c.t);
-    note_launches(cg ? 3 : 4);
+               (const T *)v.r, c.sinv, c.b, c.t);
+    note_launches(cg ? 2 : 3);
   } else {
     // coarse levels: CSR, 8 lanes per row; residual and restriction fused
     launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
@@ -1522,22 +1524,19 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
     }
   }
   vcycle<T>(s, lvl + 1, c.b, c.x, st);
-  // post-smoothing: two sweeps (on coarse levels the first one applies the
-  // coarse correction as it reads x)
+  // post-smoothing: level 0 adds the coarse correction to t and makes one
+  // sweep from it into x; coarse levels make two sweeps, the first applying
+  // the coarse correction as it reads x
   if (h16) {
     const float *bb = (const float *)b;
     float *xx = (float *)x, *tt = A.levels[0].t32;
     launch_pdl(k_prolong_scaled, g, TB, 0, st, n, (const int *)L.agg, (const float *)A.s0f,
-               (const float *)A.levels[1].x32, xx);
-    launch_pdl(jac_h, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
-               (const __half *)A.sval16, (const float *)A.sinv16, bb, (const float *)xx, tt, (const uint8_t *)L.skip);
+               (const float *)A.levels[1].x32, tt);
     launch_pdl(jac_h, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                (const __half *)A.sval16, (const float *)A.sinv16, bb, (const float *)tt, xx, (const uint8_t *)L.skip);
-    note_launches(3);
+    note_launches(2);
   } else if (lvl == 0) {
-    launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, x);
-    launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
-               v.sval, v.sinv, b, (const T *)x, v.t, (const uint8_t *)L.skip);
+    launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, v.t);
     if constexpr (sizeof(T) == 8) {
       if (cg) {
       auto jr = s->sell_u == 2 ? k_jac_sell_rz<2> : s->sell_u == 8 ? k_jac_sell_rz<8> : k_jac_sell_rz<4>;
@@ -1546,13 +1545,13 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
                  (const int *)L.scol, (const double *)v.sval, (const double *)v.sinv, (const double *)b,
                  (const double *)v.t, (double *)x, (const uint8_t *)L.skip, tl, s->partials, s->counter, s->ks,
                  s->n_done);
-      note_launches(3);
+      note_launches(2);
       return true;
       }
     }
     launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
-    note_launches(3);
+    note_launches(2);
   } else {
     launch_pdl(k_prolong_jac8<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
                (const T *)x, (const int *)L.agg, (const T *)c.x, v.t, (const uint8_t *)L.skip);

@@ -109,6 +109,10 @@ struct AmgLevel {
   int nc = 0;
   int *mptr = nullptr, *mem = nullptr;   // members of each aggregate, sorted
   double *x = nullptr, *b = nullptr, *t = nullptr;   // V-cycle work vectors
+  // level 0 only: the residual after its single pre-sweep (the V-cycle's b
+  // and x there are the caller's vectors)
+  double *r = nullptr;
+  float *r32 = nullptr;
   // sliced-ELL copy of level 0 (the system's own); coarse levels use CSR
   int *slice_ptr = nullptr, *scol = nullptr;
   double *sval = nullptr;
