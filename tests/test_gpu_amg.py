@@ -192,3 +192,30 @@ def test_fp16_needs_amg(ctx):
     _, info = s.solve(precision=pkg.VAG_MIXED_F16, precond=pkg.VAG_PC_JACOBI, raise_on_error=False)
     assert info.ret == pkg.VAG_EINVAL
     s.close()
+
+
+def test_fp64_amg_batch24_equals_alone_bitwise(ctx):
+    """A batch of 24 realisations with 3 to 7 fractures and ratios 1e2 to 1e6
+    under the FP64 AMG V-cycle: each sampled system bitwise the same alone and
+    in the batch (its hierarchy, smoother and reductions depend on the system
+    alone), and within the oracle's tolerance."""
+    import paper_1602_03641_gb300 as pkg
+    pbs = [vi.random_dfn_problem(10 + (i % 6) * 2, 3 + i % 5, 10.0 ** (2 + i % 5), seed=40 + i) for i in range(24)]
+    bs = ctx.assemble_batch([pkg.problem_arrays(p) for p in pbs])
+    lay = bs.batch_layout()
+    nv, nf = lay["node_start"][-1], lay["ff_start"][-1]
+    ub, _ = bs.solve(precond=pkg.VAG_PC_AMG, rtol=1e-10, maxit=2000, raise_on_error=False)
+    infos = bs.solve_infos()
+    ns, fs, cs = lay["node_start"], lay["ff_start"], lay["cell_start"]
+    for i in (5, 11, 17, 23):
+        pb = pbs[i]
+        s1 = pkg.assemble_problem(ctx, pb)
+        u1, inf1 = s1.solve(precond=pkg.VAG_PC_AMG, rtol=1e-10, maxit=2000, raise_on_error=False)
+        ui = np.concatenate([ub[ns[i]:ns[i + 1]], ub[nv + fs[i]:nv + fs[i + 1]], ub[nv + nf + cs[i]:nv + nf + cs[i + 1]]])
+        np.testing.assert_array_equal(ui, u1)
+        assert infos[i].iterations == inf1.iterations
+        assert inf1.rel_residual <= 1e-10
+        ref = vo.DarcyTransport(pb)
+        assert np.linalg.norm(u1 - ref.u) <= 1e-8 * np.linalg.norm(ref.u)
+        s1.close()
+    bs.close()
