@@ -176,6 +176,39 @@ def test_global_matrix_symmetric_zero_rowsum():
     assert np.abs(np.asarray(A.sum(axis=1))).max() <= 1e-13 * scale
 
 
+def test_global_matrix_invariant_under_renumbering():
+    """Relabelling the nodes and reordering the cells permutes the assembled
+    system and nothing else: the scheme depends on the mesh, not on its
+    numbering (V_K is kept sorted by node id, so the local slots move)."""
+    import dataclasses
+    pb = _scale_small(n=4, seed=5)
+    A = vo.assemble_full(pb).tocsr()
+    rng = np.random.default_rng(11)
+    pn = rng.permutation(pb.n_nodes)          # new id of node i
+    pc = rng.permutation(pb.n_cells)          # old cell at new position k
+    q = dataclasses.replace(pb)
+    xyz = np.empty_like(pb.xyz)
+    xyz[pn] = pb.xyz
+    q.xyz = xyz
+    q.faces = pn[pb.faces]
+    q.cell_nodes = pn[pb.cell_nodes][pc]
+    q.cell_faces = pb.cell_faces[pc]
+    q.lambda_m = pb.lambda_m[pc]
+    q.phi_m = pb.phi_m[pc]
+    q.ff_nodes = pn[pb.ff_nodes]
+    q.dir_nodes = pn[pb.dir_nodes]
+    B = vo.assemble_full(q).tocsr()
+    nv, nf, nc = pb.n_nodes, pb.n_ff, pb.n_cells
+    inv_pc = np.empty(nc, np.int64)
+    inv_pc[pc] = np.arange(nc)
+    new_of_old = np.concatenate([pn, nv + np.arange(nf), nv + nf + inv_pc])
+    Bp = B[new_of_old][:, new_of_old]
+    assert abs(Bp - A).max() <= 1e-13 * abs(A).max()
+    u = vo.solve_full(pb, A)
+    v = vo.solve_full(q, B)
+    assert np.abs(v[new_of_old] - u).max() <= 1e-11 * np.abs(u).max()
+
+
 def test_zero_flux_at_constant_pressure():
     pb = _scale_small()
     m = vo.Mesh(pb)
