@@ -515,7 +515,8 @@ def solvers_arm(args):
                              ("CG + Chebyshev-Jacobi", pkg.VAG_KRYLOV_CG, pkg.VAG_PC_CHEBYSHEV),
                              ("CG + aggregation AMG", pkg.VAG_KRYLOV_CG, pkg.VAG_PC_AMG),
                              ("BiCGStab + Jacobi", pkg.VAG_KRYLOV_BICGSTAB, pkg.VAG_PC_JACOBI),
-                             ("BiCGStab + aggregation AMG", pkg.VAG_KRYLOV_BICGSTAB, pkg.VAG_PC_AMG)):
+                             ("BiCGStab + aggregation AMG", pkg.VAG_KRYLOV_BICGSTAB, pkg.VAG_PC_AMG),
+                             ("GMRES(30) + aggregation AMG", pkg.VAG_KRYLOV_GMRES, pkg.VAG_PC_AMG)):
             s.solve(out=u, precond=pc, rtol=1e-8, maxit=50000, raise_on_error=False, krylov=kr)   # warm-up
             e0, e1 = ev(), ev()
             e0.record(stream)

@@ -58,9 +58,12 @@ enum { VAG_FP64 = 0, VAG_MIXED = 1, VAG_MIXED_F16 = 2 };
  * (Jacobi-CG) steps from a pseudo-random vector, FP64 only; VAG_PC_AMG, the
  * library's aggregation AMG V-cycle (FP64, or FP32 under VAG_MIXED). */
 enum { VAG_PC_JACOBI = 0, VAG_PC_CHEBYSHEV = 1, VAG_PC_AMG = 2 };
-/* Krylov method: CG (the system is SPD) or BiCGStab, the method of the
- * paper's solver experiments (§5.3), right-preconditioned. */
-enum { VAG_KRYLOV_CG = 0, VAG_KRYLOV_BICGSTAB = 1 };
+/* Krylov method: CG (the system is SPD), or one of the methods of the
+ * paper's solver experiments (§5.3), both right-preconditioned: BiCGStab, or
+ * restarted GMRES(30) (classical Gram-Schmidt applied twice, Givens
+ * rotations; a system stops when its true residual meets rtol, at maxit
+ * Arnoldi steps, or when a whole restart cycle no longer lowers it). */
+enum { VAG_KRYLOV_CG = 0, VAG_KRYLOV_BICGSTAB = 1, VAG_KRYLOV_GMRES = 2 };
 
 typedef struct vag_ctx vag_ctx;
 typedef struct vag_system vag_system;
@@ -199,9 +202,11 @@ typedef struct {
   double rtol;       /* stop at ||b - A x||_2 <= rtol ||b||_2 (> 0)           */
   int32_t maxit;     /* Krylov iteration cap (total over refinements)          */
   int mem;           /* location of u_out                                     */
-  int32_t krylov;    /* VAG_KRYLOV_CG (0, the default) or VAG_KRYLOV_BICGSTAB
-                        (FP64 iterations; with VAG_MIXED only for VAG_PC_AMG,
-                        whose V-cycle then runs on the FP32 hierarchy)     */
+  int32_t krylov;    /* VAG_KRYLOV_CG (0, the default), VAG_KRYLOV_BICGSTAB
+                        or VAG_KRYLOV_GMRES (FP64 iterations; with VAG_MIXED
+                        only for VAG_PC_AMG, whose V-cycle then runs on the
+                        FP32 hierarchy); iterations counts Arnoldi steps for
+                        GMRES                                              */
 } vag_solve_opts;
 
 typedef struct {

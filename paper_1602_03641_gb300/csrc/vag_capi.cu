@@ -435,11 +435,16 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     trace_mark(s->ctx->stream, "start");
     // VAG_MIXED: Jacobi -> FP64 refinement around FP32 CG; AMG -> FP64 CG
     // preconditioned by an FP32 copy of the AMG hierarchy
-    if (opts->krylov != VAG_KRYLOV_CG && opts->krylov != VAG_KRYLOV_BICGSTAB) fail(VAG_EINVAL, "unknown Krylov method");
+    if (opts->krylov != VAG_KRYLOV_CG && opts->krylov != VAG_KRYLOV_BICGSTAB && opts->krylov != VAG_KRYLOV_GMRES)
+      fail(VAG_EINVAL, "unknown Krylov method");
     if (opts->krylov == VAG_KRYLOV_BICGSTAB) {
       if (opts->precision == VAG_MIXED && opts->precond != VAG_PC_AMG)
         fail(VAG_EINVAL, "BiCGStab with VAG_MIXED needs VAG_PC_AMG");
       bicgstab_solve(s, opts, inf);
+    } else if (opts->krylov == VAG_KRYLOV_GMRES) {
+      if (opts->precision == VAG_MIXED && opts->precond != VAG_PC_AMG)
+        fail(VAG_EINVAL, "GMRES with VAG_MIXED needs VAG_PC_AMG");
+      gmres_solve(s, opts, inf);
     } else if (opts->precision == VAG_MIXED && opts->precond == VAG_PC_JACOBI) {
       mixed_solve(s, opts, inf);
     } else {

@@ -255,6 +255,10 @@ struct System {
   std::vector<double> cheb_bounds;
   cudaGraphExec_t pcg_graph_cheb = nullptr;
   size_t cheb_graph_nodes = 0;
+  // GMRES: Arnoldi basis [m+1][n_rows], work vector, dot-product partials,
+  // per-system state
+  double *gm_V = nullptr, *gm_w = nullptr, *gm_part = nullptr;
+  unsigned char *gm_state = nullptr;
 
   // transport (device)
   double *Fcn = nullptr;       // [8 nc]
@@ -365,6 +369,11 @@ void symbolic_phase(System *s);
 void numeric_phase(System *s);
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
+void gmres_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
+// y = A x (FP64 sliced ELL, tuned loads in flight), stream-ordered, capture-safe
+void launch_spmv_plain(System *s, const double *x, double *y, cudaStream_t st);
+// ks[sys].res2 = ||b - A x||^2 per system (x = s->kx)
+void true_residual2(System *s, cudaStream_t st);
 void amg_setup(System *s, bool f32, bool f16 = false);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
 // The FP64 V-cycle inside CG: amg_first_sweep_scale gives the finest level's

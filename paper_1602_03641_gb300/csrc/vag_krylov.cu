@@ -589,6 +589,15 @@ void ensure_krylov_buffers(System *s) {
   if (!s->n_done_host) VAG_CUDA(cudaMallocHost(&s->n_done_host, sizeof(int)));
 }
 
+void launch_spmv_plain(System *s, const double *x, double *y, cudaStream_t st) { launch_spmv(s, x, y, 0, st); }
+
+void true_residual2(System *s, cudaStream_t st) {
+  launch_spmv(s, s->kx, s->kq, 0, st);
+  k_resid2<<<s->seg.n_tiles, NT, 0, st>>>(s->rhs, s->kq, tiles_of(s), s->partials, s->counter, s->ks);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
+}
+
 void spmv_f64(System *s, const double *x, double *y) {
   ensure_krylov_buffers(s);
   tune_sell(s);

@@ -23,7 +23,7 @@ VAG_EBREAKDOWN, VAG_ETIMEOUT, VAG_ECUDA, VAG_EMESH = 5, 6, 7, 8
 VAG_MEM_HOST, VAG_MEM_DEVICE = 0, 1
 VAG_FP64, VAG_MIXED, VAG_MIXED_F16 = 0, 1, 2
 VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG = 0, 1, 2
-VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB = 0, 1
+VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB, VAG_KRYLOV_GMRES = 0, 1, 2
 VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP = 0, 1, 2
 
 STATUS_NAMES = {0: "VAG_OK", 1: "VAG_EINVAL", 2: "VAG_ENOMEM", 3: "VAG_EBUDGET", 4: "VAG_ENOTCONVERGED",
