@@ -221,8 +221,9 @@ typedef struct {
 /*
  * Solve the eliminated system by preconditioned conjugate gradients (the
  * matrix is symmetric positive definite: Galerkin form, Dirichlet rows
- * removed), then recover the cell unknowns by Eq. (eqschurcell) and keep the
- * full solution on the device for vag_transport.  u_out (optional, may be
+ * removed; opts->krylov selects BiCGStab or GMRES(30) instead), then recover
+ * the cell unknowns by Eq. (eqschurcell) and keep the full solution on the
+ * device for vag_transport.  u_out (optional, may be
  * NULL): [n_nodes + n_ff + n_cells] in the [nodes | ffaces | cells] order, the
  * Dirichlet values echoed at Dirichlet nodes.
  */
