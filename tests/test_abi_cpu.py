@@ -89,3 +89,29 @@ def test_without_gpu_context_creation_reports_an_error(vag):
     st = vag.lib().vag_ctx_create(0, 0, C.byref(h))
     assert st in (vag.VAG_ECUDA, vag.VAG_EINVAL)
     assert not h.value
+
+
+def test_binding_constants_match_the_header(vag):
+    """Every VAG_* enumerator of include/vag.h has the same value in the
+    binding (status codes, precisions, preconditioners, Krylov methods,
+    memory spaces, kernels)."""
+    src = ['#include <stdio.h>', '#include "vag.h"', "int main(void){"]
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    names = sorted(set(n for body in re.findall(r"enum\s*\{([^}]*)\}", txt)
+                       for n in re.findall(r"\b(VAG_[A-Z0-9_]+)\b", body)))
+    assert "VAG_KRYLOV_GMRES" in names and "VAG_PC_CHEBYSHEV" in names
+    for n in names:
+        src.append(f'printf("{n} %lld\\n", (long long){n});')
+    src.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "e.c")
+        exe = os.path.join(d, "e")
+        open(c, "w").write("\n".join(src))
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    import paper_1602_03641_gb300 as pkg
+    for line in out.splitlines():
+        n, v = line.split()
+        assert hasattr(vag, n) or hasattr(pkg, n), n
+        got = getattr(vag, n, getattr(pkg, n, None))
+        assert got == int(v), (n, got, v)
