@@ -3,7 +3,10 @@
 affine solution u = 1 - x, and the transported concentration at t_f = 1/2
 (time step of Sec. 4.3: the CFL maximum, the last step shortened) converges
 in L1 to the closed form, faster in the fracture than in the matrix.  At
-64 x 64 the GPU concentrations equal the oracle's."""
+64 x 64 the GPU concentrations equal the oracle's; at 64, 128 and 256 the
+L1 errors equal the oracle's stored ones."""
+import os
+
 import numpy as np
 import pytest
 
@@ -16,6 +19,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 T_F = 0.5
+# the oracle's errors at 64, 128, 256 (tests/golden/make_one_fracture_errors.py)
+GOLD = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "one_fracture_l1_errors.txt"), comments="#")
 
 
 @pytest.fixture(scope="module")
@@ -94,6 +99,11 @@ def test_one_fracture_converges_on_gpu(ctx):
         e = _errors(pb, c, vol, m)
         em.append(e[0])
         ef.append(e[1])
+        ref = GOLD[GOLD[:, 0] == n]
+        if len(ref):   # the oracle's run of the same mesh: same steps, same errors
+            _, steps_or, dt_or, em_or, ef_or = ref[0]
+            assert steps == int(steps_or) and dt == pytest.approx(dt_or, rel=1e-7)
+            assert e[0] == pytest.approx(em_or, rel=1e-4) and e[1] == pytest.approx(ef_or, rel=1e-4)
     em, ef = np.array(em), np.array(ef)
     assert np.all(np.diff(em) < 0) and np.all(np.diff(ef) < 0), (em, ef)
     assert np.all(ef < em), (em, ef)
