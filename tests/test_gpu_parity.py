@@ -1,6 +1,6 @@
 """CUDA path (through the C ABI) against the CPU oracle, element by element.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (each follows from the arithmetic noted beside it):
 * eliminated-system entries and right-hand side: 1e-12 of the largest entry
   (same FP64 formulas, different summation order);
 * pressures: relative L2 error <= 1e-10 with both sides converged far below it;
