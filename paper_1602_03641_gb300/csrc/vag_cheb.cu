@@ -30,6 +30,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "vag_cheb_host.h"
 #include "vag_internal.cuh"
 #include "vag_reduce.cuh"
 
@@ -116,35 +117,6 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const int *__restrict__ rowptr
   }
 }
 
-// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal a and
-// off-diagonal e, by bisection on the Sturm count (the number of negative
-// pivots of T - x I, which is the number of eigenvalues below x).
-double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &e) {
-  const int m = (int)a.size();
-  double lo = INFINITY, hi = -INFINITY;
-  for (int i = 0; i < m; ++i) {   // Gershgorin discs
-    const double rad = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
-    lo = std::fmin(lo, a[i] - rad);
-    hi = std::fmax(hi, a[i] + rad);
-  }
-  auto below = [&](double x) {
-    int cnt = 0;
-    double q = 1.0;
-    for (int i = 0; i < m; ++i) {
-      q = (a[i] - x) - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
-      if (q == 0.0) q = -1e-300;
-      if (q < 0.0) ++cnt;
-    }
-    return cnt;
-  };
-  for (int it = 0; it < 200 && hi - lo > 1e-13 * std::fmax(std::fabs(lo), std::fabs(hi)); ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (below(mid) >= m) hi = mid;
-    else lo = mid;
-  }
-  return hi;
-}
-
 }  // namespace
 
 void cheb_setup(System *s) {
@@ -169,30 +141,11 @@ void cheb_setup(System *s) {
   std::vector<double> coef((size_t)kCoefStride * ns, 0.0);
   s->cheb_bounds.assign(2 * (size_t)ns, 0.0);
   for (int sy = 0; sy < ns; ++sy) {
-    const int m = steps[sy];
-    double b = 2.0;   // no Lanczos step (empty system or immediate breakdown)
-    if (m > 0) {
-      std::vector<double> d(m), e(m > 1 ? m - 1 : 0);
-      const double *al = &alpha[(size_t)sy * kLanczosSteps];
-      const double *be = &beta[(size_t)sy * kLanczosSteps];
-      for (int j = 0; j < m; ++j) {
-        d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
-        if (j + 1 < m) e[j] = std::sqrt(be[j]) / al[j];
-      }
-      b = kChebSafety * tridiag_max_eig(d, e);
-      if (!(b > 0.0) || !std::isfinite(b)) b = 2.0;
-    }
+    // no Lanczos step (empty system or immediate breakdown): b = 2
+    const double b = cheb_upper_bound(&alpha[(size_t)sy * kLanczosSteps], &beta[(size_t)sy * kLanczosSteps],
+                                      steps[sy], kChebSafety);
     const double a = b / kChebRatio;
-    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
-    double *c = &coef[(size_t)kCoefStride * sy];
-    c[0] = 1.0 / theta;
-    double rho_prev = 1.0 / sigma;
-    for (int j = 1; j < kChebDegree; ++j) {
-      const double rho = 1.0 / (2.0 * sigma - rho_prev);
-      c[2 * j] = rho * rho_prev;
-      c[2 * j + 1] = 2.0 * rho / delta;
-      rho_prev = rho;
-    }
+    cheb_table(a, b, kChebDegree, &coef[(size_t)kCoefStride * sy]);
     s->cheb_bounds[2 * sy] = a;
     s->cheb_bounds[2 * sy + 1] = b;
   }
