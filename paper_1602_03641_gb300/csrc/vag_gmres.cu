@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <vector>
 
+#include "vag_gmres_ls.h"
 #include "vag_internal.cuh"
 #include "vag_reduce.cuh"
 
@@ -134,24 +135,13 @@ __global__ void __launch_bounds__(NT) k_gm_update(const double *__restrict__ V, 
     double c[kRestart + 1];
     for (int q = 0; q <= j; ++q) c[q] = G.h1[q] + G.h2[q];
     c[j + 1] = hn;
-    for (int q = 0; q < j; ++q) {
-      const double a0 = c[q], a1 = c[q + 1];
-      c[q] = G.cs[q] * a0 + G.sn[q] * a1;
-      c[q + 1] = -G.sn[q] * a0 + G.cs[q] * a1;
-    }
-    const double rho = hypot(c[j], c[j + 1]);
     bool fin = false;
-    if (!(rho > 0.0) || !isfinite(rho)) {
+    if (!gm_rotate_column(j, c, G.cs, G.sn, G.g)) {
       k.breakdown = 1;
       G.k = j;
       fin = true;
     } else {
-      G.cs[j] = c[j] / rho;
-      G.sn[j] = c[j + 1] / rho;
-      c[j] = rho;
       for (int q = 0; q <= j; ++q) G.R[j][q] = c[q];
-      G.g[j + 1] = -G.sn[j] * G.g[j];
-      G.g[j] = G.cs[j] * G.g[j];
       G.hn = hn;
       G.k = j + 1;
       k.iter += 1;
@@ -190,11 +180,7 @@ __global__ void k_gm_solve(int ns, GmState *gs) {
   const int sys = blockIdx.x * blockDim.x + threadIdx.x;
   if (sys >= ns) return;
   GmState &G = gs[sys];
-  for (int i = G.k - 1; i >= 0; --i) {
-    double a = G.g[i];
-    for (int l = i + 1; l < G.k; ++l) a = fma(-G.R[l][i], G.y[l], a);
-    G.y[i] = a / G.R[i][i];
-  }
+  gm_back_substitute(G.k, &G.R[0][0], kRestart, G.g, G.y);
 }
 
 // u = sum_{q < k} y_q V_q (zero for systems that made no step)
