@@ -41,7 +41,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "vag.h")]
+    headers = (sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(CSRC, "*.h")))
+               + [os.path.join(ROOT, "include", "vag.h")])
     objs = []
     cmds = []
     for src in sources:
