@@ -411,13 +411,16 @@ void vag_server_destroy(vag_server *srv);
  *   n_rows  rows and columns, 0 <= n_rows <= VAG_NOALLOC_MAX_ROWS (else
  *           VAG_EINVAL, nothing launched);
  *   rowptr [n_rows+1], col [nnz] (int32), val [nnz], x [n_rows], y [n_rows],
- *           xdoty [1]: device pointers owned by the caller;
+ *           xdoty [1]: device pointers owned by the caller; y must not
+ *           overlap x (VAG_EINVAL), rowptr, col or val;
  *   stream  cudaStream_t (void*), NULL = the legacy default stream.
  * Stream-ordered: returns without waiting.  VAG_ECUDA if a CUDA call fails.
  * The first call on a device looks up the scratch address (no allocation);
- * make it before any stream capture that includes a call.  All calls on a
- * device share the scratch: calls whose kernels overlap on the GPU race and
- * must be ordered (same stream, or events).
+ * make it before any stream capture that includes a call.  The address is
+ * kept for the life of the process: after cudaDeviceReset on a device, do not
+ * call this entry point on that device again in the same process.  All calls
+ * on a device share the scratch: calls whose kernels overlap on the GPU race
+ * and must be ordered (same stream, or events).
  */
 vag_status vag_spmv_dot_noalloc(int32_t n_rows, const int32_t *rowptr, const int32_t *col, const double *val,
                                 const double *x, double *y, double *xdoty, void *stream);

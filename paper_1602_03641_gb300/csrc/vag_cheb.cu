@@ -95,14 +95,12 @@ __global__ void __launch_bounds__(NT) k_cheb_step(const int *__restrict__ rowptr
   pdl_wait();
   pdl_trigger();
   if (in_iter && ks[sys].done) return;   // uniform in the block: one system per tile
-  const double s_in = j == 1 ? c[0] : 1.0;
-  const double c1 = c[2 * j], c2 = c[2 * j + 1];
   double rz = 0.0;
   if (valid) {
     const double ri = r[i];
-    const double res = fma(-s_in, sell_row<double, U>(i, rowptr, slice_ptr, scol, sval, z_in), ri);
-    const double di = fma(c1 * s_in, d_in[i], c2 * (dinv[i] * res));
-    const double zi = fma(s_in, z_in[i], di);
+    double di, zi;
+    cheb_row_step(c, j, ri, sell_row<double, U>(i, rowptr, slice_ptr, scol, sval, z_in), dinv[i], d_in[i], z_in[i],
+                  &di, &zi);
     if (d_out) d_out[i] = di;
     z_out[i] = zi;
     rz = ri * zi;

@@ -1,12 +1,19 @@
-// Host arithmetic of the Chebyshev-Jacobi preconditioner: the interval from
-// the Lanczos tridiagonal of a few Jacobi-CG steps and the coefficient table
-// of the Chebyshev recurrence (Saad, Iterative Methods for Sparse Linear
-// Systems, 2nd ed., Sec. 6.7.3 and Alg. 12.1).  Plain C++ without CUDA, so
-// that it can be compiled and checked on its own.
+// Arithmetic of the Chebyshev-Jacobi preconditioner: the interval from the
+// Lanczos tridiagonal of a few Jacobi-CG steps, the coefficient table of the
+// Chebyshev recurrence (Saad, Iterative Methods for Sparse Linear Systems,
+// 2nd ed., Sec. 6.7.3 and Alg. 12.1), and the per-row update of one step,
+// which the device kernel calls.  Compiles without CUDA, so that it can be
+// checked on its own.
 #pragma once
 
 #include <cmath>
 #include <vector>
+
+#ifdef __CUDACC__
+#define VAG_CHEB_HD __host__ __device__
+#else
+#define VAG_CHEB_HD
+#endif
 
 namespace vag {
 
@@ -69,6 +76,21 @@ inline void cheb_table(double a, double b, int degree, double *c) {
     c[2 * j + 1] = 2.0 * rho / delta;
     rho_prev = rho;
   }
+}
+
+// Step j >= 1 of the recurrence for one row, given the row's residual entry
+// r_i, the product (A z_in)_i, D^-1_ii and the previous direction and iterate
+// (d_in_i, z_in_i): with s = c[0] on the first step (its inputs are the
+// unscaled w = D^-1 r) and 1 after it,
+//   res = r_i - s (A z_in)_i,  d_out = c[2j] s d_in + c[2j+1] D^-1_ii res,
+//   z_out = s z_in + d_out.
+VAG_CHEB_HD inline void cheb_row_step(const double *c, int j, double ri, double Az, double dinv_i, double d_in,
+                                      double z_in, double *d_out, double *z_out) {
+  const double s_in = j == 1 ? c[0] : 1.0;
+  const double res = fma(-s_in, Az, ri);
+  const double di = fma(c[2 * j] * s_in, d_in, c[2 * j + 1] * (dinv_i * res));
+  *d_out = di;
+  *z_out = fma(s_in, z_in, di);
 }
 
 }  // namespace vag

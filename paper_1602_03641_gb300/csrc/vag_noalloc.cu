@@ -15,7 +15,10 @@
 // the device symbols, not device addresses: their device addresses are looked
 // up once per device with cudaGetSymbolAddress (with that device current) and
 // cached.  That lookup happens on the first call on each device, so make the
-// first call on a device before any stream capture that includes it.
+// first call on a device before any stream capture that includes it.  The
+// cache lives as long as the process: after cudaDeviceReset the module is
+// loaded again and the cached addresses may be stale, so a process that resets
+// a device must not call this entry point again on it.
 //
 // The scratch is shared by every call on a device and keeps the contents of
 // the last call.  The arrival counter must start at zero: each call clears it
@@ -95,6 +98,12 @@ extern "C" vag_status vag_spmv_dot_noalloc(int32_t n_rows, const int32_t *rowptr
                                            void *stream) {
   if (n_rows < 0 || n_rows > VAG_NOALLOC_MAX_ROWS) return VAG_EINVAL;
   if (!rowptr || !xdoty || (n_rows > 0 && (!col || !val || !x || !y))) return VAG_EINVAL;
+  // rows read x[col[k]] while other rows write y: the two must not overlap
+  if (n_rows > 0) {
+    const uintptr_t xb = reinterpret_cast<uintptr_t>(x), yb = reinterpret_cast<uintptr_t>(y);
+    const uintptr_t len = sizeof(double) * (uintptr_t)n_rows;
+    if (xb < yb + len && yb < xb + len) return VAG_EINVAL;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VAG_ECUDA;
   DeviceScratch sc;

@@ -1,8 +1,9 @@
-"""Host arithmetic of the Chebyshev-Jacobi preconditioner (the plain C++ of
-csrc/vag_cheb_host.h, compiled here with g++): the Sturm-bisection top
-eigenvalue of a tridiagonal matrix, the interval from CG's Lanczos
-coefficients, and the recurrence table, whose scalar application must give
-the residual polynomial T_k((theta - l)/delta) / T_k(theta/delta).  CPU only."""
+"""Arithmetic of the Chebyshev-Jacobi preconditioner (csrc/vag_cheb_host.h,
+compiled here with g++): the Sturm-bisection top eigenvalue of a tridiagonal
+matrix, the interval from CG's Lanczos coefficients, and the recurrence table
+applied by the kernel's own per-row step (cheb_row_step) to a scalar, which
+must give the residual polynomial T_k((theta - l)/delta) / T_k(theta/delta).
+CPU only."""
 import os
 import subprocess
 import tempfile
@@ -43,12 +44,9 @@ int main() {
       vag::cheb_table(a, b, k, c.data());
       const double r = 1.0, w = r;      // D = 1: w = D^-1 r
       double d = 0.0, z = 0.0;
-      for (int j = 1; j < k; ++j) {
-        const double s_in = j == 1 ? c[0] : 1.0;
+      for (int j = 1; j < k; ++j) {      // the kernel's per-row step, A = lambda
         const double din = j == 1 ? w : d, zin = j == 1 ? w : z;
-        const double res = r - s_in * (lam * zin);
-        d = c[2 * j] * s_in * din + c[2 * j + 1] * res;
-        z = s_in * zin + d;
+        vag::cheb_row_step(c.data(), j, r, lam * zin, 1.0, din, zin, &d, &z);
       }
       if (k == 1) z = c[0] * w;
       std::printf("%.17g\n", z);

@@ -5,13 +5,15 @@ product (inside their own stream capture, allocation-free serving threads,
 memory reserved by another runtime): its scratch is a fixed file-scope device
 array instead of an allocation.  This test calls it through the C ABI on an
 eliminated VAG system and compares its output with the existing vag_spmv
-entry point, on two calls in a row (the shared scratch must not leak state
-from one call into the next).  This file is collected last on purpose.
+entry point and with scipy's product on the exported CSR, on two calls in a
+row (the shared scratch must not leak state from one call into the next).
+This file is collected last on purpose.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
+import scipy.sparse as sps
 
 import vag_inputs as vi
 
@@ -63,6 +65,9 @@ def test_matches_vag_spmv_on_two_calls_in_a_row(setup):
         yg = y.cpu().numpy()
         tol = 1e-12 * scale * np.abs(xh).max() * 30
         assert np.abs(yg - yref).max() <= tol, call
+        # and, independently of the library, scipy's product on the exported CSR
+        ysp = sps.csr_matrix((e["val"], e["col"], e["rowptr"]), shape=(n, n)) @ xh
+        assert np.abs(yg - ysp).max() <= tol, call
         dref = float(np.dot(xh, yref))
         assert abs(dot.item() - dref) <= 1e-12 * np.abs(xh).dot(np.abs(yref)) + tol, call
 
@@ -73,3 +78,5 @@ def test_rejects_sizes_beyond_the_static_limit(setup):
     p = dummy.data_ptr()
     assert L.vag_spmv_dot_noalloc((1 << 22) + 1, p, p, p, p, p, p, None) == pkg.VAG_EINVAL
     assert L.vag_spmv_dot_noalloc(-1, p, p, p, p, p, p, None) == pkg.VAG_EINVAL
+    # the output may not overlap the input vector
+    assert L.vag_spmv_dot_noalloc(2, p, p, p, p, p + 8, p, None) == pkg.VAG_EINVAL
