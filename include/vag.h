@@ -48,10 +48,19 @@ enum {
 };
 
 enum { VAG_MEM_HOST = 0, VAG_MEM_DEVICE = 1 };
-/* VAG_MIXED_F16: VAG_MIXED with the AMG V-cycle's finest-level matrix stored
- * in FP16 after symmetric diagonal scaling (D^-1/2 A D^-1/2, entries in
- * [-1, 1]); VAG_PC_AMG only. */
-enum { VAG_FP64 = 0, VAG_MIXED = 1, VAG_MIXED_F16 = 2 };
+/* Precision of vag_solve.
+ * VAG_FP64: every operation in FP64.
+ * VAG_MIXED: FP64 iterative refinement (residual b - A x, update and
+ *   convergence test in FP64) around an FP32 inner Krylov solve: with
+ *   VAG_PC_JACOBI, FP32 CG on D^-1/2 A D^-1/2; with VAG_PC_AMG, FP32 CG on A
+ *   preconditioned by the FP32 copy of the AMG hierarchy (BiCGStab and GMRES
+ *   with VAG_PC_AMG instead run FP64 iterations with the FP32 V-cycle).
+ * VAG_MIXED_F16: VAG_MIXED with the AMG V-cycle's finest-level matrix stored
+ *   in FP16 after symmetric diagonal scaling (D^-1/2 A D^-1/2, entries in
+ *   [-1, 1]); VAG_PC_AMG only.
+ * VAG_FP64_PC32: FP64 Krylov iterations preconditioned by the FP32 AMG
+ *   V-cycle, no refinement; VAG_PC_AMG only. */
+enum { VAG_FP64 = 0, VAG_MIXED = 1, VAG_MIXED_F16 = 2, VAG_FP64_PC32 = 3 };
 /* Preconditioners: Jacobi D^-1; VAG_PC_CHEBYSHEV, four steps of Chebyshev
  * acceleration of Jacobi (a degree-3 polynomial in D^-1 A times D^-1) on
  * [b/100, b], b = 1.2 x the largest Ritz value of D^-1 A after ten Lanczos
@@ -69,8 +78,10 @@ typedef struct vag_ctx vag_ctx;
 typedef struct vag_system vag_system;
 
 /*
- * Mesh (Sec. 3.1, generalized polyhedral mesh conforming to the fracture
- * network; this library takes its hexahedral case).
+ * Mesh (Sec. 3.1: a generalized polyhedral mesh conforming to the fracture
+ * network), in one of two forms.
+ *
+ * Hexahedral fast path (cell_nodes != NULL):
  *   xyz        [3*n_nodes]  node coordinates, x y z interleaved.
  *   cell_nodes [8*n_cells]  node l of a cell sits at lattice offset
  *              (l&1, (l>>1)&1, (l>>2)&1): faces are {0,2,6,4} (-x),
@@ -79,8 +90,26 @@ typedef struct vag_system vag_system;
  *   ff_nodes   [4*n_ff]     the fracture faces F_Gamma, each a face of the
  *              mesh given by its four nodes in cyclic order.  A fracture face
  *              that is not a face of some cell is a VAG_EMESH error.
+ *
+ * General polyhedral descriptor (cell_nodes == NULL; ff_nodes ignored):
+ *   n_faces, face_node_ptr [n_faces+1], face_node_idx: the nodes of face f,
+ *              face_node_idx[face_node_ptr[f] .. face_node_ptr[f+1]), in
+ *              cyclic order (consecutive nodes share an edge);
+ *   cell_face_ptr [n_cells+1], cell_face_idx: the faces of cell K,
+ *              cell_face_idx[cell_face_ptr[K] .. cell_face_ptr[K+1]);
+ *   ff_face_ids [n_ff]: the fracture faces F_Gamma as face ids.
+ *   The library recognises hexahedral cells (six faces of four nodes forming
+ *   a cube graph) whatever the order of their faces and face nodes, numbers
+ *   them canonically (node 0 = the smallest node id, 1, 2, 4 = its edge
+ *   neighbours in increasing id) and assembles them on the fast path; on a
+ *   lattice whose node ids grow with x, then y, then z this is the lattice
+ *   numbering, so both forms give bitwise the same system.  A cell that is
+ *   not a hexahedron, or a fracture face that is not a quadrilateral, is a
+ *   VAG_EMESH error (this build's kernels take hexahedra); an offset or id
+ *   out of range is VAG_EINVAL.
+ *
  * Cell centres x_K and face centres x_sigma are the isobarycentres of their
- * nodes (beta_{sigma,s} = 1/4).
+ * nodes (beta_{sigma,s} = 1/|V_sigma|).
  */
 typedef struct {
   int32_t n_nodes;
@@ -89,6 +118,12 @@ typedef struct {
   const int32_t *cell_nodes;
   int32_t n_ff;
   const int32_t *ff_nodes;
+  int32_t n_faces;
+  const int32_t *face_node_ptr;
+  const int32_t *face_node_idx;
+  const int32_t *cell_face_ptr;
+  const int32_t *cell_face_idx;
+  const int32_t *ff_face_ids;
 } vag_mesh;
 
 /*
@@ -195,8 +230,7 @@ vag_status vag_system_get_info(const vag_system *sys, vag_system_info *info);
 /* ------------------------------------------------------------------ solve */
 
 typedef struct {
-  int precision;     /* VAG_FP64, or VAG_MIXED: FP32 inner Krylov inside FP64
-                        iterative refinement (residual and update in FP64)   */
+  int precision;     /* VAG_FP64, VAG_MIXED, VAG_MIXED_F16, VAG_FP64_PC32   */
   int precond;       /* VAG_PC_JACOBI, VAG_PC_CHEBYSHEV (VAG_FP64 only;
                         VAG_EINVAL otherwise), VAG_PC_AMG                     */
   double rtol;       /* stop at ||b - A x||_2 <= rtol ||b||_2 (> 0)           */
@@ -207,6 +241,10 @@ typedef struct {
                         only for VAG_PC_AMG, whose V-cycle then runs on the
                         FP32 hierarchy); iterations counts Arnoldi steps for
                         GMRES                                              */
+  double inner_rtol; /* VAG_MIXED(_F16) with VAG_PC_AMG and CG: smallest
+                        relative tolerance of an inner FP32 solve (each
+                        refinement step solves to max(inner_rtol, 0.3 x the
+                        reduction still needed), at most 0.1); 0 = 1e-6    */
 } vag_solve_opts;
 
 typedef struct {
@@ -307,8 +345,12 @@ vag_status vag_export_porous_volumes(const vag_system *sys, double *phi, int mem
 /* Hot kernels that vag_kernel_time can time. */
 enum {
   VAG_KERNEL_SPMV = 0,            /* q = A p, FP64 sliced ELL (the CG product)      */
-  VAG_KERNEL_SMOOTH = 1,          /* one FP64 l1-Jacobi sweep on the finest level    */
-  VAG_KERNEL_TRANSPORT_STEP = 2   /* one explicit upwind step c' = d c + W c          */
+  VAG_KERNEL_SMOOTH = 1,          /* one l1-Jacobi sweep on the finest level of the
+                                     last AMG hierarchy (FP64, or FP32 after a
+                                     mixed-precision AMG solve)                    */
+  VAG_KERNEL_TRANSPORT_STEP = 2,  /* one explicit upwind step c' = d c + W c          */
+  VAG_KERNEL_SPMV32 = 3           /* q = A p and p.q in FP32, sliced ELL (the inner
+                                     CG product of a VAG_MIXED AMG solve)          */
 };
 
 /*
@@ -316,7 +358,9 @@ enum {
  * launches of one hot kernel on this system's own data with CUDA events on the
  * context's stream and return the mean duration of a launch in *ms_per_launch.
  * VAG_KERNEL_SMOOTH needs the AMG hierarchy of a previous vag_solve with
- * VAG_PC_AMG and VAG_FP64; VAG_KERNEL_TRANSPORT_STEP needs the upwind map of a
+ * VAG_PC_AMG (VAG_MIXED_F16's FP16 finest level excepted);
+ * VAG_KERNEL_SPMV32 needs a previous VAG_MIXED or VAG_MIXED_F16 solve with
+ * VAG_PC_AMG and CG; VAG_KERNEL_TRANSPORT_STEP needs the upwind map of a
  * previous vag_transport; VAG_EINVAL otherwise, or for reps < 1.  The kernels
  * run on the system's Krylov and transport work vectors, whose contents are
  * overwritten (the solution and the concentrations already returned are not

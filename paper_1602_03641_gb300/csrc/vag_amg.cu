@@ -1101,6 +1101,16 @@ __global__ void k_prolong_scaled(int n, const int *__restrict__ agg, const float
   if (J >= 0) x[i] += si * xc[J];
 }
 
+// b = a / s (FP32), the scaled-variable conversions of VAG_MIXED_F16 for a
+// V-cycle called on FP32 vectors
+__global__ void k_div32(int n, const float *__restrict__ a, const float *__restrict__ s, float *__restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const float si = i < n ? s[i] : 1.f;
+  pdl_wait();
+  pdl_trigger();
+  if (i < n) b[i] = a[i] / si;
+}
+
 __global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   pdl_wait();
@@ -1583,6 +1593,21 @@ void amg_apply(System *s, const double *r, double *z, cudaStream_t st) {
   note_launches(2);
 }
 
+void amg_apply_f32(System *s, const float *r, float *z, cudaStream_t st) {
+  Amg &A = s->amg;
+  if (!A.f32) fail(VAG_EINVAL, "amg_apply_f32 needs the FP32 hierarchy");
+  AmgLevel &L0 = A.levels[0];
+  const int n = L0.n;
+  if (A.f16) {   // scaled variables on the finest level: b~ = S r, z = S x~
+    launch_pdl(k_div32, grid_for(n, TB), TB, 0, st, n, r, (const float *)A.s0f, L0.b32);
+    vcycle<float>(s, 0, L0.b32, L0.x32, st);
+    launch_pdl(k_div32, grid_for(n, TB), TB, 0, st, n, (const float *)L0.x32, (const float *)A.s0f, z);
+    note_launches(2);
+    return;
+  }
+  vcycle<float>(s, 0, r, z, st);
+}
+
 bool amg_apply_cg(System *s, const double *r, double *z, cudaStream_t st) {
   if (s->amg.f32 || s->amg.levels.empty() || s->amg.levels[0].all_term) return false;
   return vcycle<double>(s, 0, r, z, st, true);
@@ -1595,14 +1620,38 @@ const double *amg_first_sweep_scale(System *s, double *&t0, double &omega) {
   return s->amg.levels[0].sinv;
 }
 
-// Mean duration of one FP64 finest-level sweep (x_out = x_in + omega
-// D_l1^-1 (b - A x_in)), launched as in the V-cycle.
+// Mean duration of one finest-level sweep (x_out = x_in + omega D_l1^-1
+// (b - A x_in)) of the last hierarchy, FP64 or FP32, launched as in the
+// V-cycle.
 double time_smoother(System *s, int reps) {
   Amg &A = s->amg;
-  if (!A.built || A.f32 || A.levels.empty() || !s->kz) fail(VAG_EINVAL, "no FP64 AMG hierarchy: solve with AMG first");
+  if (!A.built || A.levels.empty() || A.f16) fail(VAG_EINVAL, "no FP64 or FP32 AMG hierarchy: solve with AMG first");
   AmgLevel &L = A.levels[0];
   cudaStream_t st = s->ctx->stream;
   const int n = L.n, g = grid_for(n, TB);
+  if (A.f32) {
+    auto jac = s->sell_u == 2 ? k_jac_sell<float, 2> : s->sell_u == 8 ? k_jac_sell<float, 8> : k_jac_sell<float, 4>;
+    auto sweep32 = [&](const float *xin, float *xout) {
+      launch_pdl(jac, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
+                 (const float *)L.sval32, (const float *)L.sinv32, (const float *)L.b32, xin, xout,
+                 (const uint8_t *)L.skip);
+      note_launches(1);
+    };
+    VAG_CUDA(cudaMemsetAsync(L.x32, 0, sizeof(float) * n, st));
+    VAG_CUDA(cudaMemsetAsync(L.b32, 0, sizeof(float) * n, st));
+    sweep32(L.x32, L.t32);   // warm-up
+    VAG_CUDA(cudaEventRecord(s->ev0, st));
+    for (int r = 0; r < reps; ++r) {
+      if (r & 1) sweep32(L.t32, L.x32);
+      else sweep32(L.x32, L.t32);
+    }
+    VAG_CUDA(cudaEventRecord(s->ev1, st));
+    VAG_CUDA(cudaEventSynchronize(s->ev1));
+    float ms = 0.f;
+    VAG_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+    return (double)ms / reps;
+  }
+  if (!s->kz) fail(VAG_EINVAL, "no FP64 AMG hierarchy: solve with AMG first");
   auto sweep = [&](const double *xin, double *xout) {
     auto jac = s->sell_u == 2 ? k_jac_sell<double, 2> : s->sell_u == 8 ? k_jac_sell<double, 8> : k_jac_sell<double, 4>;
     launch_pdl(jac, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,

@@ -324,6 +324,7 @@ void numeric_phase(System *s) {
   VAG_CHECK_LAUNCH();
   if (s->sval) sell_values(s);
   s->mx.stale = true;
+  s->mx.dstale = true;
   const int stv = read_status(s);
   if (stv & ST_BAD_GEOMETRY) fail(VAG_EMESH, "degenerate sub-tetrahedron or fracture triangle");
   if (stv & ST_NONPOSITIVE) fail(VAG_EINVAL, "non-positive diagonal in the eliminated system");

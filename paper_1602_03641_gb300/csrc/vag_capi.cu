@@ -101,6 +101,7 @@ void destroy_system(vag_system *sys) {
   if (c && c->stream) cudaStreamSynchronize(c->stream);
   if (s->pcg_graph) cudaGraphExecDestroy(s->pcg_graph);
   if (s->mx.graph) cudaGraphExecDestroy(s->mx.graph);
+  if (s->mx.graph_amg) cudaGraphExecDestroy(s->mx.graph_amg);
   if (s->pcg_graph_amg) cudaGraphExecDestroy(s->pcg_graph_amg);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   if (s->bicg_graph) cudaGraphExecDestroy(s->bicg_graph);
@@ -218,8 +219,14 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
     trace_mark(s->ctx->stream, "start");
     s->status = sys_alloc<int>(s, 4);
     s->xyz = upload(s, mesh->xyz, 3 * (size_t)s->nv, mem, "xyz");
-    s->cell_nodes = upload(s, mesh->cell_nodes, 8 * (size_t)s->nc, mem, "cell_nodes");
-    s->ff_nodes = upload(s, mesh->ff_nodes, 4 * (size_t)s->nf, mem, "ff_nodes");
+    if (mesh->cell_nodes) {   // hexahedral fast path
+      s->cell_nodes = upload(s, mesh->cell_nodes, 8 * (size_t)s->nc, mem, "cell_nodes");
+      s->ff_nodes = upload(s, mesh->ff_nodes, 4 * (size_t)s->nf, mem, "ff_nodes");
+    } else {                  // general polyhedral descriptor
+      s->cell_nodes = sys_alloc<int>(s, 8 * (size_t)s->nc);
+      s->ff_nodes = sys_alloc<int>(s, 4 * (size_t)s->nf);
+      general_to_hex(s->ctx, *mesh, mem, s->cell_nodes, s->ff_nodes);
+    }
     s->dir_nodes = upload(s, bc->nodes, (size_t)s->nd, mem, "dirichlet nodes");
     s->dir_vals = upload(s, bc->values, (size_t)s->nd, mem, "dirichlet values");
     s->lam = upload(s, props->lambda_m, 6 * (size_t)s->nc, mem, "lambda_m");
@@ -305,8 +312,12 @@ vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshe
       const vag_mesh &m = meshes[i];
       const int v0 = g.node_start[i], c0 = g.cell_start[i], f0 = g.ff_start[i], d0 = g.dir_start[i];
       copy_in(s, s->xyz + 3 * (size_t)v0, m.xyz, 3 * (size_t)m.n_nodes, mem, "xyz");
-      copy_in(s, s->cell_nodes + 8 * (size_t)c0, m.cell_nodes, 8 * (size_t)m.n_cells, mem, "cell_nodes");
-      copy_in(s, s->ff_nodes + 4 * (size_t)f0, m.ff_nodes, 4 * (size_t)m.n_ff, mem, "ff_nodes");
+      if (m.cell_nodes) {
+        copy_in(s, s->cell_nodes + 8 * (size_t)c0, m.cell_nodes, 8 * (size_t)m.n_cells, mem, "cell_nodes");
+        copy_in(s, s->ff_nodes + 4 * (size_t)f0, m.ff_nodes, 4 * (size_t)m.n_ff, mem, "ff_nodes");
+      } else {
+        general_to_hex(s->ctx, m, mem, s->cell_nodes + 8 * (size_t)c0, s->ff_nodes + 4 * (size_t)f0);
+      }
       copy_in(s, s->dir_nodes + d0, bcs[i].nodes, (size_t)bcs[i].n_dir, mem, "dirichlet nodes");
       copy_in(s, s->dir_vals + d0, bcs[i].values, (size_t)bcs[i].n_dir, mem, "dirichlet values");
       copy_in(s, s->lam + 6 * (size_t)c0, props[i].lambda_m, 6 * (size_t)m.n_cells, mem, "lambda_m");
@@ -423,18 +434,23 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     if (!opts) fail(VAG_EINVAL, "null options");
     check_mem(opts->mem);
     if (!(opts->rtol > 0.0) || opts->maxit <= 0) fail(VAG_EINVAL, "rtol must be > 0 and maxit > 0");
-    if (opts->precision != VAG_FP64 && opts->precision != VAG_MIXED && opts->precision != VAG_MIXED_F16)
+    if (opts->precision != VAG_FP64 && opts->precision != VAG_MIXED && opts->precision != VAG_MIXED_F16 &&
+        opts->precision != VAG_FP64_PC32)
       fail(VAG_EINVAL, "unknown precision");
     if (opts->precision == VAG_MIXED_F16 && opts->precond != VAG_PC_AMG)
       fail(VAG_EINVAL, "VAG_MIXED_F16 stores the AMG finest level in FP16: it needs VAG_PC_AMG");
+    if (opts->precision == VAG_FP64_PC32 && opts->precond != VAG_PC_AMG)
+      fail(VAG_EINVAL, "VAG_FP64_PC32 preconditions by the FP32 AMG hierarchy: it needs VAG_PC_AMG");
+    if (!(opts->inner_rtol >= 0.0 && opts->inner_rtol < 1.0)) fail(VAG_EINVAL, "inner_rtol must be in [0, 1)");
     if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_CHEBYSHEV && opts->precond != VAG_PC_AMG)
       fail(VAG_EINVAL, "unknown preconditioner");
     if (opts->precond == VAG_PC_CHEBYSHEV && opts->precision != VAG_FP64)
       fail(VAG_EINVAL, "VAG_PC_CHEBYSHEV runs in FP64 only");
     use_device(s->ctx);
     trace_mark(s->ctx->stream, "start");
-    // VAG_MIXED: Jacobi -> FP64 refinement around FP32 CG; AMG -> FP64 CG
-    // preconditioned by an FP32 copy of the AMG hierarchy
+    // VAG_MIXED(_F16): FP64 refinement around FP32 CG (Jacobi: on the scaled
+    // system; AMG: preconditioned by the FP32 hierarchy); VAG_FP64_PC32: FP64
+    // CG preconditioned by the FP32 hierarchy
     if (opts->krylov != VAG_KRYLOV_CG && opts->krylov != VAG_KRYLOV_BICGSTAB && opts->krylov != VAG_KRYLOV_GMRES)
       fail(VAG_EINVAL, "unknown Krylov method");
     if (opts->krylov == VAG_KRYLOV_BICGSTAB) {
@@ -447,6 +463,8 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
       gmres_solve(s, opts, inf);
     } else if (opts->precision == VAG_MIXED && opts->precond == VAG_PC_JACOBI) {
       mixed_solve(s, opts, inf);
+    } else if ((opts->precision == VAG_MIXED || opts->precision == VAG_MIXED_F16) && opts->precond == VAG_PC_AMG) {
+      mixed_amg_solve(s, opts, inf);
     } else {
       pcg_solve(s, opts, inf);
     }
@@ -471,6 +489,7 @@ vag_status vag_kernel_time(vag_system *sys, int kernel, int32_t reps, double *ms
       case VAG_KERNEL_SPMV: *ms_per_launch = time_spmv(s, reps); break;
       case VAG_KERNEL_SMOOTH: *ms_per_launch = time_smoother(s, reps); break;
       case VAG_KERNEL_TRANSPORT_STEP: *ms_per_launch = time_transport_step(s, reps); break;
+      case VAG_KERNEL_SPMV32: *ms_per_launch = time_spmv32(s, reps); break;
       default: fail(VAG_EINVAL, "unknown kernel");
     }
     VAG_CHECK_LAUNCH();

@@ -141,8 +141,13 @@ struct Amg {
 
 // State of the mixed-precision solve (FP32 inner CG inside FP64 refinement).
 struct Mixed {
-  float *sval32 = nullptr;     // FP32 sliced-ELL values of S A S, S = D^{-1/2}
+  float *sval32 = nullptr;     // FP32 sliced-ELL values of S A S, S = D^{-1/2} (Jacobi)
   float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  float *z32 = nullptr;        // preconditioned inner residual (AMG)
+  float *dval32 = nullptr;     // FP32 difference-form values of A, sliced ELL (AMG)
+  bool dstale = true;
+  cudaGraphExec_t graph_amg = nullptr;   // inner iterations with the V-cycle, rebuilt per solve
+  size_t graph_amg_nodes = 0;
   double *sc = nullptr;        // S
   KrylovScalars *ks_in = nullptr;
   int *n_done_in = nullptr;
@@ -271,6 +276,16 @@ struct System {
   int *tcol = nullptr;         // [nnz_t]
   double *tval = nullptr;      // [nnz_t]
   int64_t t_cap = 0;
+  // the same map as the step kernel reads it: per 256-CV tile the rows sorted
+  // by inflow count (tperm: row offset inside the tile, tlen: its count,
+  // tdiag_s: its diagonal), entries column-major in 32-row slices
+  int n_tiles_t = 0;
+  uint8_t *tperm = nullptr, *tlen = nullptr;   // [256 n_tiles_t]
+  double *tdiag_s = nullptr;                   // [256 n_tiles_t]
+  int *tslice_ptr = nullptr;                   // [8 n_tiles_t + 1] element offsets
+  int *tscol = nullptr;                        // [ts_cap]
+  double *tsval = nullptr;                     // [ts_cap]
+  int64_t ts_cap = 0;
   double *cbuf = nullptr;      // [2 n_cv]
   double *dts = nullptr;       // [2 n_sys]: per system dt_max, dt
   cudaGraphExec_t step_graph = nullptr;   // kStepChunk transport steps
@@ -364,6 +379,12 @@ bool trace_enabled();
 void trace_mark(cudaStream_t st, const char *label);
 void trace_report(const char *call);
 
+// General polyhedral descriptor (vag_mesh with cell_nodes == NULL) -> the
+// hexahedral fast path: device outputs cell_nodes [8 n_cells] and ff_nodes
+// [4 n_ff] (ids local to the mesh).  VAG_EMESH for a cell that is not a
+// hexahedron, VAG_EINVAL for an offset or id out of range.
+void general_to_hex(Ctx *c, const vag_mesh &m, int mem, int32_t *cell_nodes, int32_t *ff_nodes);
+
 // ------------------------------------------------------------- phases -----
 void symbolic_phase(System *s);
 void numeric_phase(System *s);
@@ -376,6 +397,9 @@ void launch_spmv_plain(System *s, const double *x, double *y, cudaStream_t st);
 void true_residual2(System *s, cudaStream_t st);
 void amg_setup(System *s, bool f32, bool f16 = false);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
+// z = V(r) on FP32 vectors with the FP32 hierarchy (the inner solve of the
+// refinement loop); r and z must not be the hierarchy's own level-0 vectors
+void amg_apply_f32(System *s, const float *r, float *z, cudaStream_t st);
 // The FP64 V-cycle inside CG: amg_first_sweep_scale gives the finest level's
 // l1 scaling, its first-sweep buffer t0 and omega (null for the FP32
 // hierarchy or a hierarchy without coarse levels) so that the CG update can
@@ -404,7 +428,11 @@ void tune_sell(System *s);
 double time_spmv(System *s, int reps);
 double time_smoother(System *s, int reps);
 double time_transport_step(System *s, int reps);
+double time_spmv32(System *s, int reps);
 void mixed_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
+// FP64 iterative refinement around FP32 CG preconditioned by the FP32 AMG
+// V-cycle (VAG_MIXED / VAG_MIXED_F16 with VAG_PC_AMG and CG)
+void mixed_amg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void ensure_krylov_buffers(System *s);
 // Krylov result in s->kx and per-system scalars in s->ks: scatter into u,
 // recover the cells, compute the fluxes, fill the aggregate info.

@@ -19,6 +19,7 @@
 #include <thread>
 #include <vector>
 
+#include "vag_hexmap.h"
 #include "vag_internal.cuh"
 
 namespace {
@@ -104,7 +105,7 @@ void vag_server::run_batch(vag_ctx *ctx, std::vector<std::shared_ptr<Req>> &batc
     vag_system_get_info(sys, &si);
     vag_system_get_batch(sys, nullptr, ns.data(), fs.data(), cs.data(), nullptr);
     u.resize(si.n_cv);
-    vag_solve_opts so{r0.precision, r0.precond, r0.rtol, r0.maxit, VAG_MEM_HOST};
+    vag_solve_opts so{r0.precision, r0.precond, r0.rtol, r0.maxit, VAG_MEM_HOST, VAG_KRYLOV_CG, 0.0};
     st = vag_solve(sys, &so, u.data(), &agg);
     if (st == VAG_OK || st == VAG_ENOTCONVERGED) vag_solve_get_infos(sys, infos.data());
     if (st == VAG_OK && r0.n_steps > 0) {
@@ -236,16 +237,37 @@ vag_status vag_server_create(const vag_server_opts *opts, vag_server **out) {
 vag_status vag_server_submit(vag_server *s, const vag_request *q, uint64_t *ticket) {
   if (!s || !q || !ticket) return VAG_EINVAL;
   const vag_mesh &m = q->mesh;
+  const bool general = !m.cell_nodes;
   if (m.n_nodes <= 0 || m.n_cells <= 0 || m.n_ff < 0 || q->bc.n_dir <= 0 || !(q->props.mu > 0.0) ||
-      !m.xyz || !m.cell_nodes || (m.n_ff && !m.ff_nodes) || !q->props.lambda_m ||
+      !m.xyz || (!general && m.n_ff && !m.ff_nodes) ||
+      (general && (m.n_faces <= 0 || !m.face_node_ptr || !m.face_node_idx || !m.cell_face_ptr ||
+                   !m.cell_face_idx || (m.n_ff && !m.ff_face_ids))) ||
+      !q->props.lambda_m ||
       (m.n_ff && (!q->props.lambda_f || !q->props.d_f)) || !q->bc.nodes || !q->bc.values || q->n_steps < 0 ||
       (q->n_steps > 0 && (!q->phi_m || (m.n_ff && !q->phi_f) || !q->cbar)) || !(q->rtol > 0.0) || q->maxit <= 0)
     return VAG_EINVAL;
   auto r = std::make_shared<Req>();
   const size_t nv = m.n_nodes, nc = m.n_cells, nf = m.n_ff, nd = q->bc.n_dir;
   r->xyz.assign(m.xyz, m.xyz + 3 * nv);
-  r->cn.assign(m.cell_nodes, m.cell_nodes + 8 * nc);
-  if (nf) r->ffn.assign(m.ff_nodes, m.ff_nodes + 4 * nf);
+  if (!general) {
+    r->cn.assign(m.cell_nodes, m.cell_nodes + 8 * nc);
+    if (nf) r->ffn.assign(m.ff_nodes, m.ff_nodes + 4 * nf);
+  } else {   // the general descriptor, turned into the hexahedral fast path here
+    const int64_t flen = m.face_node_ptr[m.n_faces], clen = m.cell_face_ptr[m.n_cells];
+    if (flen < 0 || clen < 0) return VAG_EINVAL;
+    r->cn.resize(8 * nc);
+    r->ffn.resize(4 * nf);
+    for (size_t K = 0; K < nc; ++K) {
+      const int e = vag::hex_from_faces(m.face_node_ptr, m.face_node_idx, flen, m.cell_face_ptr, m.cell_face_idx,
+                                        clen, m.n_faces, m.n_nodes, (int32_t)K, r->cn.data() + 8 * K);
+      if (e != vag::HEXMAP_OK) return e == vag::HEXMAP_NOT_HEX ? VAG_EMESH : VAG_EINVAL;
+    }
+    for (size_t i = 0; i < nf; ++i) {
+      const int e = vag::quad_of_face(m.face_node_ptr, m.face_node_idx, flen, m.n_faces, m.n_nodes,
+                                      m.ff_face_ids[i], r->ffn.data() + 4 * i);
+      if (e != vag::HEXMAP_OK) return e == vag::HEXMAP_NOT_HEX ? VAG_EMESH : VAG_EINVAL;
+    }
+  }
   r->lam.assign(q->props.lambda_m, q->props.lambda_m + 6 * nc);
   if (nf) {
     r->lamf.assign(q->props.lambda_f, q->props.lambda_f + nf);

@@ -21,10 +21,10 @@ LIB_PATH = os.path.join(HERE, "libvag.so")
 VAG_OK, VAG_EINVAL, VAG_ENOMEM, VAG_EBUDGET, VAG_ENOTCONVERGED = 0, 1, 2, 3, 4
 VAG_EBREAKDOWN, VAG_ETIMEOUT, VAG_ECUDA, VAG_EMESH = 5, 6, 7, 8
 VAG_MEM_HOST, VAG_MEM_DEVICE = 0, 1
-VAG_FP64, VAG_MIXED, VAG_MIXED_F16 = 0, 1, 2
+VAG_FP64, VAG_MIXED, VAG_MIXED_F16, VAG_FP64_PC32 = 0, 1, 2, 3
 VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG = 0, 1, 2
 VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB, VAG_KRYLOV_GMRES = 0, 1, 2
-VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP = 0, 1, 2
+VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP, VAG_KERNEL_SPMV32 = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "VAG_OK", 1: "VAG_EINVAL", 2: "VAG_ENOMEM", 3: "VAG_EBUDGET", 4: "VAG_ENOTCONVERGED",
                 5: "VAG_EBREAKDOWN", 6: "VAG_ETIMEOUT", 7: "VAG_ECUDA", 8: "VAG_EMESH"}
@@ -32,7 +32,9 @@ STATUS_NAMES = {0: "VAG_OK", 1: "VAG_EINVAL", 2: "VAG_ENOMEM", 3: "VAG_EBUDGET",
 
 class vag_mesh(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("xyz", C.c_void_p), ("n_cells", C.c_int32),
-                ("cell_nodes", C.c_void_p), ("n_ff", C.c_int32), ("ff_nodes", C.c_void_p)]
+                ("cell_nodes", C.c_void_p), ("n_ff", C.c_int32), ("ff_nodes", C.c_void_p),
+                ("n_faces", C.c_int32), ("face_node_ptr", C.c_void_p), ("face_node_idx", C.c_void_p),
+                ("cell_face_ptr", C.c_void_p), ("cell_face_idx", C.c_void_p), ("ff_face_ids", C.c_void_p)]
 
 
 class vag_props(C.Structure):
@@ -51,7 +53,7 @@ class vag_system_info(C.Structure):
 
 class vag_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int32),
-                ("mem", C.c_int), ("krylov", C.c_int32)]
+                ("mem", C.c_int), ("krylov", C.c_int32), ("inner_rtol", C.c_double)]
 
 
 class vag_solve_info(C.Structure):
@@ -185,6 +187,17 @@ def _ptr(x, dtype=None):
     return a.ctypes.data
 
 
+def _size(a):
+    return int(a.numel() if _is_torch(a) else a.size)
+
+
+def _general_mesh(xyz, face_node_ptr, face_node_idx, cell_face_ptr, cell_face_idx, ff_face_ids):
+    """vag_mesh in the general polyhedral form (cell_nodes = NULL)."""
+    return vag_mesh(_size(xyz) // 3, _ptr(xyz, np.float64), _size(cell_face_ptr) - 1, None, _size(ff_face_ids), None,
+                    _size(face_node_ptr) - 1, _ptr(face_node_ptr, np.int32), _ptr(face_node_idx, np.int32),
+                    _ptr(cell_face_ptr, np.int32), _ptr(cell_face_idx, np.int32), _ptr(ff_face_ids, np.int32))
+
+
 def _mem_of(*xs):
     kinds = set()
     for x in xs:
@@ -243,6 +256,21 @@ class Context:
         self.check(self._L.vag_assemble(self.h, C.byref(m), C.byref(p), C.byref(b), mem, C.byref(h)))
         return System(self, h)
 
+    def assemble_general(self, xyz, face_node_ptr, face_node_idx, cell_face_ptr, cell_face_idx, ff_face_ids,
+                         lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values):
+        """The general polyhedral descriptor (faces as cyclic node lists,
+        cells as face lists, fracture faces as face ids); numpy (host) or CUDA
+        tensors (device), float64 / int32."""
+        mem = _mem_of(xyz, face_node_ptr, face_node_idx, cell_face_ptr, cell_face_idx, ff_face_ids, lambda_m,
+                      lambda_f, d_f, dir_nodes, dir_values)
+        m = _general_mesh(xyz, face_node_ptr, face_node_idx, cell_face_ptr, cell_face_idx, ff_face_ids)
+        p = vag_props(_ptr(lambda_m, np.float64), _ptr(lambda_f, np.float64), _ptr(d_f, np.float64), float(mu))
+        nd = _size(dir_nodes)
+        b = vag_dirichlet(nd, _ptr(dir_nodes, np.int32), _ptr(dir_values, np.float64))
+        h = P()
+        self.check(self._L.vag_assemble(self.h, C.byref(m), C.byref(p), C.byref(b), mem, C.byref(h)))
+        return System(self, h)
+
     def assemble_batch(self, problems):
         """problems: list of dicts with keys xyz, cell_nodes, ff_nodes,
         lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values (numpy host or
@@ -252,17 +280,23 @@ class Context:
         keep = []
         mem = None
         for i, q in enumerate(problems):
-            arrs = [q["xyz"], q["cell_nodes"], q["ff_nodes"], q["lambda_m"], q["lambda_f"], q["d_f"],
-                    q["dir_nodes"], q["dir_values"]]
+            general = "face_node_ptr" in q
+            topo = ([q[k] for k in ("face_node_ptr", "face_node_idx", "cell_face_ptr", "cell_face_idx",
+                                    "ff_face_ids")] if general else [q["cell_nodes"], q["ff_nodes"]])
+            arrs = [q["xyz"], *topo, q["lambda_m"], q["lambda_f"], q["d_f"], q["dir_nodes"], q["dir_values"]]
             keep.append(arrs)
             mm = _mem_of(*arrs)
             if mem is None:
                 mem = mm
             elif mm != mem:
                 raise ValueError("mix of host and device arrays in one batch")
-            size = (lambda a: int(a.numel() if _is_torch(a) else a.size))
-            ms[i] = vag_mesh(size(q["xyz"]) // 3, _ptr(q["xyz"], np.float64), size(q["cell_nodes"]) // 8,
-                             _ptr(q["cell_nodes"], np.int32), size(q["ff_nodes"]) // 4, _ptr(q["ff_nodes"], np.int32))
+            size = _size
+            if general:
+                ms[i] = _general_mesh(q["xyz"], *topo)
+            else:
+                ms[i] = vag_mesh(size(q["xyz"]) // 3, _ptr(q["xyz"], np.float64), size(q["cell_nodes"]) // 8,
+                                 _ptr(q["cell_nodes"], np.int32), size(q["ff_nodes"]) // 4,
+                                 _ptr(q["ff_nodes"], np.int32))
             ps[i] = vag_props(_ptr(q["lambda_m"], np.float64), _ptr(q["lambda_f"], np.float64),
                               _ptr(q["d_f"], np.float64), float(q["mu"]))
             bs[i] = vag_dirichlet(size(q["dir_nodes"]), _ptr(q["dir_nodes"], np.int32),
@@ -324,13 +358,13 @@ class System:
         self.ctx.check(self._L.vag_update_props(self.h, C.byref(p), mem))
 
     def solve(self, out=None, precision=VAG_FP64, precond=VAG_PC_JACOBI, rtol=1e-12, maxit=20000,
-              raise_on_error=True, krylov=VAG_KRYLOV_CG):
+              raise_on_error=True, krylov=VAG_KRYLOV_CG, inner_rtol=0.0):
         """Returns (u, info); u over [nodes | ffaces | cells]."""
         n = self.info().n_cv
         if out is None:
             out = np.empty(n)
         mem = _mem_of(out)
-        o = vag_solve_opts(precision, precond, float(rtol), int(maxit), mem, int(krylov))
+        o = vag_solve_opts(precision, precond, float(rtol), int(maxit), mem, int(krylov), float(inner_rtol))
         inf = vag_solve_info()
         st = self._L.vag_solve(self.h, C.byref(o), _ptr(out, np.float64), C.byref(inf))
         if raise_on_error:
@@ -347,7 +381,7 @@ class System:
 
     def kernel_time(self, kernel, reps=100):
         """Mean ms of one launch of a hot kernel on this system's data
-        (VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP)."""
+        (VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP, VAG_KERNEL_SPMV32)."""
         ms = C.c_double()
         self.ctx.check(self._L.vag_kernel_time(self.h, int(kernel), int(reps), C.byref(ms)))
         return ms.value
@@ -420,6 +454,30 @@ def problem_arrays(pb, device=False):
     return q
 
 
+def general_arrays(pb, device=False):
+    """The general polyhedral descriptor of a ``vag_inputs.Problem``-like
+    object (attributes faces [n_faces, q], cell_faces [n_cells, f], ff_faces
+    and the physical data) as a dict for ``Context.assemble_general`` or
+    ``Context.assemble_batch``."""
+    faces = np.ascontiguousarray(pb.faces, np.int32)
+    cf = np.ascontiguousarray(pb.cell_faces, np.int32)
+    q = dict(xyz=np.ascontiguousarray(pb.xyz, np.float64).ravel(),
+             face_node_ptr=np.arange(0, faces.size + 1, faces.shape[1], dtype=np.int32),
+             face_node_idx=faces.ravel(),
+             cell_face_ptr=np.arange(0, cf.size + 1, cf.shape[1], dtype=np.int32),
+             cell_face_idx=cf.ravel(),
+             ff_face_ids=np.ascontiguousarray(pb.ff_faces, np.int32),
+             lambda_m=np.ascontiguousarray(pb.lambda_m, np.float64).ravel(),
+             lambda_f=np.ascontiguousarray(pb.lambda_f, np.float64), d_f=np.ascontiguousarray(pb.d_f, np.float64),
+             dir_nodes=np.ascontiguousarray(pb.dir_nodes, np.int32),
+             dir_values=np.ascontiguousarray(pb.dir_values, np.float64))
+    if device:
+        import torch
+        q = {k: torch.from_numpy(v).cuda() for k, v in q.items()}
+    q["mu"] = pb.mu
+    return q
+
+
 def assemble_problem(ctx: Context, pb, device=False):
     """Marshal a ``vag_inputs.Problem``-like object (attributes xyz,
     cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values)."""
@@ -452,14 +510,20 @@ class Server:
         self._out = {}
 
     def submit(self, pb, n_steps=0, precision=VAG_FP64, precond=VAG_PC_JACOBI, rtol=1e-8, maxit=20000,
-               cfl=0.9, omega=0.5):
-        a = problem_arrays(pb)
+               cfl=0.9, omega=0.5, general=False):
+        """general: pass the mesh in the general polyhedral form."""
+        a = general_arrays(pb) if general else problem_arrays(pb)
         n_cv = pb.n_nodes + pb.n_ff + pb.n_cells
         u = np.empty(n_cv)
         c = np.empty(n_cv)
         keep = [a, np.ascontiguousarray(pb.phi_m, np.float64), np.ascontiguousarray(pb.phi_f, np.float64),
                 np.ascontiguousarray(pb.cbar, np.float64)]
-        m = vag_mesh(pb.n_nodes, _ptr(a["xyz"]), pb.n_cells, _ptr(a["cell_nodes"]), pb.n_ff, _ptr(a["ff_nodes"]))
+        if general:
+            m = _general_mesh(a["xyz"], a["face_node_ptr"], a["face_node_idx"], a["cell_face_ptr"],
+                              a["cell_face_idx"], a["ff_face_ids"])
+        else:
+            m = vag_mesh(pb.n_nodes, _ptr(a["xyz"]), pb.n_cells, _ptr(a["cell_nodes"]), pb.n_ff,
+                         _ptr(a["ff_nodes"]))
         pr = vag_props(_ptr(a["lambda_m"]), _ptr(a["lambda_f"]), _ptr(a["d_f"]), float(pb.mu))
         bc = vag_dirichlet(len(a["dir_nodes"]), _ptr(a["dir_nodes"]), _ptr(a["dir_values"]))
         q = vag_request(m, pr, bc, _ptr(keep[1]), _ptr(keep[2]), _ptr(keep[3]), None, float(omega), float(cfl),
