@@ -8,7 +8,7 @@ fracture/matrix permeability ratio 1e4.  One step, through the C ABI:
   vag_assemble  (symbolic phase, local VAG matrices on the 24 sub-tetrahedra
                  of every cell, fracture matrices, Schur row gather into CSR)
   vag_solve     (FP64 iterative refinement around FP32 CG preconditioned by
-                 the FP32 aggregation-AMG V-cycle, to ||b - A x|| <= 1e-8 ||b||
+                 the FP32 classical-AMG V-cycle, to ||b - A x|| <= 1e-8 ||b||
                  in FP64; cell recovery; fluxes)
   vag_transport (porous volumes, CFL step at CFL 0.9, upwind map, 1000
                  explicit steps)
@@ -52,7 +52,8 @@ WORKLOADS = {
         "metric": "Darcy solves/s (assemble + solve to 1e-8 rel. residual + 1000 transport steps), 128^3 DFN",
         "desc": ("mixed128: 128^3 jittered hex (2097152 cells, 2146689 nodes), DFN of 50 seeded rectangles "
                  "(97542 fracture faces), lognormal anisotropic Lambda_m, Lambda_f/Lambda_m = 1e4; FP64 iterative "
-                 "refinement around FP32 AMG-preconditioned CG to 1e-8 (FP64 residual); 1000 upwind steps at CFL 0.9"),
+                 "refinement around FP32 CG preconditioned by the FP32 AMG V-cycle, to 1e-8 (FP64 residual); "
+                 "1000 upwind steps at CFL 0.9"),
     },
     "scale64": {
         "n": 64, "ratio": 1e4, "precision": "fp64", "rtol": 1e-10, "transport_steps": 200,
@@ -79,6 +80,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precond", default="amg_rs", choices=["amg", "amg_rs"],
+                    help="the headline solver's preconditioner: aggregation (amg) or classical (amg_rs) AMG")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -583,7 +586,7 @@ def headline_arm(args):
     full_size = n_edge == w["n"]
     mixed = w["precision"] == "mixed"
     prec_main = pkg.VAG_MIXED if mixed else pkg.VAG_FP64
-    AMG = pkg.VAG_PC_AMG
+    AMG = pkg.VAG_PC_AMG_RS if args.precond == "amg_rs" else pkg.VAG_PC_AMG
     RTOL, NSTEPS = w["rtol"], w["transport_steps"]
 
     def upload(pb):
@@ -703,9 +706,13 @@ def headline_arm(args):
     if not args.no_extras:
         # the same step with every solver variant, to the workload's tolerance
         # (FP64 residual in all of them)
+        AGG, RS = pkg.VAG_PC_AMG, pkg.VAG_PC_AMG_RS
         if mixed:
             variants = [("mixed_amg", pkg.VAG_MIXED, AMG, 3), ("fp64_amg", pkg.VAG_FP64, AMG, 3),
-                        ("fp64_pc32_amg", pkg.VAG_FP64_PC32, AMG, 3), ("mixed16_amg", pkg.VAG_MIXED_F16, AMG, 3),
+                        ("fp64_pc32_amg", pkg.VAG_FP64_PC32, AMG, 3),
+                        ("mixed_agg", pkg.VAG_MIXED, AGG, 3), ("mixed_rs", pkg.VAG_MIXED, RS, 3),
+                        ("fp64_agg", pkg.VAG_FP64, AGG, 3), ("fp64_rs", pkg.VAG_FP64, RS, 3),
+                        ("mixed16_agg", pkg.VAG_MIXED_F16, AGG, 3),
                         ("fp64_jacobi", pkg.VAG_FP64, pkg.VAG_PC_JACOBI, 1)]
         else:
             variants = [("fp64_amg", pkg.VAG_FP64, AMG, 3), ("mixed_amg", pkg.VAG_MIXED, AMG, 3),
@@ -773,11 +780,10 @@ def headline_arm(args):
                       "bytes": nbytes, "gbs": nbytes / t / 1e6, "frac_hbm": nbytes / t / 1e6 / peak,
                       "fp64_gflops": flops / t / 1e6, "frac_fp64": flops / t / 1e6 / fp64_peak}
 
-    # per control volume: its position and length in the sorted tile (2 B),
-    # diagonal (8), c read (8), c' written (8), a slice offset per 32 rows;
-    # per inflow edge: weight (8) and column (4)
-    add("k_step (upwind transport step)", pkg.VAG_KERNEL_TRANSPORT_STEP, NSTEPS,
-        ncv * 26 + nnzt * 12 + 4 * ((ncv + 31) // 32), 2 * nnzt + ncv)
+    # per control volume: row pointer (4 B), diagonal (8), c read (8), c'
+    # written (8); per inflow edge: weight (8) and column (4)
+    add("k_step (upwind transport step)", pkg.VAG_KERNEL_TRANSPORT_STEP, NSTEPS, ncv * 28 + nnzt * 12,
+        2 * nnzt + ncv)
     if mixed:
         add("k_spmv32 (FP32 SELL q = A p of the inner CG)", pkg.VAG_KERNEL_SPMV32, its,
             nnz * 8 + (nr + 1) * 4 + nr * 8, 0)
@@ -808,7 +814,9 @@ def headline_arm(args):
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
             "config": {"workload": w["desc"] if full_size else f"{workload} at {n_edge}^3 (profiling case)",
-                       "precision": w["precision"], "precond": "amg", "rtol": RTOL, "transport_steps": NSTEPS,
+                       "precision": w["precision"],
+                       "precond": "classical AMG" if args.precond == "amg_rs" else "aggregation AMG",
+                       "rtol": RTOL, "transport_steps": NSTEPS,
                        "n_rows": nr, "nnz": nnz, "n_cv": ncv, "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},

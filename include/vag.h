@@ -65,8 +65,15 @@ enum { VAG_FP64 = 0, VAG_MIXED = 1, VAG_MIXED_F16 = 2, VAG_FP64_PC32 = 3 };
  * acceleration of Jacobi (a degree-3 polynomial in D^-1 A times D^-1) on
  * [b/100, b], b = 1.2 x the largest Ritz value of D^-1 A after ten Lanczos
  * (Jacobi-CG) steps from a pseudo-random vector, FP64 only; VAG_PC_AMG, the
- * library's aggregation AMG V-cycle (FP64, or FP32 under VAG_MIXED). */
-enum { VAG_PC_JACOBI = 0, VAG_PC_CHEBYSHEV = 1, VAG_PC_AMG = 2 };
+ * library's aggregation AMG V-cycle (FP64, or FP32 under VAG_MIXED);
+ * VAG_PC_AMG_RS, a classical (Ruge-Stueben-type) AMG V-cycle, the counterpart
+ * of the classical AMG of the paper's solver experiments (Sec. 5.3): strength
+ * on negative couplings (theta = 0.25), PMIS coarse/fine splitting with a
+ * second pass, direct interpolation from at most four coarse neighbours,
+ * Galerkin R A P with R = P^T, the same l1-Jacobi sweeps; FP64, FP32 under
+ * VAG_MIXED or VAG_FP64_PC32 (not VAG_MIXED_F16).  Wherever VAG_PC_AMG is
+ * accepted, VAG_PC_AMG_RS is too. */
+enum { VAG_PC_JACOBI = 0, VAG_PC_CHEBYSHEV = 1, VAG_PC_AMG = 2, VAG_PC_AMG_RS = 3 };
 /* Krylov method: CG (the system is SPD), or one of the methods of the
  * paper's solver experiments (§5.3), both right-preconditioned: BiCGStab, or
  * restarted GMRES(30) (classical Gram-Schmidt applied twice, Givens

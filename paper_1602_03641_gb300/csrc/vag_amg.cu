@@ -628,6 +628,43 @@ __device__ __forceinline__ T restrict_row(int I, const int *__restrict__ mptr, c
 }
 
 
+// classical levels: bc = R r and the coarse level's zero-start sweep tc =
+// omega D_l1^-1 bc, row_lanes<T>() lanes per coarse row
+template <class T>
+__global__ void __launch_bounds__(256) k_rs_restrict(int nc, const int *__restrict__ rrow, const int *__restrict__ rcol,
+                                                     const T *__restrict__ rval, const T *__restrict__ r,
+                                                     const T *__restrict__ sinv_c, T *__restrict__ bc,
+                                                     T *__restrict__ tc) {
+  constexpr int LN = row_lanes<T>();
+  const int lane = threadIdx.x & (LN - 1);
+  const int I = blockIdx.x * (256 / LN) + threadIdx.x / LN;
+  const bool valid = I < nc;
+  RowPF<T> f;
+  row_prefetch<LN>(f, I, valid, lane, rrow, rcol, rval);
+  const T si = valid ? sinv_c[I] : (T)0;
+  pdl_wait();
+  pdl_trigger();
+  const T s = row_finish<LN>(f, rcol, rval, r);
+  if (valid && lane == 0) {
+    bc[I] = s;
+    tc[I] = jac_first_row(s, si);
+  }
+}
+
+// classical levels: x += P xc, one thread per fine row (at most four entries)
+template <class T>
+__global__ void k_rs_prolong(int n, const int *__restrict__ prow, const int *__restrict__ pcol,
+                             const T *__restrict__ pval, const T *__restrict__ xc, T *x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = i < n ? prow[i] : 0, e = i < n ? prow[i + 1] : 0;
+  pdl_wait();
+  pdl_trigger();
+  if (i >= n || b == e) return;
+  T s = 0;
+  for (int k = b; k < e; ++k) s = fma(pval[k], xc[pcol[k]], s);
+  x[i] += s;
+}
+
 template <class T>
 __global__ void k_prolong(int n, const int *__restrict__ agg, const T *__restrict__ xc, T *x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1130,7 +1167,8 @@ __global__ void k_to_f64(int n, const float *__restrict__ a, double *__restrict_
 
 // Build the hierarchy for the current matrix values (called before every
 // AMG solve: the numeric phase may have changed them).
-void amg_setup(System *s, bool f32, bool f16) {
+void amg_setup(System *s, bool f32, bool f16, bool classical) {
+  if (classical && f16) fail(VAG_EINVAL, "the FP16 finest level is for the aggregation hierarchy only");
   cudaStream_t st = s->ctx->stream;
   Amg &A = s->amg;
   const int ns = s->seg.n_sys;
@@ -1209,6 +1247,13 @@ void amg_setup(System *s, bool f32, bool f16) {
         if (read_status(s) & ST_NONPOSITIVE) fail(VAG_EINVAL, "AMG: a terminal block is not positive definite");
       }
       if (all) break;
+    }
+    if (classical) {   // C/F splitting, interpolation, Galerkin R A P
+      AmgLevel C;
+      rs_coarsen(s, A.levels[lvl], C, alloc);
+      trace_mark(st, "level: classical coarsening + Galerkin product");
+      A.levels.push_back(C);
+      continue;
     }
     AmgLevel &L = A.levels[lvl];
     const int n = L.n;
@@ -1315,6 +1360,7 @@ void amg_setup(System *s, bool f32, bool f16) {
   // FP32 copy of the hierarchy (the mixed-precision path)
   A.f32 = f32;
   A.f16 = false;
+  A.classical = classical;
   if (f32) {
     auto cast = [&](const double *src, int64_t n) -> float * {
       float *d = static_cast<float *>(alloc(4 * (size_t)std::max<int64_t>(n, 1)));
@@ -1349,6 +1395,10 @@ void amg_setup(System *s, bool f32, bool f16) {
       }
       L.sinv32 = cast(L.sinv, L.n);
       L.inv32 = L.any_term ? cast(L.inv, L.n_inv) : nullptr;
+      if (L.prow) {
+        L.pval32 = cast(L.pval, L.p_nnz);
+        L.rval32 = cast(L.rval, L.r_nnz);
+      }
       L.x32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
       L.b32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
       L.t32 = static_cast<float *>(alloc(4 * (size_t)std::max(L.n, 1)));
@@ -1369,8 +1419,8 @@ void amg_setup(System *s, bool f32, bool f16) {
   // fit the tail's shared memory; from there the V-cycle runs in one kernel.
   // (Not for FP64: one SM issues about two FP64 FMAs per clock on GB300, so
   // FP64 work must spread over the whole GPU.)
-  A.tail_start = -1;
-  for (size_t l0 = 1; f32 && l0 < A.levels.size() && A.tail_start < 0; ++l0) {
+  A.tail_start = -1;   // the one-kernel tail walks aggregates: not for classical levels
+  for (size_t l0 = 1; f32 && !classical && l0 < A.levels.size() && A.tail_start < 0; ++l0) {
     if ((int)(A.levels.size() - l0) > kTailLevels) continue;
     size_t need[2] = {0, 0};
     for (int g = 0; g < ns; ++g) {
@@ -1424,16 +1474,17 @@ template <class T>
 struct LV {
   const T *val, *sinv, *inv, *sval;
   T *x, *b, *t, *r;
+  const T *pv, *rv;   // classical levels: values of P and R
 };
 template <class T>
 static LV<T> lv(System *s, AmgLevel &L);
 template <>
 LV<double> lv<double>(System *, AmgLevel &L) {
-  return {L.val, L.sinv, L.inv, L.sval, L.x, L.b, L.t, L.r};
+  return {L.val, L.sinv, L.inv, L.sval, L.x, L.b, L.t, L.r, L.pval, L.rval};
 }
 template <>
 LV<float> lv<float>(System *, AmgLevel &L) {
-  return {L.val32, L.sinv32, L.inv32, L.sval32, L.x32, L.b32, L.t32, L.r32};
+  return {L.val32, L.sinv32, L.inv32, L.sval32, L.x32, L.b32, L.t32, L.r32, L.pval32, L.rval32};
 }   // val32 on coarse levels, sval32 on level 0
 
 // The levels from lvl down, V(2,2) from a zero initial guess, in one kernel.
@@ -1514,9 +1565,22 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
     if (!cg) launch_pdl(k_jac_first<T>, g, TB, 0, st, n, b, v.sinv, v.t);
     launch_pdl(resid_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr,
                (const int *)L.scol, v.sval, b, (const T *)v.t, v.r);
-    launch_pdl(k_restrict_first<T>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
-               (const T *)v.r, c.sinv, c.b, c.t);
+    if (A.classical)
+      launch_pdl(k_rs_restrict<T>, grid_for(C.n, 256 / LN), 256, 0, st, C.n, (const int *)L.rrow,
+                 (const int *)L.rcol, v.rv, (const T *)v.r, c.sinv, c.b, c.t);
+    else
+      launch_pdl(k_restrict_first<T>, grid_for(C.n, TB), TB, 0, st, C.n, (const int *)L.mptr, (const int *)L.mem,
+                 (const T *)v.r, c.sinv, c.b, c.t);
     note_launches(cg ? 2 : 3);
+  } else if (A.classical) {
+    // classical coarse levels: second sweep, residual, restriction R
+    launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
+               (const T *)v.t, x, (const uint8_t *)L.skip);
+    launch_pdl(k_resid_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, b,
+               (const T *)x, v.t);
+    launch_pdl(k_rs_restrict<T>, grid_for(C.n, 256 / LN), 256, 0, st, C.n, (const int *)L.rrow, (const int *)L.rcol,
+               v.rv, (const T *)v.t, c.sinv, c.b, c.t);
+    note_launches(3);
   } else {
     // coarse levels: CSR, 8 lanes per row; residual and restriction fused
     launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
@@ -1546,11 +1610,16 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
                (const __half *)A.sval16, (const float *)A.sinv16, bb, (const float *)tt, xx, (const uint8_t *)L.skip);
     note_launches(2);
   } else if (lvl == 0) {
-    launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, v.t);
+    if (A.classical)
+      launch_pdl(k_rs_prolong<T>, g, TB, 0, st, n, (const int *)L.prow, (const int *)L.pcol, v.pv, (const T *)c.x,
+                 v.t);
+    else
+      launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, v.t);
     if constexpr (sizeof(T) == 8) {
       if (cg) {
       auto jr = s->sell_u == 2 ? k_jac_sell_rz<2> : s->sell_u == 8 ? k_jac_sell_rz<8> : k_jac_sell_rz<4>;
-      const Tiles tl{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0};
+      const Tiles tl{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0, s->seg.sys_grp0,
+                     s->seg.n_tiles, s->seg.n_sys};
       launch_pdl(jr, s->seg.n_tiles, 256, 0, st, (const int *)L.rowptr, (const int *)L.slice_ptr,
                  (const int *)L.scol, (const double *)v.sval, (const double *)v.sinv, (const double *)b,
                  (const double *)v.t, (double *)x, (const uint8_t *)L.skip, tl, s->partials, s->counter, s->ks,
@@ -1562,6 +1631,14 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
     launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
     note_launches(2);
+  } else if (A.classical) {
+    // coarse correction x += P x_c, then two sweeps
+    launch_pdl(k_rs_prolong<T>, g, TB, 0, st, n, (const int *)L.prow, (const int *)L.pcol, v.pv, (const T *)c.x, x);
+    launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
+               (const T *)x, v.t, (const uint8_t *)L.skip);
+    launch_pdl(k_jac_csr<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
+               (const T *)v.t, x, (const uint8_t *)L.skip);
+    note_launches(3);
   } else {
     launch_pdl(k_prolong_jac8<T>, gL, 256, 0, st, n, (const int *)L.rowptr, (const int *)L.col, v.val, v.sinv, b,
                (const T *)x, (const int *)L.agg, (const T *)c.x, v.t, (const uint8_t *)L.skip);

@@ -437,12 +437,13 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     if (opts->precision != VAG_FP64 && opts->precision != VAG_MIXED && opts->precision != VAG_MIXED_F16 &&
         opts->precision != VAG_FP64_PC32)
       fail(VAG_EINVAL, "unknown precision");
+    const bool amg = opts->precond == VAG_PC_AMG || opts->precond == VAG_PC_AMG_RS;
     if (opts->precision == VAG_MIXED_F16 && opts->precond != VAG_PC_AMG)
-      fail(VAG_EINVAL, "VAG_MIXED_F16 stores the AMG finest level in FP16: it needs VAG_PC_AMG");
-    if (opts->precision == VAG_FP64_PC32 && opts->precond != VAG_PC_AMG)
-      fail(VAG_EINVAL, "VAG_FP64_PC32 preconditions by the FP32 AMG hierarchy: it needs VAG_PC_AMG");
+      fail(VAG_EINVAL, "VAG_MIXED_F16 stores the aggregation AMG finest level in FP16: it needs VAG_PC_AMG");
+    if (opts->precision == VAG_FP64_PC32 && !amg)
+      fail(VAG_EINVAL, "VAG_FP64_PC32 preconditions by the FP32 AMG hierarchy: it needs an AMG preconditioner");
     if (!(opts->inner_rtol >= 0.0 && opts->inner_rtol < 1.0)) fail(VAG_EINVAL, "inner_rtol must be in [0, 1)");
-    if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_CHEBYSHEV && opts->precond != VAG_PC_AMG)
+    if (opts->precond != VAG_PC_JACOBI && opts->precond != VAG_PC_CHEBYSHEV && !amg)
       fail(VAG_EINVAL, "unknown preconditioner");
     if (opts->precond == VAG_PC_CHEBYSHEV && opts->precision != VAG_FP64)
       fail(VAG_EINVAL, "VAG_PC_CHEBYSHEV runs in FP64 only");
@@ -454,16 +455,14 @@ vag_status vag_solve(vag_system *sys, const vag_solve_opts *opts, double *u_out,
     if (opts->krylov != VAG_KRYLOV_CG && opts->krylov != VAG_KRYLOV_BICGSTAB && opts->krylov != VAG_KRYLOV_GMRES)
       fail(VAG_EINVAL, "unknown Krylov method");
     if (opts->krylov == VAG_KRYLOV_BICGSTAB) {
-      if (opts->precision == VAG_MIXED && opts->precond != VAG_PC_AMG)
-        fail(VAG_EINVAL, "BiCGStab with VAG_MIXED needs VAG_PC_AMG");
+      if (opts->precision == VAG_MIXED && !amg) fail(VAG_EINVAL, "BiCGStab with VAG_MIXED needs an AMG preconditioner");
       bicgstab_solve(s, opts, inf);
     } else if (opts->krylov == VAG_KRYLOV_GMRES) {
-      if (opts->precision == VAG_MIXED && opts->precond != VAG_PC_AMG)
-        fail(VAG_EINVAL, "GMRES with VAG_MIXED needs VAG_PC_AMG");
+      if (opts->precision == VAG_MIXED && !amg) fail(VAG_EINVAL, "GMRES with VAG_MIXED needs an AMG preconditioner");
       gmres_solve(s, opts, inf);
     } else if (opts->precision == VAG_MIXED && opts->precond == VAG_PC_JACOBI) {
       mixed_solve(s, opts, inf);
-    } else if ((opts->precision == VAG_MIXED || opts->precision == VAG_MIXED_F16) && opts->precond == VAG_PC_AMG) {
+    } else if ((opts->precision == VAG_MIXED || opts->precision == VAG_MIXED_F16) && amg) {
       mixed_amg_solve(s, opts, inf);
     } else {
       pcg_solve(s, opts, inf);

@@ -45,7 +45,8 @@ constexpr double kChebRatio = 100.0;
 constexpr int kCoefStride = 2 * kChebDegree;
 
 Tiles tiles_of(const System *s) {
-  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0};
+  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0, s->seg.sys_grp0,
+               s->seg.n_tiles, s->seg.n_sys};
 }
 
 // Pseudo-random start vector, uniform in [-1, 1): the SplitMix64 output

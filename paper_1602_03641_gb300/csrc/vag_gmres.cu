@@ -46,7 +46,8 @@ struct GmState {
 };
 
 Tiles tiles_of(const System *s) {
-  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0};
+  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0, s->seg.sys_grp0,
+               s->seg.n_tiles, s->seg.n_sys};
 }
 
 // Sum over the 32 lanes of a warp (all lanes get the total).
@@ -280,7 +281,7 @@ void gmres_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   cudaStream_t st = s->ctx->stream;
   ensure_krylov_buffers(s);
   tune_sell(s);
-  const bool amg = o->precond == VAG_PC_AMG;
+  const bool amg = o->precond == VAG_PC_AMG || o->precond == VAG_PC_AMG_RS;
   const bool cheb = o->precond == VAG_PC_CHEBYSHEV;
   const int ns = s->seg.n_sys;
   const int nt = s->seg.n_tiles;
@@ -298,7 +299,7 @@ void gmres_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   float setup_ms = 0.f;
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   if (amg || cheb) {
-    if (amg) amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16);
+    if (amg) amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16, o->precond == VAG_PC_AMG_RS);
     else cheb_setup(s);
     VAG_CUDA(cudaEventRecord(s->ev1, st));
     VAG_CUDA(cudaEventSynchronize(s->ev1));

@@ -121,6 +121,12 @@ struct AmgLevel {
   // FP32 copy (mixed-precision path)
   float *val32 = nullptr, *sinv32 = nullptr, *inv32 = nullptr;
   float *x32 = nullptr, *b32 = nullptr, *t32 = nullptr;
+  // classical hierarchy: interpolation P [n x nc] and restriction R = P^T
+  // [nc x n] in CSR (FP64, FP32 copies for the mixed path)
+  int *prow = nullptr, *pcol = nullptr, *rrow = nullptr, *rcol = nullptr;
+  double *pval = nullptr, *rval = nullptr;
+  float *pval32 = nullptr, *rval32 = nullptr;
+  int64_t p_nnz = 0, r_nnz = 0;
 };
 struct Amg {
   std::vector<AmgLevel> levels;
@@ -128,6 +134,7 @@ struct Amg {
   size_t bytes = 0;
   bool built = false;
   bool f32 = false;                // V-cycle in FP32
+  bool classical = false;          // classical (Ruge-Stueben-type) levels instead of aggregation
   int tail_start = -1;             // first level run by the one-kernel tail
   size_t tail_smem[2] = {0, 0};    // its dynamic shared memory (FP64, FP32)
   float *sval32 = nullptr;         // FP32 sliced-ELL values of A (finest level)
@@ -145,6 +152,7 @@ struct Mixed {
   float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
   float *z32 = nullptr;        // preconditioned inner residual (AMG)
   float *dval32 = nullptr;     // FP32 difference-form values of A, sliced ELL (AMG)
+  float *rowsum32 = nullptr;   // [n_rows] its row sums
   bool dstale = true;
   cudaGraphExec_t graph_amg = nullptr;   // inner iterations with the V-cycle, rebuilt per solve
   size_t graph_amg_nodes = 0;
@@ -170,6 +178,8 @@ struct Segments {
   int *tile_row0 = nullptr;          // [n_tiles+1] (row range of tile t: [row0[t], row1[t]))
   int *tile_row1 = nullptr;
   int *sys_tile0 = nullptr;          // [n_sys+1] first tile of each system
+  int *sys_grp0 = nullptr;           // [n_sys+1] first reduction group of each system
+  int n_groups = 0;                  // reduction groups (kSegGroup tiles each, per system)
   int *cv_sys = nullptr;             // [n_cv] system of each control volume
 };
 
@@ -276,16 +286,6 @@ struct System {
   int *tcol = nullptr;         // [nnz_t]
   double *tval = nullptr;      // [nnz_t]
   int64_t t_cap = 0;
-  // the same map as the step kernel reads it: per 256-CV tile the rows sorted
-  // by inflow count (tperm: row offset inside the tile, tlen: its count,
-  // tdiag_s: its diagonal), entries column-major in 32-row slices
-  int n_tiles_t = 0;
-  uint8_t *tperm = nullptr, *tlen = nullptr;   // [256 n_tiles_t]
-  double *tdiag_s = nullptr;                   // [256 n_tiles_t]
-  int *tslice_ptr = nullptr;                   // [8 n_tiles_t + 1] element offsets
-  int *tscol = nullptr;                        // [ts_cap]
-  double *tsval = nullptr;                     // [ts_cap]
-  int64_t ts_cap = 0;
   double *cbuf = nullptr;      // [2 n_cv]
   double *dts = nullptr;       // [2 n_sys]: per system dt_max, dt
   cudaGraphExec_t step_graph = nullptr;   // kStepChunk transport steps
@@ -395,7 +395,11 @@ void gmres_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void launch_spmv_plain(System *s, const double *x, double *y, cudaStream_t st);
 // ks[sys].res2 = ||b - A x||^2 per system (x = s->kx)
 void true_residual2(System *s, cudaStream_t st);
-void amg_setup(System *s, bool f32, bool f16 = false);
+void amg_setup(System *s, bool f32, bool f16 = false, bool classical = false);
+// classical coarsening of level L into C (vag_amg_rs.cu): fills L's P and R
+// and C's matrix, diagonal inverse and system row starts; alloc gives the
+// hierarchy's own memory
+void rs_coarsen(System *s, AmgLevel &L, AmgLevel &C, const std::function<void *(size_t)> &alloc);
 void amg_apply(System *s, const double *r, double *z, cudaStream_t st);
 // z = V(r) on FP32 vectors with the FP32 hierarchy (the inner solve of the
 // refinement loop); r and z must not be the hierarchy's own level-0 vectors

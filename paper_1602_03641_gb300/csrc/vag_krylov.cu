@@ -339,7 +339,8 @@ __global__ void k_scatter_dir(int nd, const int *__restrict__ dn, const double *
 }
 
 Tiles tiles_of(const System *s) {
-  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0};
+  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0, s->seg.sys_grp0,
+               s->seg.n_tiles, s->seg.n_sys};
 }
 
 // ------------------------------------------------------------- BiCGStab ----
@@ -512,6 +513,10 @@ void build_tiles(System *s) {
   st[g.n_sys] = (int)tsys.size();
   g.n_tiles = (int)tsys.size();
   g.tile_start_h = st;
+  std::vector<int> gr(g.n_sys + 1, 0);   // reduction groups of each system's tiles
+  for (int i = 0; i < g.n_sys; ++i) gr[i + 1] = gr[i] + (st[i + 1] - st[i] + kSegGroup - 1) / kSegGroup;
+  g.n_groups = gr[g.n_sys];
+  g.sys_grp0 = sys_alloc<int>(s, g.n_sys + 1);
   g.tile_sys = sys_alloc<int>(s, g.n_tiles);
   g.tile_row0 = sys_alloc<int>(s, g.n_tiles);
   g.tile_row1 = sys_alloc<int>(s, g.n_tiles);
@@ -521,6 +526,7 @@ void build_tiles(System *s) {
   VAG_CUDA(cudaMemcpyAsync(g.tile_row0, t0.data(), sizeof(int) * g.n_tiles, cudaMemcpyHostToDevice, str));
   VAG_CUDA(cudaMemcpyAsync(g.tile_row1, t1.data(), sizeof(int) * g.n_tiles, cudaMemcpyHostToDevice, str));
   VAG_CUDA(cudaMemcpyAsync(g.sys_tile0, st.data(), sizeof(int) * (g.n_sys + 1), cudaMemcpyHostToDevice, str));
+  VAG_CUDA(cudaMemcpyAsync(g.sys_grp0, gr.data(), sizeof(int) * (g.n_sys + 1), cudaMemcpyHostToDevice, str));
   VAG_CUDA(cudaStreamSynchronize(str));   // host vectors go out of scope
 }
 
@@ -578,12 +584,15 @@ void ensure_krylov_buffers(System *s) {
   s->kr = sys_alloc<double>(s, s->n_rows);
   s->kp = sys_alloc<double>(s, s->n_rows);
   s->kq = sys_alloc<double>(s, s->n_rows);
-  s->partials = sys_alloc<double>(s, std::max<size_t>(2 * (size_t)s->seg.n_tiles, (size_t)kMaxRedBlocks));
-  s->counter = sys_alloc<unsigned>(s, ns + 1);
+  // tile partials, then group partials (two values each at most)
+  s->partials = sys_alloc<double>(s, std::max<size_t>(2 * ((size_t)s->seg.n_tiles + s->seg.n_groups),
+                                                      (size_t)kMaxRedBlocks));
+  // per-system counters, one spare, then the group counters
+  s->counter = sys_alloc<unsigned>(s, ns + 1 + s->seg.n_groups);
   s->ks = sys_alloc<KrylovScalars>(s, ns);
   s->n_done = sys_alloc<int>(s, 1);
   s->u = sys_alloc<double>(s, (size_t)s->n_cv);
-  VAG_CUDA(cudaMemsetAsync(s->counter, 0, (ns + 1) * sizeof(unsigned), s->ctx->stream));
+  VAG_CUDA(cudaMemsetAsync(s->counter, 0, (ns + 1 + s->seg.n_groups) * sizeof(unsigned), s->ctx->stream));
   VAG_CUDA(cudaMemsetAsync(s->u, 0, sizeof(double) * s->n_cv, s->ctx->stream));
   if (!s->ks_host) VAG_CUDA(cudaMallocHost(&s->ks_host, sizeof(KrylovScalars) * ns));
   if (!s->n_done_host) VAG_CUDA(cudaMallocHost(&s->n_done_host, sizeof(int)));
@@ -696,7 +705,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   cudaStream_t st = s->ctx->stream;
   ensure_krylov_buffers(s);
   tune_sell(s);
-  const bool amg = o->precond == VAG_PC_AMG;
+  const bool amg = o->precond == VAG_PC_AMG || o->precond == VAG_PC_AMG_RS;
   const bool cheb = o->precond == VAG_PC_CHEBYSHEV;
   const bool general = amg || cheb;   // z = M r by a general operator
   const int ns = s->seg.n_sys;
@@ -706,7 +715,7 @@ void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   if (general) {
     if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
-    if (amg) amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16);
+    if (amg) amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16, o->precond == VAG_PC_AMG_RS);
     else cheb_setup(s);
     trace_mark(st, amg ? "AMG setup" : "Chebyshev setup (Lanczos bounds)");
     VAG_CUDA(cudaEventRecord(s->ev1, st));
@@ -812,7 +821,7 @@ void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   cudaStream_t st = s->ctx->stream;
   ensure_krylov_buffers(s);
   tune_sell(s);
-  const bool amg = o->precond == VAG_PC_AMG;
+  const bool amg = o->precond == VAG_PC_AMG || o->precond == VAG_PC_AMG_RS;
   const bool cheb = o->precond == VAG_PC_CHEBYSHEV;
   const int nt = s->seg.n_tiles;
   const Tiles tl = tiles_of(s);
@@ -827,7 +836,7 @@ void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   VAG_CUDA(cudaEventRecord(s->ev0, st));
   if (amg) {
     if (!s->kz) s->kz = sys_alloc<double>(s, s->n_rows);
-    amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16);
+    amg_setup(s, o->precision != VAG_FP64, o->precision == VAG_MIXED_F16, o->precond == VAG_PC_AMG_RS);
     VAG_CUDA(cudaEventRecord(s->ev1, st));
     VAG_CUDA(cudaEventSynchronize(s->ev1));
     cudaEventElapsedTime(&setup_ms, s->ev0, s->ev1);

@@ -20,8 +20,8 @@
 // needs; the correction is x += ||r|| y.  The inner product uses the
 // difference form of A,
 //   (A p)_i = sum_{j != i} a_ij (p_j - p_i) + (sum_j a_ij) p_i,
-// with the off-diagonal entries in FP32 and the row sum (FP64, rounded once)
-// in the diagonal slot: rounding each entry of a VAG row to FP32 would break
+// with the off-diagonal entries in FP32 (0 in the diagonal slot) and the row
+// sum (FP64, rounded once) in an array of its own: rounding each entry of a VAG row to FP32 would break
 // its zero row sum by about 6e-8 |a_ii|, a spurious reaction term that, at
 // fracture/matrix contrasts near 1e6, changes the smooth modes of the inner
 // operator; in difference form constants are annihilated exactly and p_j -
@@ -42,7 +42,8 @@ constexpr double kEtaAmg = 1e-6;
 constexpr int kMaxOuter = 40;
 
 Tiles tiles_of(const System *s) {
-  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0};
+  return Tiles{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0, s->seg.sys_grp0,
+               s->seg.n_tiles, s->seg.n_sys};
 }
 
 __global__ void k_dscale(int n, const double *__restrict__ dinv, double *__restrict__ sc) {
@@ -230,25 +231,28 @@ __global__ void __launch_bounds__(NT) k_ir_resid(const double *__restrict__ b, c
 // ---- inner FP32 CG preconditioned by the FP32 AMG V-cycle ----
 
 // FP32 difference-form values in the sliced-ELL layout (padding stays 0):
-// off-diagonal entries as they are, the diagonal slot holding sum_j a_ij
+// off-diagonal entries as they are, 0 in the diagonal slot, and the row sum
+// sum_j a_ij (FP64, rounded once) in its own array
 __global__ void k_dform_vals(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
                              const double *__restrict__ val, const int *__restrict__ slice_ptr,
-                             float *__restrict__ out) {
+                             float *__restrict__ out, float *__restrict__ rowsum) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = rowptr[i], e = rowptr[i + 1];
   double rs = 0.0;
   for (int k = b; k < e; ++k) rs += val[k];
   const int base = slice_ptr[i >> 5] + (i & 31);
-  for (int k = b; k < e; ++k) out[base + 32 * (k - b)] = (float)(col[k] == i ? rs : val[k]);
+  for (int k = b; k < e; ++k) out[base + 32 * (k - b)] = col[k] == i ? 0.f : (float)val[k];
+  rowsum[i] = (float)rs;
 }
 
 // q = A p in difference form and the partial p.q (as k_spmv32)
 template <int U>
 __global__ void __launch_bounds__(NT) k_spmv32d(const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
                                                 const int *__restrict__ scol, const float *__restrict__ sval,
-                                                const float *__restrict__ x, float *__restrict__ y, Tiles tl,
-                                                double *partials, unsigned *counter, KrylovScalars *ks, int *n_done) {
+                                                const float *__restrict__ rowsum, const float *__restrict__ x,
+                                                float *__restrict__ y, Tiles tl, double *partials, unsigned *counter,
+                                                KrylovScalars *ks, int *n_done) {
   const int t = blockIdx.x;
   const int sys = tl.sys[t];
   pdl_wait();
@@ -262,11 +266,11 @@ __global__ void __launch_bounds__(NT) k_spmv32d(const int *__restrict__ rowptr, 
     const float pi = x[row];
     float s = 0.f;
 #pragma unroll(U)
-    for (int k = 0; k < len; ++k) {
+    for (int k = 0; k < len; ++k) {   // the diagonal slot holds 0 and x_i - x_i = 0
       const int idx = base + 32 * k;
-      const int c = scol[idx];
-      s = fmaf(sval[idx], c == row ? pi : x[c] - pi, s);
+      s = fmaf(sval[idx], x[scol[idx]] - pi, s);
     }
+    s = fmaf(rowsum[row], pi, s);
     y[row] = s;
     dp = fmaf(pi, s, dp);
   }
@@ -534,15 +538,16 @@ void mixed_amg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   const int ns = s->seg.n_sys, nt = s->seg.n_tiles;
   const Tiles tl = tiles_of(s);
   VAG_CUDA(cudaEventRecord(s->ev0, st));
-  amg_setup(s, /*f32=*/true, o->precision == VAG_MIXED_F16);
+  amg_setup(s, /*f32=*/true, o->precision == VAG_MIXED_F16, o->precond == VAG_PC_AMG_RS);
   if (!m.dval32) {
     m.dval32 = sys_alloc<float>(s, (size_t)std::max<int64_t>(s->sell_nnz, 1));
+    m.rowsum32 = sys_alloc<float>(s, (size_t)s->n_rows);
     m.dstale = true;
   }
   if (m.dstale) {   // after every numeric phase
     VAG_CUDA(cudaMemsetAsync(m.dval32, 0, sizeof(float) * (size_t)s->sell_nnz, st));
     k_dform_vals<<<grid_for(s->n_rows, NT), NT, 0, st>>>(s->n_rows, s->rowptr, s->col, s->val, s->slice_ptr,
-                                                          m.dval32);
+                                                          m.dval32, m.rowsum32);
     note_launches(1);
     VAG_CHECK_LAUNCH();
     m.dstale = false;
@@ -557,7 +562,8 @@ void mixed_amg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   // one inner iteration: q = A p (p.q, alpha), x/r update, z = V(r), r.z, p
   auto iteration = [&]() {
     launch_pdl(spmv32, nt, NT, 0, st, (const int *)s->rowptr, (const int *)s->slice_ptr, (const int *)s->scol, a32,
-               (const float *)m.p32, m.q32, tl, s->partials, s->counter, m.ks_in, m.n_done_in);
+               (const float *)m.rowsum32, (const float *)m.p32, m.q32, tl, s->partials, s->counter, m.ks_in,
+               m.n_done_in);
     launch_pdl(k_irm_update, nt, NT, 0, st, m.x32, m.r32, (const float *)m.p32, (const float *)m.q32, tl, s->partials,
                s->counter, m.ks_in, m.n_done_in);
     amg_apply_f32(s, m.r32, m.z32, st);
@@ -638,8 +644,8 @@ double time_spmv32(System *s, int reps) {
   VAG_CUDA(cudaMemsetAsync(m.ks_in, 0, sizeof(KrylovScalars) * ns, st));   // done = 0 everywhere
   auto launch = [&]() {
     launch_pdl(spmv32, nt, NT, 0, st, (const int *)s->rowptr, (const int *)s->slice_ptr, (const int *)s->scol,
-               (const float *)m.dval32, (const float *)m.p32, m.q32, tl, s->partials, s->counter, m.ks_in,
-               m.n_done_in);
+               (const float *)m.dval32, (const float *)m.rowsum32, (const float *)m.p32, m.q32, tl, s->partials,
+               s->counter, m.ks_in, m.n_done_in);
     note_launches(1);
   };
   launch();   // warm-up

@@ -56,13 +56,24 @@ __device__ __forceinline__ bool grid_sum(const double (&v)[K], double *partials,
 
 // Row tiles of a batch: tile t covers rows [row0[t], row1[t]) of system
 // sys[t]; sys_tile0 gives the first tile of each system (n_sys+1 entries).
+// The tiles of a system form groups of kSegGroup consecutive tiles (the last
+// one shorter); grp0 gives each system's first group (n_sys+1 entries).
+constexpr int kSegGroup = 32;
 struct Tiles {
   const int *sys, *row0, *row1, *sys_tile0;
+  const int *grp0;
+  int n_tiles, n_sys;
 };
 
-// Sums K values per system: per-tile block sums go to partials[K*t + k]; the
-// last tile of system `sys` to arrive adds its system's partials in tile
-// order and returns true in all its threads with out[] valid in thread 0.
+// Sums K values per system in two levels, so that no counter sees more than
+// about kSegGroup or n_tiles / kSegGroup arrivals (a system of 8 000 tiles
+// otherwise queues 8 000 atomics on one address): per-tile block sums go to
+// partials[K*t + k]; the last tile of a group to arrive adds the group's
+// tile partials in tile order into partials[K*(n_tiles + g) + k]; the last
+// group of system `sys` to finish adds its group partials in group order and
+// returns true in all its threads with out[] valid in thread 0.  The grouping
+// depends on the system alone, so the sums do too.  Counters: counter[sys]
+// per system, counter[n_sys + 1 + g] per group.
 template <int NT, int K>
 __device__ __forceinline__ bool seg_sum(const double (&v)[K], double *partials, unsigned *counter, const Tiles &tl,
                                         int t, int sys, double (&out)[K]) {
@@ -72,20 +83,46 @@ __device__ __forceinline__ bool seg_sum(const double (&v)[K], double *partials, 
 #pragma unroll
   for (int k = 0; k < K; ++k) bs[k] = block_sum<NT>(v[k], sh);
   const int t0 = tl.sys_tile0[sys], t1 = tl.sys_tile0[sys + 1];
+  const int gl = (t - t0) / kSegGroup;                 // group within the system
+  const int ga = t0 + gl * kSegGroup;                  // its tiles [ga, gb)
+  const int gb = min(ga + kSegGroup, t1);
+  const int g = tl.grp0[sys] + gl;                     // its storage index
+  const int ng = tl.grp0[sys + 1] - tl.grp0[sys];
+  unsigned *gctr = counter + tl.n_sys + 1;
+  double *gpart = partials + (size_t)K * tl.n_tiles;
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) partials[(size_t)K * t + k] = bs[k];
     __threadfence();
-    const unsigned ticket = atomicAdd(&counter[sys], 1u);
-    last = (ticket == (unsigned)(t1 - t0 - 1));
+    const unsigned ticket = atomicAdd(&gctr[g], 1u);
+    last = (ticket == (unsigned)(gb - ga - 1));
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  double gs[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     double acc = 0.0;
-    for (int b = t0 + threadIdx.x; b < t1; b += NT) acc += __ldcg(&partials[(size_t)K * b + k]);
+    for (int b = ga + threadIdx.x; b < gb; b += NT) acc += __ldcg(&partials[(size_t)K * b + k]);
+    gs[k] = block_sum<NT>(acc, sh);
+  }
+  if (threadIdx.x == 0) {
+    gctr[g] = 0u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) gpart[(size_t)K * g + k] = gs[k];
+    __threadfence();
+    const unsigned ticket = atomicAdd(&counter[sys], 1u);
+    last = (ticket == (unsigned)(ng - 1));
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  const int g0 = tl.grp0[sys];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < ng; b += NT) acc += __ldcg(&gpart[(size_t)K * (g0 + b) + k]);
     out[k] = block_sum<NT>(acc, sh);
   }
   if (threadIdx.x == 0) counter[sys] = 0u;

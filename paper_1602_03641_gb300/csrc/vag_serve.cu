@@ -54,6 +54,7 @@ size_t estimate_bytes(const Req &r) {
   const double nc = r.nc(), nv = r.nv(), nf = r.nf();
   double b = 1400.0 * nc + 900.0 * nv + 1200.0 * nf;
   if (r.precond == VAG_PC_AMG) b *= 1.6;
+  if (r.precond == VAG_PC_AMG_RS) b *= 2.2;   // denser coarse levels and P, R
   if (r.precond == VAG_PC_CHEBYSHEV) b *= 1.05;   // four more row vectors
   if (r.precision != VAG_FP64) b *= 1.25;
   return (size_t)(b * 1.2) + (1u << 20);

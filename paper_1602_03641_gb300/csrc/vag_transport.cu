@@ -15,18 +15,7 @@
 //                is built once per (fluxes, dt) as a CSR of the inflow edges;
 //                Dirichlet rows keep c = cbar (d = 1, no inflow).
 //  k_cfl         Eq. (eq_CFL): min over non-Dirichlet CVs of phi / outflow.
-//  k_tile_sort / k_sell_fill
-//                the map as the step reads it: in every tile of 256 control
-//                volumes the rows are ordered by inflow count (largest first,
-//                ties by index), and each 32-row slice stores its entries
-//                column-major (entry k of the slice's rows contiguous).  A
-//                warp then runs rows of nearly equal length (on GB300 an FP64
-//                warp instruction costs its full issue slot whatever its
-//                active lanes) and reads each entry row k as one contiguous
-//                segment.  Row lengths are kept, so no padding is read.
-//  k_step        c' = d c + W c (one thread per control volume, one warp per
-//                slice); each row performs the same FMAs in the same order as
-//                a CSR row loop over its inflow edges.
+//  k_step        c' = d c + W c (one thread per control volume).
 #include "vag_internal.cuh"
 #include "vag_reduce.cuh"
 #include "vag_hex.cuh"
@@ -281,68 +270,22 @@ __global__ void k_cv_sys(int nv, int nf, int nc, int n_sys, const int *__restric
   cv_sys[mu] = lo;
 }
 
-// Per tile of 256 control volumes: the rows ordered by inflow count (largest
-// first, ties by index; rows past n last), their diagonal in that order, and
-// each 32-row slice's width (its first row's count) x 32.  Counts above 255
-// set ST_ROW_OVERFLOW.
-static_assert(TB == 256, "transport tiles are one block of 256 rows");
-__global__ void __launch_bounds__(TB) k_tile_sort(int n, const int *__restrict__ rowptr,
-                                                  const double *__restrict__ diag, uint8_t *__restrict__ perm,
-                                                  uint8_t *__restrict__ len, double *__restrict__ diag_s,
-                                                  int *__restrict__ slice_elems, int *status) {
-  __shared__ int cnt[TB];
-  const int t = blockIdx.x, j = threadIdx.x, mu = t * TB + j;
-  const int c = mu < n ? rowptr[mu + 1] - rowptr[mu] : -1;
-  cnt[j] = c;
-  __syncthreads();
-  int rank = 0;
-  for (int i = 0; i < TB; ++i) {
-    const int ci = cnt[i];
-    rank += (ci > c) || (ci == c && i < j);
-  }
-  if (c > 255) atomicOr(status, ST_ROW_OVERFLOW);
-  const int cc = c < 0 ? 0 : (c > 255 ? 255 : c);
-  perm[t * TB + rank] = (uint8_t)j;
-  len[t * TB + rank] = (uint8_t)cc;
-  diag_s[t * TB + rank] = mu < n ? diag[mu] : 0.0;
-  if ((rank & 31) == 0) slice_elems[t * (TB / 32) + (rank >> 5)] = 32 * cc;
-}
-
-// Entries of the sorted rows into their slices (column-major).
-__global__ void __launch_bounds__(TB) k_sell_fill(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                                                  const double *__restrict__ w, const uint8_t *__restrict__ perm,
-                                                  const uint8_t *__restrict__ len, const int *__restrict__ slice_ptr,
-                                                  int *__restrict__ scol, double *__restrict__ sval) {
-  const int t = blockIdx.x, p = t * TB + threadIdx.x;
-  const int mu = t * TB + perm[p];
-  if (mu >= n) return;
-  const int L = len[p], b = rowptr[mu];
-  const int off = slice_ptr[p >> 5] + (p & 31);
-  for (int k = 0; k < L; ++k) {
-    scol[off + 32 * k] = col[b + k];
-    sval[off + 32 * k] = w[b + k];
-  }
-}
-
 // Launched with programmatic dependent launch: the map (written once per
 // solve) is read before the dependency wait, the previous step's c after it.
 constexpr int kStepPF = 4;
-__global__ void __launch_bounds__(TB) k_step(int n, const uint8_t *__restrict__ perm, const uint8_t *__restrict__ len,
-                                             const double *__restrict__ diag_s, const int *__restrict__ slice_ptr,
-                                             const int *__restrict__ scol, const double *__restrict__ sval,
+__global__ void __launch_bounds__(TB) k_step(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                             const double *__restrict__ w, const double *__restrict__ diag,
                                              const double *__restrict__ c, double *__restrict__ cn) {
-  const int p = blockIdx.x * TB + threadIdx.x;
-  const int mu = blockIdx.x * TB + perm[p];
+  const int mu = blockIdx.x * TB + threadIdx.x;
   const bool valid = mu < n;
-  const int L = len[p];
-  const double d = diag_s[p];
-  const int off = slice_ptr[p >> 5] + (p & 31);
+  const int b = valid ? rowptr[mu] : 0, e = valid ? rowptr[mu + 1] : 0;
+  const double d = valid ? diag[mu] : 0.0;
   int pc[kStepPF];
   double pw[kStepPF];
 #pragma unroll
   for (int u = 0; u < kStepPF; ++u) {
-    pc[u] = u < L ? scol[off + 32 * u] : 0;
-    pw[u] = u < L ? sval[off + 32 * u] : 0.0;
+    pc[u] = b + u < e ? col[b + u] : 0;
+    pw[u] = b + u < e ? w[b + u] : 0.0;
   }
   pdl_wait();
   pdl_trigger();
@@ -350,8 +293,8 @@ __global__ void __launch_bounds__(TB) k_step(int n, const uint8_t *__restrict__ 
   double v = d * c[mu];
 #pragma unroll
   for (int u = 0; u < kStepPF; ++u)
-    if (u < L) v = fma(pw[u], c[pc[u]], v);
-  for (int k = kStepPF; k < L; ++k) v = fma(sval[off + 32 * k], c[scol[off + 32 * k]], v);
+    if (b + u < e) v = fma(pw[u], c[pc[u]], v);
+  for (int k = b + kStepPF; k < e; ++k) v = fma(w[k], c[col[k]], v);
   cn[mu] = v;
 }
 
@@ -362,52 +305,16 @@ __global__ void k_set_dir(int nd, const int *__restrict__ dn, const double *__re
 
 }  // namespace
 
-// One explicit step c -> cn on the sorted sliced-ELL map.
-static void launch_step(System *s, const double *c, double *cn, cudaStream_t st) {
-  launch_pdl(k_step, s->n_tiles_t, TB, 0, st, s->n_cv, (const uint8_t *)s->tperm, (const uint8_t *)s->tlen,
-             (const double *)s->tdiag_s, (const int *)s->tslice_ptr, (const int *)s->tscol, (const double *)s->tsval,
-             c, cn);
-}
-
-// The CSR map (trowptr, tcol, tval, tdiag) in the step's layout.
-static void build_step_map(System *s, cudaStream_t st) {
-  const int n = s->n_cv;
-  const int nt = (n + TB - 1) / TB;
-  if (s->n_tiles_t != nt) {
-    s->n_tiles_t = nt;
-    s->tperm = sys_alloc<uint8_t>(s, (size_t)nt * TB);
-    s->tlen = sys_alloc<uint8_t>(s, (size_t)nt * TB);
-    s->tdiag_s = sys_alloc<double>(s, (size_t)nt * TB);
-    s->tslice_ptr = sys_alloc<int>(s, (size_t)nt * (TB / 32) + 1);
-  }
-  int *elems;
-  VAG_CUDA(cudaMallocAsync(&elems, sizeof(int) * ((size_t)nt * (TB / 32) + 1), st));
-  VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
-  k_tile_sort<<<nt, TB, 0, st>>>(n, s->trowptr, s->tdiag, s->tperm, s->tlen, s->tdiag_s, elems, s->status);
-  note_launches(1);
-  VAG_CHECK_LAUNCH();
-  const int64_t total = scan_exclusive(elems, s->tslice_ptr, nt * (TB / 32), st);
-  VAG_CUDA(cudaFreeAsync(elems, st));
-  if (read_status(s) & ST_ROW_OVERFLOW) fail(VAG_EMESH, "a control volume has more than 255 inflow edges");
-  if (total > s->ts_cap) {
-    s->tscol = sys_alloc<int>(s, (size_t)total);
-    s->tsval = sys_alloc<double>(s, (size_t)total);
-    s->ts_cap = total;
-  }
-  k_sell_fill<<<nt, TB, 0, st>>>(n, s->trowptr, s->tcol, s->tval, s->tperm, s->tlen, s->tslice_ptr, s->tscol,
-                                 s->tsval);
-  note_launches(1);
-  VAG_CHECK_LAUNCH();
-}
-
 // Mean duration of one explicit step on the current upwind map.
 double time_transport_step(System *s, int reps) {
-  if (!s->tsval || !s->cbuf || !s->tdiag_s) fail(VAG_EINVAL, "no upwind map: run vag_transport first");
+  if (!s->trowptr || !s->cbuf || !s->tdiag) fail(VAG_EINVAL, "no upwind map: run vag_transport first");
   cudaStream_t st = s->ctx->stream;
   const int n = s->n_cv;
+  const int gs = grid_for(n, TB);
   double *a = s->cbuf, *b = s->cbuf + n;
   auto step = [&](const double *c, double *cn) {
-    launch_step(s, c, cn, st);
+    launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
+               (const double *)s->tdiag, c, cn);
     note_launches(1);
   };
   step(a, b);   // warm-up
@@ -489,8 +396,6 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
   k_map_fill<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->seg.cv_sys, s->trowptr, s->dts, s->tdiag, s->tcol,
                                              s->tval);
   note_launches(1);
-  const int64_t ts_cap_before = s->ts_cap;
-  build_step_map(s, st);
   // c^0 with the Dirichlet values
   double *c0 = s->cbuf, *c1 = s->cbuf + n;
   VAG_CUDA(cudaMemcpyAsync(c0, c_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -499,13 +404,13 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
   VAG_CHECK_LAUNCH();
   trace_mark(st, "porous volumes + CFL + upwind map");
   VAG_CUDA(cudaEventRecord(s->ev0, st));
+  const int gs = grid_for(n, TB);
   // steps in CUDA graphs of kStepChunk launches (an even count: the chunk
-  // starts and ends in the same buffer), the remainder launched directly;
-  // the graph holds the map's pointers, so it is rebuilt when they change
+  // starts and ends in the same buffer), the remainder launched directly
   constexpr int kStepChunk = 20;
   const int chunks = o->n_steps / kStepChunk;
   if (chunks > 0) {
-    if (!s->step_graph || s->step_graph_cap != s->ts_cap || s->ts_cap != ts_cap_before) {
+    if (!s->step_graph || s->step_graph_cap != s->t_cap) {
       if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
       s->step_graph = nullptr;
       cudaGraph_t graph;
@@ -513,14 +418,15 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
       set_capturing(true);
       double *a = s->cbuf, *b = s->cbuf + n;
       for (int k = 0; k < kStepChunk; ++k) {
-        launch_step(s, a, b, st);
+        launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
+                   (const double *)s->tdiag, (const double *)a, b);
         std::swap(a, b);
       }
       set_capturing(false);
       VAG_CUDA(cudaStreamEndCapture(st, &graph));
       VAG_CUDA(cudaGraphInstantiate(&s->step_graph, graph, 0));
       cudaGraphDestroy(graph);
-      s->step_graph_cap = s->ts_cap;
+      s->step_graph_cap = s->t_cap;
     }
     for (int c = 0; c < chunks; ++c) {
       VAG_CUDA(cudaGraphLaunch(s->step_graph, st));
@@ -528,7 +434,8 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     }
   }
   for (int k = chunks * kStepChunk; k < o->n_steps; ++k) {
-    launch_step(s, c0, c1, st);
+    launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
+               (const double *)s->tdiag, (const double *)c0, c1);
     note_launches(1);
     std::swap(c0, c1);
   }

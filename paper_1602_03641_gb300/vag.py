@@ -22,7 +22,7 @@ VAG_OK, VAG_EINVAL, VAG_ENOMEM, VAG_EBUDGET, VAG_ENOTCONVERGED = 0, 1, 2, 3, 4
 VAG_EBREAKDOWN, VAG_ETIMEOUT, VAG_ECUDA, VAG_EMESH = 5, 6, 7, 8
 VAG_MEM_HOST, VAG_MEM_DEVICE = 0, 1
 VAG_FP64, VAG_MIXED, VAG_MIXED_F16, VAG_FP64_PC32 = 0, 1, 2, 3
-VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG = 0, 1, 2
+VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG, VAG_PC_AMG_RS = 0, 1, 2, 3
 VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB, VAG_KRYLOV_GMRES = 0, 1, 2
 VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP, VAG_KERNEL_SPMV32 = 0, 1, 2, 3
 
