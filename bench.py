@@ -185,11 +185,35 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def _code_block(text, start):
+    """The text from the first line containing ``start`` to the end of the
+    first brace block that opens after it (a kernel and what precedes it)."""
+    i = text.find(start)
+    if i < 0:
+        return None
+    j = text.find("{", i)
+    depth = 0
+    for k in range(j, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[k], 0)
+        if depth == 0:
+            return text[i:k + 1]
+    return None
+
+
 def source_hash(files):
+    """Hash of the sources a capture depends on: whole files, or
+    ``file::start`` for one kernel's text (see _code_block)."""
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        path, _, start = f.partition("::")
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            data = fh.read()
+        if start:
+            block = _code_block(data.decode(), start)
+            if block is None:
+                return None
+            data = block.encode()
+        h.update(data)
     return h.hexdigest()[:16]
 
 

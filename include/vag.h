@@ -105,15 +105,18 @@ typedef struct vag_system vag_system;
  *   cell_face_ptr [n_cells+1], cell_face_idx: the faces of cell K,
  *              cell_face_idx[cell_face_ptr[K] .. cell_face_ptr[K+1]);
  *   ff_face_ids [n_ff]: the fracture faces F_Gamma as face ids.
- *   The library recognises hexahedral cells (six faces of four nodes forming
- *   a cube graph) whatever the order of their faces and face nodes, numbers
- *   them canonically (node 0 = the smallest node id, 1, 2, 4 = its edge
- *   neighbours in increasing id) and assembles them on the fast path; on a
- *   lattice whose node ids grow with x, then y, then z this is the lattice
- *   numbering, so both forms give bitwise the same system.  A cell that is
- *   not a hexahedron, or a fracture face that is not a quadrilateral, is a
- *   VAG_EMESH error (this build's kernels take hexahedra); an offset or id
- *   out of range is VAG_EINVAL.
+ *   The library recognises four cell shapes from their faces, whatever the
+ *   order of the faces and the starting node of each face: hexahedra (six
+ *   quadrilaterals forming a cube graph), tetrahedra (four triangles),
+ *   triangular prisms (two triangles, three quadrilaterals) and pyramids
+ *   (one quadrilateral, four triangles), in any mix.  Each cell is numbered
+ *   canonically from its node ids (a hexahedron: node 0 = the smallest id,
+ *   1, 2, 4 = its edge neighbours in increasing id), so on a lattice whose
+ *   node ids grow with x, then y, then z a hexahedral mesh gets the lattice
+ *   numbering and both forms give bitwise the same system; a mesh of
+ *   hexahedra alone runs on the hexahedral kernels.  Fracture faces are
+ *   triangles or quadrilaterals.  Any other cell or face is a VAG_EMESH
+ *   error; an offset or id out of range is VAG_EINVAL.
  *
  * Cell centres x_K and face centres x_sigma are the isobarycentres of their
  * nodes (beta_{sigma,s} = 1/|V_sigma|).
@@ -140,18 +143,51 @@ typedef struct {
  *   lambda_f [n_ff]      isotropic tangential fracture permeability;
  *   d_f      [n_ff]      fracture aperture (width);
  *   mu                   viscosity (> 0).
+ * Wells (Sec. 5.5, optional; n_perf = 0 for none): perforation p connects
+ * fracture face well_ff[p] to a well through the Peaceman model, the
+ * volume rate leaving the face into the well being
+ *   q_p = well_wi[p] (u_sigma - well_pw[p]) - well_q[p],
+ * so a producer has WI > 0 and its well pressure p_w, and an injector with
+ * an imposed rate has WI = 0 and q > 0 (both terms may be combined).  The
+ * pressure equation of the face gains q_p; in the transport a positive q_p
+ * leaves the face with its concentration and a negative one enters it with
+ * concentration well_cin[p].  Perforated faces are distinct fracture faces
+ * of this mesh (0-based); every array has n_perf entries; WI >= 0.
+ * vag_peaceman_wi gives the well index of a perforated fracture face.
  */
 typedef struct {
   const double *lambda_m;
   const double *lambda_f;
   const double *d_f;
   double mu;
+  int32_t n_perf;
+  const int32_t *well_ff;
+  const double *well_wi;
+  const double *well_pw;
+  const double *well_q;
+  const double *well_cin;
 } vag_props;
+
+/*
+ * Peaceman well index of a vertical well through a fracture face (Sec. 5.5):
+ * the face expanded as a box dx x d_f x dz, the well's analytic radial
+ * pressure imposed at the box corners and its rate at the box centre give
+ *   WI = 2 pi dz Lambda_f / (mu log(r_0 / r_w)),  r_0 = D exp(-2 pi dz / C),
+ *   C = 4/3 (dx dz / d_f + dx d_f / dz + dz d_f / dx),
+ *   D = sqrt(dx^2 + d_f^2) / 2,
+ * C being the cell diagonal of the VAG scheme on that box with unit
+ * permeability.  Host arrays of n entries; every input > 0 and r_0 > r_w,
+ * else VAG_EINVAL (wi_out untouched).  mu = 1 reproduces the paper's
+ * expression, which has no viscosity.
+ */
+vag_status vag_peaceman_wi(int32_t n, const double *dx, const double *dz, const double *d_f,
+                           const double *lambda_f, const double *r_w, double mu, double *wi_out);
 
 /*
  * Dirichlet nodes V_D with pressure u_s = values[i] (Sec. 3.1; the paper's
  * V_ext).  Every other boundary node is a no-flow node.  Nodes must be
- * distinct and at least one node must be given.
+ * distinct.  At least one node must be given unless a well perforation with
+ * WI > 0 fixes the pressure level (VAG_EINVAL otherwise).
  */
 typedef struct {
   int32_t n_dir;
@@ -219,7 +255,9 @@ vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshe
 vag_status vag_system_get_batch(const vag_system *sys, int32_t *n_sys, int32_t *node_start, int32_t *ff_start,
                                 int32_t *cell_start, int32_t *row_start);
 
-/* Re-run the numeric phase with new properties on the same mesh. */
+/* Re-run the numeric phase with new properties (and wells) on the same mesh.
+ * On a batch, props' arrays (and the wells' fracture-face ids) cover the
+ * union. */
 vag_status vag_update_props(vag_system *sys, const vag_props *props, int mem);
 void vag_system_destroy(vag_system *sys);
 
@@ -335,12 +373,36 @@ vag_status vag_transport_get_dts(const vag_system *sys, double *dt_max, double *
 vag_status vag_export_system(const vag_system *sys, int32_t *rowptr, int32_t *col, double *val,
                              double *rhs, int32_t *row_dof, int mem);
 /* Fluxes of Eq. (VAGFluxMatrix) / Eq. (VAGFluxFracture) in the library's
- * layout: F_cell_nodes [8*n_cells] (F_{K,s}, s in cell_nodes order),
- * F_cell_faces [6*n_cells] (F_{K,sigma} on the cell's six faces in the face
- * order of vag_mesh, 0 where the face is not a fracture face), F_frac
- * [4*n_ff] (F_{sigma,s}, s in ff_nodes order). */
+ * layout: F_cell_nodes [8*n_cells] (F_{K,s}, s in the cell's node-slot
+ * order, see vag_export_cells; 0 in unused slots), F_cell_faces
+ * [6*n_cells] (F_{K,sigma} on the cell's faces in the local face order of
+ * its shape, the hexahedral fast path's being that of vag_mesh; 0 where
+ * the face is not a fracture face or does not exist), F_frac [4*n_ff]
+ * (F_{sigma,s}, s in the order of vag_export_cells' ff_nodes; 0 in a
+ * triangle's fourth slot). */
+/* The numbering the kernels run on: cell_nodes [8*n_cells] (the node slots
+ * of each cell in its shape's local order, -1 in unused slots), shape
+ * [n_cells] (VAG_SHAPE_*), ff_nodes [4*n_ff] (each fracture face's nodes in
+ * cyclic order, -1 in a triangle's fourth slot).  For the hexahedral fast
+ * path these are the caller's arrays; for the general descriptor the
+ * canonical numbering described at vag_mesh.  Any pointer may be NULL. */
+/* Local numbering of the shapes (faces in local face order, each cyclic):
+ *   VAG_SHAPE_HEX     node l at offset (l&1, (l>>1)&1, (l>>2)&1); faces
+ *                     {0,2,6,4} {1,3,7,5} {0,1,5,4} {2,3,7,6} {0,1,3,2} {4,5,7,6}
+ *   VAG_SHAPE_TET     faces {1,2,3} {0,3,2} {0,1,3} {0,2,1} (face l opposite node l)
+ *   VAG_SHAPE_PRISM   0 1 2 bottom, 3+i above i; faces {0,1,2} {3,4,5} {0,1,4,3}
+ *                     {1,2,5,4} {2,0,3,5}
+ *   VAG_SHAPE_PYRAMID 0 1 2 3 base, 4 apex; faces {0,1,2,3} {0,1,4} {1,2,4}
+ *                     {2,3,4} {3,0,4} */
+enum { VAG_SHAPE_HEX = 0, VAG_SHAPE_TET = 1, VAG_SHAPE_PRISM = 2, VAG_SHAPE_PYRAMID = 3 };
+vag_status vag_export_cells(const vag_system *sys, int32_t *cell_nodes, int8_t *shape, int32_t *ff_nodes, int mem);
 vag_status vag_export_fluxes(const vag_system *sys, double *F_cell_nodes, double *F_cell_faces,
                              double *F_frac, int mem);
+/* Rates q_p of the well perforations (n_perf entries, in the order given in
+ * vag_props) from the last vag_solve: positive = leaving the fracture face
+ * into the well (production).  Zero before the first solve. */
+vag_status vag_export_well_rates(const vag_system *sys, double *q_out, int mem);
+
 /* Replace the fluxes (same layout) used by the next vag_transport. */
 vag_status vag_set_fluxes(vag_system *sys, const double *F_cell_nodes, const double *F_cell_faces,
                           const double *F_frac, int mem);

@@ -97,7 +97,14 @@ def sym6_to_3x3(l6):
 
 class Mesh:
     """Cells -> faces -> nodes with the sets the paper names: V_K, F_Gamma,K,
-    V_sigma, x_K, x_sigma (beta = 1/|V_sigma|)."""
+    V_sigma, x_K, x_sigma (beta = 1/|V_sigma|).
+
+    ``pb.faces`` [n_faces, q_max] lists each face's nodes in cyclic order,
+    padded at the end with -1 where a face has fewer than q_max nodes;
+    ``pb.cell_faces`` [n_cells, f_max] is padded the same way.  Cells are
+    grouped by the node counts of their faces (in ``cell_faces`` order), so
+    every group has one |V_K| and one face layout; ``groups`` lists
+    (cells, V_K [B, |V_K|] sorted, face ids [B, n_F], face sizes)."""
 
     def __init__(self, pb):
         self.xyz = pb.xyz
@@ -108,22 +115,45 @@ class Mesh:
         self.nF = pb.faces.shape[0]
         self.ff = pb.ff_faces
         self.nf = self.ff.shape[0]
+        fvalid = self.faces >= 0
+        self.fq = fvalid.sum(axis=1)                          # |V_sigma| of every face
+        if np.any(fvalid[:, 1:] & ~fvalid[:, :-1]):
+            raise ValueError("face padding must come after the nodes")
         # face id -> fracture-face index (or -1)
         self.face_ff = -np.ones(self.nF, np.int64)
         self.face_ff[self.ff] = np.arange(self.nf)
-        # V_K: union of the nodes of the faces of K (sorted)
-        allnodes = np.sort(self.faces[self.cell_faces].reshape(self.nc, -1), axis=1)
-        keep = np.ones(allnodes.shape, bool)
-        keep[:, 1:] = allnodes[:, 1:] != allnodes[:, :-1]
-        cnt = keep.sum(axis=1)
-        if not np.all(cnt == cnt[0]):
-            raise NotImplementedError("oracle handles one cell type per mesh")
-        self.VK = allnodes[keep].reshape(self.nc, cnt[0])
-        self.xK = self.xyz[self.VK].mean(axis=1)
-        self.xS = self.xyz[self.faces].mean(axis=1)          # every face centre
+        if np.all(fvalid):
+            self.xS = self.xyz[self.faces].mean(axis=1)       # every face centre
+        else:
+            f0 = np.where(fvalid, self.faces, 0)
+            self.xS = (self.xyz[f0] * fvalid[..., None]).sum(axis=1) / self.fq[:, None]
+        # cells grouped by the sizes of their faces
+        cf = self.cell_faces
+        sizes = np.where(cf >= 0, self.fq[np.where(cf >= 0, cf, 0)], 0)
+        sig, gid = np.unique(sizes, axis=0, return_inverse=True)
+        self.group_of = gid.reshape(-1)
+        self.groups = []
+        self.xK = np.zeros((self.nc, 3))
+        for g in range(sig.shape[0]):
+            cells = np.nonzero(self.group_of == g)[0]
+            cols = np.nonzero(sig[g] > 0)[0]
+            fids = cf[cells][:, cols]
+            fsz = sig[g][cols]
+            allnodes = np.sort(np.concatenate([self.faces[fids[:, j]][:, :fsz[j]] for j in range(cols.size)],
+                                              axis=1), axis=1)
+            keep = np.ones(allnodes.shape, bool)
+            keep[:, 1:] = allnodes[:, 1:] != allnodes[:, :-1]
+            cnt = keep.sum(axis=1)
+            if not np.all(cnt == cnt[0]):
+                raise ValueError("cells with the same face sizes but different node counts")
+            VK = allnodes[keep].reshape(cells.size, cnt[0])
+            self.xK[cells] = self.xyz[VK].mean(axis=1)
+            self.groups.append((cells, VK, fids, fsz))
+        self.VK = self.groups[0][1] if len(self.groups) == 1 else None
         self.VG = np.zeros(self.nv, bool)                   # V_Gamma
         if self.nf:
-            self.VG[np.unique(self.faces[self.ff])] = True
+            fn = self.faces[self.ff]
+            self.VG[np.unique(fn[fn >= 0])] = True
 
 
 # ----------------------------------------------------------------------------
@@ -143,15 +173,20 @@ def cell_local_matrices(pb, mesh=None, cells=None):
     if cells is None:
         cells = np.arange(m.nc)
     cells = np.asarray(cells)
+    g = np.unique(m.group_of[cells])
+    if g.size != 1:
+        raise ValueError("cells of one face layout per call (Mesh.groups)")
+    gcells, gVK, gfids, fsz = m.groups[int(g[0])]
+    row = np.searchsorted(gcells, cells)
     nv, nf = m.nv, m.nf
-    nVK = m.VK.shape[1]
-    nFK = m.cell_faces.shape[1]
+    nVK = gVK.shape[1]
+    nFK = fsz.size
     L = 1 + nVK + nFK
     B = cells.shape[0]
     dofs = -np.ones((B, L), np.int64)
     dofs[:, 0] = nv + nf + cells
-    dofs[:, 1:1 + nVK] = m.VK[cells]
-    cf = m.cell_faces[cells]                      # [B, nFK]
+    dofs[:, 1:1 + nVK] = gVK[row]
+    cf = gfids[row]                               # [B, nFK]
     cff = m.face_ff[cf]                           # fracture index or -1
     slot_of_face = np.full(cf.shape, -1)
     isff = cff >= 0
@@ -163,12 +198,12 @@ def cell_local_matrices(pb, mesh=None, cells=None):
     vol = np.zeros(B)
     lam = sym6_to_3x3(pb.lambda_m[cells]) / pb.mu
     xK = m.xK[cells]
-    VKc = m.VK[cells]
+    VKc = gVK[row]
     bidx = np.arange(B)
     for f in range(nFK):
         fid = cf[:, f]
-        fnodes = m.faces[fid]                     # [B, q] cyclic
-        q = fnodes.shape[1]
+        q = int(fsz[f])
+        fnodes = m.faces[fid][:, :q]              # [B, q] cyclic
         xs = m.xS[fid]
         for e in range(q):
             a = fnodes[:, e]
@@ -196,38 +231,44 @@ def fracture_local_matrices(pb, mesh=None):
     """Per-fracture-face matrix over (sigma, V_sigma):
     M[i, j] = int_sigma d_f Lambda_f / mu grad_tau(eta_i) . grad_tau(eta_j)
     (Eq. VAGFluxFracture) on the triangles (x_sigma, e).
-    Returns dict(dofs [nf, 1+q], M [nf, 1+q, 1+q], area [nf])."""
+    Returns dict(dofs [nf, 1+Q], M [nf, 1+Q, 1+Q], area [nf]) with Q the
+    largest |V_sigma|; a face with fewer nodes has dof -1 and zero rows and
+    columns in its unused slots."""
     m = mesh or Mesh(pb)
     nv, nf = m.nv, m.nf
-    fn = m.faces[m.ff]                            # [nf, q]
-    q = fn.shape[1]
+    fn = m.faces[m.ff]                            # [nf, Q] cyclic, -1 padded
+    Q = fn.shape[1]
+    qf = m.fq[m.ff]
     xs = m.xS[m.ff]
     coef = pb.d_f * pb.lambda_f / pb.mu
-    M = np.zeros((nf, 1 + q, 1 + q))
+    M = np.zeros((nf, 1 + Q, 1 + Q))
     area = np.zeros(nf)
-    for e in range(q):
-        a = fn[:, e]; b = fn[:, (e + 1) % q]
-        v = np.stack([xs, m.xyz[a], m.xyz[b]], axis=1)
-        S, ar = tri_p1_stiffness(v, coef)
-        area += ar
-        idx = [0, 1 + e, 1 + (e + 1) % q]
-        for i in range(3):
-            for j in range(3):
-                M[:, idx[i], idx[j]] += S[:, i, j]
+    for q in np.unique(qf):
+        sel = np.nonzero(qf == q)[0]
+        for e in range(q):
+            a = fn[sel, e]; b = fn[sel, (e + 1) % q]
+            v = np.stack([xs[sel], m.xyz[a], m.xyz[b]], axis=1)
+            S, ar = tri_p1_stiffness(v, coef[sel])
+            area[sel] += ar
+            idx = [0, 1 + e, 1 + (e + 1) % q]
+            for i in range(3):
+                for j in range(3):
+                    M[sel, idx[i], idx[j]] += S[:, i, j]
     dofs = np.concatenate([(nv + np.arange(nf))[:, None], fn], axis=1)
     return dict(dofs=dofs, M=M, area=area)
+
+
+def _all_cell_matrices(pb, mesh):
+    out = []
+    for cells, _, _, _ in mesh.groups:
+        for s in range(0, cells.size, CHUNK):
+            out.append(cell_local_matrices(pb, mesh, cells[s:s + CHUNK]))
+    return out
 
 
 # ----------------------------------------------------------------------------
 # global system, elimination, solve (Sec. 3.1 and Sec. 4.2)
 # ----------------------------------------------------------------------------
-
-def _all_cell_matrices(pb, mesh):
-    out = []
-    for s in range(0, mesh.nc, CHUNK):
-        out.append(cell_local_matrices(pb, mesh, np.arange(s, min(s + CHUNK, mesh.nc))))
-    return out
-
 
 def assemble_full(pb, mesh=None, cellmats=None, fracmats=None):
     """Full Galerkin matrix over X_D, ordered [nodes | ffaces | cells]."""
@@ -246,13 +287,52 @@ def assemble_full(pb, mesh=None, cellmats=None, fracmats=None):
     if m.nf:
         d = fracmats["dofs"]; M = fracmats["M"]
         L = d.shape[1]
-        rows.append(np.repeat(d[:, :, None], L, axis=2).ravel())
-        cols.append(np.repeat(d[:, None, :], L, axis=1).ravel())
-        vals.append(M.ravel())
+        R = np.repeat(d[:, :, None], L, axis=2)
+        C = np.repeat(d[:, None, :], L, axis=1)
+        ok = (R >= 0) & (C >= 0)
+        rows.append(R[ok]); cols.append(C[ok]); vals.append(M[ok])
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(n, n)).tocsr()
     A.sum_duplicates()
     return A
+
+
+def peaceman_wi(dx, dz, d_f, lam_f, r_w, mu=1.0):
+    """Sec. 5.5: well index of a vertical well of radius r_w through a
+    fracture face seen as a box dx x d_f x dz (dx the face's horizontal
+    edge, dz its height): WI = 2 pi dz Lambda_f / (mu log(r_0 / r_w)) with
+    r_0 = D exp(-2 pi dz / C), C = 4/3 (dx dz/d_f + dx d_f/dz + dz d_f/dx),
+    D = sqrt(dx^2 + d_f^2) / 2.  (C is the cell diagonal of the VAG scheme
+    on that box with unit permeability; the paper's expression has mu = 1.)"""
+    dx, dz, d_f, lam_f, r_w = (np.asarray(a, np.float64) for a in (dx, dz, d_f, lam_f, r_w))
+    C = 4.0 / 3.0 * (dx * dz / d_f + dx * d_f / dz + dz * d_f / dx)
+    D = 0.5 * np.sqrt(dx ** 2 + d_f ** 2)
+    r0 = D * np.exp(-2.0 * np.pi * dz / C)
+    return 2.0 * np.pi * dz * lam_f / (mu * np.log(r0 / r_w))
+
+
+def well_terms(pb):
+    """Peaceman wells of ``pb.wells`` (per perforation: fracture face ff,
+    WI, p_w, imposed rate q, injected concentration c_in).  The rate leaving
+    face sigma into the well, q_p = WI (u_sigma - p_w) - q, enters the face's
+    conservation equation: WI goes to its diagonal and WI p_w + q to its
+    right-hand side.  Returns (d, g) over the full DOFs, or (None, None)."""
+    w = getattr(pb, "wells", None)
+    if not w:
+        return None, None
+    n = pb.n_nodes + pb.n_ff + pb.n_cells
+    dof = pb.n_nodes + np.asarray(w["ff"], np.int64)
+    d = np.zeros(n); g = np.zeros(n)
+    np.add.at(d, dof, w["wi"])
+    np.add.at(g, dof, np.asarray(w["wi"]) * np.asarray(w["pw"]) + np.asarray(w["q"]))
+    return d, g
+
+
+def well_rates(pb, u):
+    """q_p = WI (u_sigma - p_w) - q for every perforation."""
+    w = pb.wells
+    return np.asarray(w["wi"]) * (u[pb.n_nodes + np.asarray(w["ff"], np.int64)] - np.asarray(w["pw"])) \
+        - np.asarray(w["q"])
 
 
 def split_dofs(pb):
@@ -265,10 +345,11 @@ def split_dofs(pb):
     return R, C, D
 
 
-def schur_system(pb, A=None, mesh=None):
+def schur_system(pb, A=None, mesh=None, g=None):
     """Eq. (eqschur): eliminate the cell unknowns (A_cc is diagonal).
     Rows/columns: the non-Dirichlet nodes in increasing id, then the fracture
-    faces.  Returns (S csr, b, R)."""
+    faces; g: an optional source over the full DOFs (the wells).  Returns
+    (S csr, b, R)."""
     A = A if A is not None else assemble_full(pb, mesh)
     R, C, D = split_dofs(pb)
     uD = pb.dir_values
@@ -276,15 +357,19 @@ def schur_system(pb, A=None, mesh=None):
     A_CC = A[C][:, C].diagonal()
     b_R = -(A[R][:, D] @ uD)
     b_C = -(A[C][:, D] @ uD)
+    if g is not None:
+        b_R = b_R + g[R]
+        b_C = b_C + g[C]
     S = (A_RR - A_RC @ sp.diags(1.0 / A_CC) @ A_CR).tocsr()
     b = b_R - A_RC @ (b_C / A_CC)
     S.sort_indices()
     return S, b, R
 
 
-def solve_full(pb, A=None, mesh=None):
+def solve_full(pb, A=None, mesh=None, g=None):
     """Direct sparse solve of the full Galerkin system with the Dirichlet
-    values substituted.  Returns u over [nodes | ffaces | cells]."""
+    values substituted (and an optional source g over the full DOFs).
+    Returns u over [nodes | ffaces | cells]."""
     A = A if A is not None else assemble_full(pb, mesh)
     n = A.shape[0]
     isdir = np.zeros(n, bool); isdir[pb.dir_nodes] = True
@@ -292,14 +377,16 @@ def solve_full(pb, A=None, mesh=None):
     u = np.zeros(n)
     u[pb.dir_nodes] = pb.dir_values
     rhs = -(A[U][:, pb.dir_nodes] @ pb.dir_values)
+    if g is not None:
+        rhs = rhs + g[U]
     u[U] = spla.spsolve(A[U][:, U].tocsc(), rhs)
     return u
 
 
-def solve_schur_direct(pb, A=None, mesh=None):
+def solve_schur_direct(pb, A=None, mesh=None, g=None):
     """Solve Eq. (eqschur) directly, then recover the cells by Eq. (eqschurcell)."""
     A = A if A is not None else assemble_full(pb, mesh)
-    S, b, R = schur_system(pb, A)
+    S, b, R = schur_system(pb, A, g=g)
     n = A.shape[0]
     u = np.zeros(n)
     u[pb.dir_nodes] = pb.dir_values
@@ -373,7 +460,8 @@ def fracture_fluxes(fm, u):
     """F_{sigma,s} = sum_{s'} a_{sigma,s}^{s'} (u_sigma - u_{s'})."""
     d = fm["dofs"]; M = fm["M"]
     a = M[:, 1:, 1:]
-    diff = u[d[:, 0]][:, None] - u[d[:, 1:]]
+    valid = d[:, 1:] >= 0
+    diff = np.where(valid, u[d[:, 0]][:, None] - u[np.where(valid, d[:, 1:], 0)], 0.0)
     return np.einsum("bij,bj->bi", a, diff)
 
 
@@ -389,10 +477,19 @@ class Transport:
     the [nodes | ffaces | cells] order.
     """
 
-    def __init__(self, pb, cellmats, fracmats, F_cell, F_frac, omega=0.5, mesh=None):
+    def __init__(self, pb, cellmats, fracmats, F_cell, F_frac, omega=0.5, mesh=None, well_rates=None):
         m = mesh or Mesh(pb)
         nv, nf, nc = m.nv, m.nf, m.nc
         self.n = nv + nf + nc
+        # well perforations (Sec. 5.5): rate q_p leaving face sigma into the
+        # well; a negative rate enters the face at the injected concentration
+        w = getattr(pb, "wells", None)
+        if w:
+            self.w_cv = nv + np.asarray(w["ff"], np.int64)
+            self.w_F = np.asarray(well_rates, np.float64)
+            self.w_cin = np.asarray(w["cin"], np.float64)
+        else:
+            self.w_cv = np.zeros(0, np.int64); self.w_F = np.zeros(0); self.w_cin = np.zeros(0)
         isdir = np.zeros(nv, bool); isdir[pb.dir_nodes] = True
         self.isdir = isdir
         self.dir_nodes = pb.dir_nodes
@@ -409,25 +506,27 @@ class Transport:
         if nf:
             d = fracmats["dofs"]
             S = np.repeat(d[:, :1], d.shape[1] - 1, axis=1)
-            src.append(S.ravel()); dst.append(d[:, 1:].ravel()); flx.append(F_frac.ravel())
+            ok = d[:, 1:] >= 0
+            src.append(S[ok]); dst.append(d[:, 1:][ok]); flx.append(F_frac[ok])
         self.src = np.concatenate(src); self.dst = np.concatenate(dst); self.F = np.concatenate(flx)
         # porous volumes (Sec. 3.2.1)
         phi = np.zeros(self.n)
-        VK = m.VK
-        nVK = VK.shape[1]
-        elig = ~(isdir[VK] | m.VG[VK])                      # s in V_K \ (V_D u V_Gamma)
-        aK = omega / nVK
         pv_cell = vol * pb.phi_m
-        phi[nv + nf:] = (1.0 - aK * elig.sum(axis=1)) * pv_cell
-        np.add.at(phi, VK[elig], np.repeat(aK * pv_cell[:, None], nVK, axis=1)[elig])
+        for cells, VK, _, _ in m.groups:
+            nVK = VK.shape[1]
+            elig = ~(isdir[VK] | m.VG[VK])                  # s in V_K \ (V_D u V_Gamma)
+            aK = omega / nVK
+            phi[nv + nf + cells] = (1.0 - aK * elig.sum(axis=1)) * pv_cell[cells]
+            np.add.at(phi, VK[elig], np.repeat(aK * pv_cell[cells][:, None], nVK, axis=1)[elig])
         if nf:
             fn = m.faces[m.ff]
-            q = fn.shape[1]
-            eligf = ~isdir[fn]
+            valid = fn >= 0
+            q = m.fq[m.ff]
+            eligf = valid & ~isdir[np.where(valid, fn, 0)]
             af = omega / q
             pv_ff = pb.d_f * fracmats["area"] * pb.phi_f
             phi[nv:nv + nf] = (1.0 - af * eligf.sum(axis=1)) * pv_ff
-            np.add.at(phi, fn[eligf], np.repeat(af * pv_ff[:, None], q, axis=1)[eligf])
+            np.add.at(phi, fn[eligf], np.repeat((af * pv_ff)[:, None], fn.shape[1], axis=1)[eligf])
         phi[pb.dir_nodes] = 0.0
         self.phi = phi
         self.vol = vol
@@ -437,6 +536,7 @@ class Transport:
         out = np.zeros(self.n)
         np.add.at(out, self.src, np.maximum(self.F, 0.0))
         np.add.at(out, self.dst, np.maximum(-self.F, 0.0))
+        np.add.at(out, self.w_cv, np.maximum(self.w_F, 0.0))
         return out
 
     def cfl_dt(self):
@@ -449,14 +549,20 @@ class Transport:
             r = np.where(out[active] > 0, self.phi[active] / out[active], np.inf)
         return float(np.min(r))
 
+    def _well_H(self, c):
+        """Upwind well terms: q c_sigma for production, q c_in for injection."""
+        return np.where(self.w_F > 0.0, c[self.w_cv] * self.w_F, self.w_cin * self.w_F)
+
     def step(self, c, dt):
         """One explicit Euler step with the upwind fluxes of Eq. (darcyfluxH):
         H = c_src F^+ + c_dst F^-; the source CV of each edge loses H, the
-        destination gains it; Dirichlet nodes are reset to cbar."""
+        destination gains it; a well takes H = q c_sigma (q > 0) or q c_in
+        (q < 0) from its face; Dirichlet nodes are reset to cbar."""
         H = c[self.src] * np.maximum(self.F, 0.0) + c[self.dst] * np.minimum(self.F, 0.0)
         net = np.zeros(self.n)
         np.add.at(net, self.src, -H)
         np.add.at(net, self.dst, H)
+        np.add.at(net, self.w_cv, -self._well_H(c))
         cn = c.copy()
         act = np.ones(self.n, bool); act[self.dir_nodes] = False
         cn[act] = c[act] + dt / self.phi[act] * net[act]
@@ -465,12 +571,12 @@ class Transport:
 
     def boundary_inflow(self, c):
         """Net upwind flux entering the non-Dirichlet CVs through edges that
-        touch a Dirichlet node (the only edges that do not cancel in the total
-        mass)."""
+        touch a Dirichlet node, and through the wells (the only terms that do
+        not cancel in the total mass)."""
         H = c[self.src] * np.maximum(self.F, 0.0) + c[self.dst] * np.minimum(self.F, 0.0)
         dd = self.isdir_full(self.dst)
         ds = self.isdir_full(self.src)
-        return float(np.sum(-H[dd & ~ds]) + np.sum(H[ds & ~dd]))
+        return float(np.sum(-H[dd & ~ds]) + np.sum(H[ds & ~dd]) - np.sum(self._well_H(c)))
 
     def isdir_full(self, ids):
         out = np.zeros(ids.shape, bool)
@@ -492,24 +598,27 @@ class DarcyTransport:
         self.cellmats = _all_cell_matrices(pb, self.mesh)
         self.fracmats = fracture_local_matrices(pb, self.mesh)
         self.A = assemble_full(pb, self.mesh, self.cellmats, self.fracmats)
+        wd, g = well_terms(pb)
+        Aw = self.A if wd is None else (self.A + sp.diags(wd)).tocsr()   # the system with the wells
         if solver == "auto":
             solver = "direct" if self.A.shape[0] <= 30000 else "schur_pcg"
         self.solver = solver
         if solver == "direct":
-            self.u = solve_full(pb, self.A)
+            self.u = solve_full(pb, Aw, g=g)
         elif solver == "schur_direct":
-            self.u = solve_schur_direct(pb, self.A)
+            self.u = solve_schur_direct(pb, Aw, g=g)
         elif solver == "schur_pcg":
-            S, b, R = schur_system(pb, self.A)
+            S, b, R = schur_system(pb, Aw, g=g)
             x, self.iters = pcg_jacobi(S, b, rtol=rtol)
             u = np.zeros(self.A.shape[0]); u[pb.dir_nodes] = pb.dir_values; u[R] = x
-            self.u = recover_cells(pb, self.A, u)
+            self.u = recover_cells(pb, Aw, u)
         else:
             raise ValueError(solver)
         self.F_cell = [cell_fluxes(cm, self.u) for cm in self.cellmats]
         self.F_frac = fracture_fluxes(self.fracmats, self.u) if pb.n_ff else np.zeros((0, 4))
+        self.q_well = well_rates(pb, self.u) if wd is not None else np.zeros(0)
         self.tr = Transport(pb, self.cellmats, self.fracmats, self.F_cell, self.F_frac,
-                            omega=omega, mesh=self.mesh)
+                            omega=omega, mesh=self.mesh, well_rates=self.q_well)
 
     def run_transport(self, n_steps, cfl=0.9, c=None):
         dt = cfl * self.tr.cfl_dt()
@@ -537,14 +646,17 @@ def stationary_concentration(tr: Transport):
     Dirichlet nodes held at cbar.  Sparse direct solve."""
     n = tr.n
     Fp = np.maximum(tr.F, 0.0); Fm = np.minimum(tr.F, 0.0)
-    r = np.concatenate([tr.src, tr.src, tr.dst, tr.dst])
-    c = np.concatenate([tr.src, tr.dst, tr.src, tr.dst])
-    v = np.concatenate([-Fp, -Fm, Fp, Fm])
+    wp = tr.w_F > 0.0
+    r = np.concatenate([tr.src, tr.src, tr.dst, tr.dst, tr.w_cv[wp]])
+    c = np.concatenate([tr.src, tr.dst, tr.src, tr.dst, tr.w_cv[wp]])
+    v = np.concatenate([-Fp, -Fm, Fp, Fm, -tr.w_F[wp]])
     B = sp.coo_matrix((v, (r, c)), shape=(n, n)).tocsr()
+    inj = np.zeros(n)                                      # injection: -q c_in enters the face
+    np.add.at(inj, tr.w_cv[~wp], -tr.w_F[~wp] * tr.w_cin[~wp])
     isd = np.zeros(n, bool); isd[tr.dir_nodes] = True
     U = np.nonzero(~isd)[0]
     cfull = np.zeros(n)
     cfull[tr.dir_nodes] = tr.cbar
-    rhs = -(B[U][:, tr.dir_nodes] @ tr.cbar)
+    rhs = -(B[U][:, tr.dir_nodes] @ tr.cbar) - inj[U]
     cfull[U] = spla.spsolve(B[U][:, U].tocsc(), rhs)
     return cfull

@@ -1,11 +1,13 @@
 // Numeric phase of vag_assemble (FP64):
 //  k_cell_local  one thread per cell: the local VAG matrix
 //                a_{K,nu}^{nu'} = int_K Lambda_m/mu grad eta_nu . grad eta_nu'
-//                of Eq. (VAGFluxMatrix), integrated exactly on the 24
-//                tetrahedra T_{K,sigma,e} = conv(x_K, x_sigma, e) (Sec. 3.1).
-//                The face-centre vertex of a non-fracture face is the
-//                interpolation I_sigma (beta = 1/4 on the face nodes); on a
-//                fracture face it is the unknown v_sigma.
+//                of Eq. (VAGFluxMatrix), integrated exactly on the
+//                tetrahedra T_{K,sigma,e} = conv(x_K, x_sigma, e) (Sec. 3.1):
+//                24 for a hexahedron, 18 for a prism, 16 for a pyramid, 12
+//                for a tetrahedron (vag_topo.h).  The face-centre vertex of
+//                a non-fracture face is the interpolation I_sigma (beta =
+//                1/|V_sigma| on the face nodes); on a fracture face it is the
+//                unknown v_sigma.
 //  k_ff_local    one thread per fracture face: a_{sigma,s}^{s'} of
 //                Eq. (VAGFluxFracture) on the triangles (x_sigma, e).
 //  k_gather_rows one thread per Krylov row: the Schur complement of
@@ -13,8 +15,11 @@
 //                summed over the row's cells and fracture faces in a fixed
 //                order (deterministic, no atomics); Dirichlet columns go to
 //                the right-hand side.
+//  k_wells       one thread per well perforation: the Peaceman term of
+//                Sec. 5.5, q_sigma = WI_sigma (p_sigma - p_w) - q_sigma^inj,
+//                on the fracture-face row (diagonal and right-hand side).
 #include "vag_internal.cuh"
-#include "vag_hex.cuh"
+#include "vag_topo.h"
 
 namespace vag {
 namespace {
@@ -69,106 +74,137 @@ __device__ __forceinline__ void tet_stiffness(V3 p0, V3 p1, V3 p2, V3 p3, const 
     for (int j = i; j < 4; ++j) S[p4(i, j)] = dot(n[i], Ln[j]) * inv;
 }
 
-__global__ void __launch_bounds__(128) k_cell_local(int nc, const int *__restrict__ cn, const double *__restrict__ xyz,
-                                                    const double *__restrict__ lam, double inv_mu,
-                                                    const int *__restrict__ cell_ff, const int *__restrict__ fc_index,
-                                                    int n_fc, double *__restrict__ Mc, double *__restrict__ Mfc,
-                                                    double *__restrict__ cvol, int *status) {
-  const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K >= nc) return;
-  double L[6];
+// The local matrix of one cell of shape SH: M over (K, node slots 0..7)
+// packed, Mfc over (sigma sigma, sigma K, sigma n_t) for each fracture face.
+template <int SH>
+__device__ __forceinline__ void cell_local(int K, int nc, const int *__restrict__ cn, const double *__restrict__ xyz,
+                                           const double (&L)[6], const int *__restrict__ cell_ff, int fi, int n_fc,
+                                           double *__restrict__ Mc, double *__restrict__ Mfc,
+                                           double *__restrict__ cvol, int *status) {
+  constexpr int NN = topo::n_nodes(SH), NF = topo::n_faces(SH);
+  int nd[NN];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) L[k] = lam[6 * (size_t)K + k] * inv_mu;
-  int nd[8];
-#pragma unroll
-  for (int l = 0; l < 8; ++l) nd[l] = cn[8 * (size_t)K + l];
+  for (int l = 0; l < NN; ++l) nd[l] = cn[8 * (size_t)K + l];
   V3 xK = {0, 0, 0};
 #pragma unroll
-  for (int l = 0; l < 8; ++l) xK = xK + ldv(xyz, nd[l]);
-  xK = {xK.x * 0.125, xK.y * 0.125, xK.z * 0.125};
-  const int fi = fc_index[K];
+  for (int l = 0; l < NN; ++l) xK = xK + ldv(xyz, nd[l]);
+  xK = {xK.x / NN, xK.y / NN, xK.z / NN};
 
-  double M[hex::kPacked];
+  double M[topo::kPacked];
 #pragma unroll
-  for (int k = 0; k < hex::kPacked; ++k) M[k] = 0.0;
+  for (int k = 0; k < topo::kPacked; ++k) M[k] = 0.0;
   double vol = 0.0;
   double minvol = 1e300;
 
 #pragma unroll
-  for (int lf = 0; lf < 6; ++lf) {
-    V3 q[4];
+  for (int lf = 0; lf < NF; ++lf) {
+    constexpr int Q4 = 4;
+    const int Q = topo::face_size(SH, lf);     // 3 or 4, known at compile time
+    const double w = 1.0 / Q;                  // beta_{sigma,s} of I_sigma
+    V3 q[Q4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) q[t] = ldv(xyz, nd[hex::face(lf, t)]);
-    const V3 xs = {0.25 * (q[0].x + q[1].x + q[2].x + q[3].x), 0.25 * (q[0].y + q[1].y + q[2].y + q[3].y),
-                   0.25 * (q[0].z + q[1].z + q[2].z + q[3].z)};
+    for (int t = 0; t < Q4; ++t) q[t] = t < Q ? ldv(xyz, nd[topo::face(SH, lf, t)]) : V3{0, 0, 0};
+    V3 xs = q[0] + q[1] + q[2];
+    if (Q == 4) xs = xs + q[3];
+    xs = {xs.x / Q, xs.y / Q, xs.z / Q};
     double F[21];
 #pragma unroll
     for (int k = 0; k < 21; ++k) F[k] = 0.0;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < Q4; ++e) {
+      if (e >= Q) break;
+      const int e1 = e + 1 == Q ? 0 : e + 1;
       double S[10], tv;
-      tet_stiffness(xK, xs, q[e], q[(e + 1) & 3], L, S, tv);
+      tet_stiffness(xK, xs, q[e], q[e1], L, S, tv);
       vol += tv;
       minvol = fmin(minvol, tv);
-      const int map[4] = {0, 1, 2 + e, 2 + ((e + 1) & 3)};
+      const int map[4] = {0, 1, 2 + e, 2 + e1};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = i; j < 4; ++j) F[p6(map[i], map[j])] += S[p4(i, j)];
     }
     const bool isff = cell_ff[6 * (size_t)K + lf] >= 0;
-    M[hex::pidx(0, 0)] += F[p6(0, 0)];
+    M[topo::pidx(0, 0)] += F[p6(0, 0)];
     if (!isff) {
-      // x_sigma = I_sigma: the sigma row/column is spread with weight 1/4
+      // x_sigma = I_sigma: the sigma row/column is spread with weight 1/Q
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int a = 1 + hex::face(lf, t);
-        M[hex::pidx(0, a)] += F[p6(0, 2 + t)] + 0.25 * F[p6(0, 1)];
+      for (int t = 0; t < Q4; ++t) {
+        if (t >= Q) break;
+        const int a = 1 + topo::face(SH, lf, t);
+        M[topo::pidx(0, a)] += F[p6(0, 2 + t)] + w * F[p6(0, 1)];
 #pragma unroll
-        for (int u = t; u < 4; ++u) {
-          const int b = 1 + hex::face(lf, u);
-          M[hex::pidx(a, b)] += F[p6(2 + t, 2 + u)] + 0.25 * (F[p6(1, 2 + u)] + F[p6(1, 2 + t)]) +
-                                0.0625 * F[p6(1, 1)];
+        for (int u = t; u < Q4; ++u) {
+          if (u >= Q) break;
+          const int b = 1 + topo::face(SH, lf, u);
+          M[topo::pidx(a, b)] += F[p6(2 + t, 2 + u)] + w * (F[p6(1, 2 + u)] + F[p6(1, 2 + t)]) +
+                                 (w * w) * F[p6(1, 1)];
         }
       }
     } else {
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int a = 1 + hex::face(lf, t);
-        M[hex::pidx(0, a)] += F[p6(0, 2 + t)];
+      for (int t = 0; t < Q4; ++t) {
+        if (t >= Q) break;
+        const int a = 1 + topo::face(SH, lf, t);
+        M[topo::pidx(0, a)] += F[p6(0, 2 + t)];
 #pragma unroll
-        for (int u = t; u < 4; ++u) {
-          const int b = 1 + hex::face(lf, u);
-          M[hex::pidx(a, b)] += F[p6(2 + t, 2 + u)];
+        for (int u = t; u < Q4; ++u) {
+          if (u >= Q) break;
+          const int b = 1 + topo::face(SH, lf, u);
+          M[topo::pidx(a, b)] += F[p6(2 + t, 2 + u)];
         }
       }
       if (fi >= 0) {
         Mfc[(size_t)(lf * 6 + 0) * n_fc + fi] = F[p6(1, 1)];
         Mfc[(size_t)(lf * 6 + 1) * n_fc + fi] = F[p6(0, 1)];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) Mfc[(size_t)(lf * 6 + 2 + t) * n_fc + fi] = F[p6(1, 2 + t)];
+        for (int t = 0; t < Q4; ++t) Mfc[(size_t)(lf * 6 + 2 + t) * n_fc + fi] = t < Q ? F[p6(1, 2 + t)] : 0.0;
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < hex::kPacked; ++k) Mc[(size_t)k * nc + K] = M[k];
+  for (int k = 0; k < topo::kPacked; ++k) Mc[(size_t)k * nc + K] = M[k];
   cvol[K] = vol;
   if (!(minvol > 0.0)) atomicOr(status, ST_BAD_GEOMETRY);
 }
 
+// One thread per cell of shape SH: cell cells[i] (or cell i when the list is
+// NULL, a mesh of that shape alone).  Every cell of a shape runs this one
+// kernel whatever else the mesh or batch holds, so its arithmetic, and the
+// system's, do not depend on the other cells.
+template <int SH>
+__global__ void __launch_bounds__(128) k_cell_local(int n, const int *__restrict__ cells, int nc,
+                                                    const int *__restrict__ cn, const double *__restrict__ xyz,
+                                                    const double *__restrict__ lam, double inv_mu,
+                                                    const int *__restrict__ cell_ff, const int *__restrict__ fc_index,
+                                                    int n_fc, double *__restrict__ Mc, double *__restrict__ Mfc,
+                                                    double *__restrict__ cvol, int *status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int K = cells ? cells[i] : i;
+  double L[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) L[k] = lam[6 * (size_t)K + k] * inv_mu;
+  cell_local<SH>(K, nc, cn, xyz, L, cell_ff, fc_index[K], n_fc, Mc, Mfc, cvol, status);
+}
+
 // Fracture-face matrix on (sigma, n0..n3) from the P1 tangential stiffness of
-// the triangles (x_sigma, n_e, n_{e+1}): with the edge vectors E_i opposite
+// the triangles (x_sigma, n_e, n_{e+1}) of a quadrilateral or triangular
+// face (node slot 3 = -1; its row and column stay zero): with the edge vectors E_i opposite
 // vertex i (E0 + E1 + E2 = 0), S_ij = coef (E_i . E_j) / (4 |T|).
 __global__ void k_ff_local(int nf, const int *__restrict__ ffn, const double *__restrict__ xyz,
                            const double *__restrict__ lamf, const double *__restrict__ df, double inv_mu,
                            double *__restrict__ Mff, double *__restrict__ area, int *status) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
+  const int Q = ffn[4 * (size_t)f + 3] < 0 ? 3 : 4;   // triangle or quadrilateral
   V3 q[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) q[t] = ldv(xyz, ffn[4 * (size_t)f + t]);
-  const V3 xs = {0.25 * (q[0].x + q[1].x + q[2].x + q[3].x), 0.25 * (q[0].y + q[1].y + q[2].y + q[3].y),
-                 0.25 * (q[0].z + q[1].z + q[2].z + q[3].z)};
+  for (int t = 0; t < 4; ++t) q[t] = t < Q ? ldv(xyz, ffn[4 * (size_t)f + t]) : V3{0, 0, 0};
+  const V3 xs = Q == 4 ? V3{0.25 * (q[0].x + q[1].x + q[2].x + q[3].x), 0.25 * (q[0].y + q[1].y + q[2].y + q[3].y),
+                            0.25 * (q[0].z + q[1].z + q[2].z + q[3].z)}
+                       : V3{(q[0].x + q[1].x + q[2].x) / 3.0, (q[0].y + q[1].y + q[2].y) / 3.0,
+                            (q[0].z + q[1].z + q[2].z) / 3.0};
   const double coef = df[f] * lamf[f] * inv_mu;
   double M[25];
 #pragma unroll
@@ -176,14 +212,16 @@ __global__ void k_ff_local(int nf, const int *__restrict__ ffn, const double *__
   double ar = 0.0, minar = 1e300;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const V3 a = q[e], b = q[(e + 1) & 3];
+    if (e >= Q) break;
+    const int e1 = e + 1 == Q ? 0 : e + 1;
+    const V3 a = q[e], b = q[e1];
     const V3 E[3] = {b - a, xs - b, a - xs};
     const V3 nrm = cross(a - xs, b - xs);
     const double A = 0.5 * sqrt(dot(nrm, nrm));
     ar += A;
     minar = fmin(minar, A);
     const double c = coef / (4.0 * A);
-    const int map[3] = {0, 1 + e, 1 + ((e + 1) & 3)};
+    const int map[3] = {0, 1 + e, 1 + e1};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -197,6 +235,7 @@ __global__ void k_ff_local(int nf, const int *__restrict__ ffn, const double *__
 
 struct GatherView {
   int nv, nc, nf, n_fc;
+  const int8_t *shape;   // per-cell shape, or nullptr when every cell is a hexahedron
   const int *cn, *ffn, *node_dir, *cell_ff, *ff_cells, *ff_lface, *fc_index;
   const int *n2c_ptr, *n2c, *n2f_ptr, *n2f, *row_of_dof, *dof_of_row;
   const int *rowptr, *col, *diag_pos;
@@ -227,12 +266,15 @@ struct RowAcc {
 };
 
 __device__ __forceinline__ double mc(const GatherView &g, int i, int j, int K) {
-  return g.Mc[(size_t)hex::pidx(i, j) * g.nc + K];
+  return g.Mc[(size_t)topo::pidx(i, j) * g.nc + K];
 }
 __device__ __forceinline__ double mfc(const GatherView &g, int lf, int k, int fi) {
   return g.Mfc[(size_t)(lf * 6 + k) * g.n_fc + fi];
 }
 
+// GEN: cells of any shape (g.shape) and triangular fracture faces (node
+// slot 3 = -1); otherwise every cell is a hexahedron.
+template <bool GEN>
 __global__ void k_gather_rows(GatherView g, int n_rows, int *status) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
@@ -244,15 +286,19 @@ __global__ void k_gather_rows(GatherView g, int n_rows, int *status) {
     // node row s: Schur rows of the cells around s, then fracture rows
     for (int e = g.n2c_ptr[dof]; e < g.n2c_ptr[dof + 1]; ++e) {
       const int K = g.n2c[e] >> 3, a = g.n2c[e] & 7;
+      const int sh = GEN ? g.shape[K] : topo::HEX;
       const double fac = mc(g, 0, 1 + a, K) / mc(g, 0, 0, K);     // M_aK / M_KK
-      for (int bn = 0; bn < 8; ++bn)
-        acc.add(g.cn[8 * (size_t)K + bn], mc(g, 1 + a, 1 + bn, K) - fac * mc(g, 0, 1 + bn, K));
+      for (int bn = 0; bn < 8; ++bn) {
+        const int nb = g.cn[8 * (size_t)K + bn];
+        if (GEN && nb < 0) continue;
+        acc.add(nb, mc(g, 1 + a, 1 + bn, K) - fac * mc(g, 0, 1 + bn, K));
+      }
       const int fi = g.fc_index[K];
       if (fi >= 0) {
         for (int lf = 0; lf < 6; ++lf) {
           const int f = g.cell_ff[6 * (size_t)K + lf];
           if (f < 0) continue;
-          const int t = hex::pos_on_face(lf, a);
+          const int t = topo::pos_on_face(sh, lf, a);
           const double Mas = t >= 0 ? mfc(g, lf, 2 + t, fi) : 0.0;
           acc.add(g.nv + f, Mas - fac * mfc(g, lf, 1, fi));
         }
@@ -261,7 +307,11 @@ __global__ void k_gather_rows(GatherView g, int n_rows, int *status) {
     for (int e = g.n2f_ptr[dof]; e < g.n2f_ptr[dof + 1]; ++e) {
       const int f = g.n2f[e] >> 2, t = g.n2f[e] & 3;
       acc.add(g.nv + f, g.Mff[(size_t)((1 + t) * 5) * g.nf + f]);
-      for (int u = 0; u < 4; ++u) acc.add(g.ffn[4 * (size_t)f + u], g.Mff[(size_t)((1 + t) * 5 + 1 + u) * g.nf + f]);
+      for (int u = 0; u < 4; ++u) {
+        const int nb = g.ffn[4 * (size_t)f + u];
+        if (GEN && nb < 0) continue;
+        acc.add(nb, g.Mff[(size_t)((1 + t) * 5 + 1 + u) * g.nf + f]);
+      }
     }
   } else {
     const int f = dof - g.nv;
@@ -270,11 +320,14 @@ __global__ void k_gather_rows(GatherView g, int n_rows, int *status) {
       if (K < 0) continue;
       const int lf = g.ff_lface[2 * f + c];
       const int fi = g.fc_index[K];
+      const int sh = GEN ? g.shape[K] : topo::HEX;
       const double fac = mfc(g, lf, 1, fi) / mc(g, 0, 0, K);      // M_sigmaK / M_KK
       for (int bn = 0; bn < 8; ++bn) {
-        const int t = hex::pos_on_face(lf, bn);
+        const int nb = g.cn[8 * (size_t)K + bn];
+        if (GEN && nb < 0) continue;
+        const int t = topo::pos_on_face(sh, lf, bn);
         const double Msb = t >= 0 ? mfc(g, lf, 2 + t, fi) : 0.0;
-        acc.add(g.cn[8 * (size_t)K + bn], Msb - fac * mc(g, 0, 1 + bn, K));
+        acc.add(nb, Msb - fac * mc(g, 0, 1 + bn, K));
       }
       for (int lf2 = 0; lf2 < 6; ++lf2) {
         const int f2 = g.cell_ff[6 * (size_t)K + lf2];
@@ -284,7 +337,11 @@ __global__ void k_gather_rows(GatherView g, int n_rows, int *status) {
       }
     }
     acc.add(g.nv + f, g.Mff[(size_t)0 * g.nf + f]);
-    for (int u = 0; u < 4; ++u) acc.add(g.ffn[4 * (size_t)f + u], g.Mff[(size_t)(1 + u) * g.nf + f]);
+    for (int u = 0; u < 4; ++u) {
+      const int nb = g.ffn[4 * (size_t)f + u];
+      if (GEN && nb < 0) continue;
+      acc.add(nb, g.Mff[(size_t)(1 + u) * g.nf + f]);
+    }
   }
   g.rhs[r] = acc.b;
   const double d = g.val[g.diag_pos[r]];   // the symbolic phase guarantees a diagonal slot
@@ -292,12 +349,28 @@ __global__ void k_gather_rows(GatherView g, int n_rows, int *status) {
   g.dinv[r] = 1.0 / d;
 }
 
+// Perforation p of fracture face ff[p] adds WI[p] to the face's diagonal and
+// WI[p] p_w[p] + q[p] to its right-hand side (the faces are distinct).
+__global__ void k_wells(int n_perf, int nv, const int *__restrict__ ff, const double *__restrict__ wi,
+                        const double *__restrict__ pw, const double *__restrict__ q, const int *__restrict__ row_of_dof,
+                        const int *__restrict__ diag_pos, double *__restrict__ val, double *__restrict__ rhs,
+                        double *__restrict__ dinv) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_perf) return;
+  const int r = row_of_dof[nv + ff[p]];
+  const int k = diag_pos[r];
+  const double d = val[k] + wi[p];
+  val[k] = d;
+  rhs[r] += fma(wi[p], pw[p], q[p]);
+  dinv[r] = 1.0 / d;
+}
+
 }  // namespace
 
 void numeric_phase(System *s) {
   cudaStream_t st = s->ctx->stream;
   if (!s->Mc) {
-    s->Mc = sys_alloc<double>(s, (size_t)hex::kPacked * s->nc);
+    s->Mc = sys_alloc<double>(s, (size_t)topo::kPacked * s->nc);
     s->Mfc = sys_alloc<double>(s, (size_t)36 * (s->n_fc > 0 ? s->n_fc : 1));
     s->Mff = sys_alloc<double>(s, (size_t)25 * (s->nf > 0 ? s->nf : 1));
     s->cvol = sys_alloc<double>(s, s->nc);
@@ -308,20 +381,46 @@ void numeric_phase(System *s) {
   }
   VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   const double inv_mu = 1.0 / s->mu;
-  k_cell_local<<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, s->cell_nodes, s->xyz, s->lam, inv_mu, s->cell_ff,
-                                                      s->fc_index, s->n_fc, s->Mc, s->Mfc, s->cvol, s->status); note_launches(1);
+  if (!s->cell_shape) {
+    k_cell_local<topo::HEX><<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, nullptr, s->nc, s->cell_nodes, s->xyz,
+                                                                   s->lam, inv_mu, s->cell_ff, s->fc_index, s->n_fc,
+                                                                   s->Mc, s->Mfc, s->cvol, s->status);
+    note_launches(1);
+  } else {   // one launch per shape over its cell list
+    decltype(&k_cell_local<topo::HEX>) kern[topo::N_SHAPES] = {k_cell_local<topo::HEX>, k_cell_local<topo::TET>,
+                                                               k_cell_local<topo::PRISM>, k_cell_local<topo::PYRAMID>};
+    for (int sh = 0; sh < topo::N_SHAPES; ++sh) {
+      const int n = s->shape_start[sh + 1] - s->shape_start[sh];
+      if (!n) continue;
+      kern[sh]<<<grid_for(n, 128), 128, 0, st>>>(n, s->shape_cells + s->shape_start[sh], s->nc, s->cell_nodes,
+                                                 s->xyz, s->lam, inv_mu, s->cell_ff, s->fc_index, s->n_fc, s->Mc,
+                                                 s->Mfc, s->cvol, s->status);
+      note_launches(1);
+    }
+  }
   VAG_CHECK_LAUNCH();
   if (s->nf) {
     k_ff_local<<<grid_for(s->nf, 128), 128, 0, st>>>(s->nf, s->ff_nodes, s->xyz, s->lamf, s->df, inv_mu, s->Mff,
                                                       s->ffarea, s->status); note_launches(1);
     VAG_CHECK_LAUNCH();
   }
-  GatherView g{s->nv, s->nc, s->nf, s->n_fc, s->cell_nodes, s->ff_nodes, s->node_dir, s->cell_ff,
+  GatherView g{s->nv, s->nc, s->nf, s->n_fc, s->cell_shape, s->cell_nodes, s->ff_nodes, s->node_dir, s->cell_ff,
                s->ff_cells, s->ff_lface, s->fc_index, s->n2c_ptr, s->n2c, s->n2f_ptr, s->n2f,
                s->row_of_dof, s->dof_of_row, s->rowptr, s->col, s->diag_pos, s->Mc, s->Mfc, s->Mff,
                s->dir_vals, s->val, s->rhs, s->dinv};
-  k_gather_rows<<<grid_for(s->n_rows, 128), 128, 0, st>>>(g, s->n_rows, s->status); note_launches(1);
+  if (s->cell_shape || s->tri_ff)
+    k_gather_rows<true><<<grid_for(s->n_rows, 128), 128, 0, st>>>(g, s->n_rows, s->status);
+  else
+    k_gather_rows<false><<<grid_for(s->n_rows, 128), 128, 0, st>>>(g, s->n_rows, s->status);
+  note_launches(1);
   VAG_CHECK_LAUNCH();
+  if (s->n_perf) {
+    k_wells<<<grid_for(s->n_perf, 128), 128, 0, st>>>(s->n_perf, s->nv, s->well_ff, s->well_wi, s->well_pw,
+                                                       s->well_q, s->row_of_dof, s->diag_pos, s->val, s->rhs,
+                                                       s->dinv);
+    note_launches(1);
+    VAG_CHECK_LAUNCH();
+  }
   if (s->sval) sell_values(s);
   s->mx.stale = true;
   s->mx.dstale = true;

@@ -3,10 +3,13 @@
 // codes.  No exception crosses this boundary.
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 
 #include "vag_internal.cuh"
+#include "vag_topo.h"
 
 using namespace vag;
 
@@ -59,6 +62,86 @@ void copy_in(System *s, T *dst, const T *src, size_t n, int mem, const char *wha
   if (n) VAG_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * n, to_dev(mem), s->ctx->stream));
 }
 
+// Peaceman wells of one or more systems, validated on the host and put in
+// the union's fracture-face numbering.
+struct WellsHost {
+  std::vector<int> ff;
+  std::vector<double> wi, pw, q, cin;
+  bool fixes_level = false;   // some perforation has WI > 0
+};
+
+template <class T>
+void fetch(std::vector<T> &dst, const T *src, size_t n, int mem, cudaStream_t st, const char *what) {
+  if (n && !src) fail(VAG_EINVAL, std::string(what) + " is NULL");
+  const size_t old = dst.size();
+  dst.resize(old + n);
+  if (!n) return;
+  if (mem == VAG_MEM_HOST) {
+    std::copy(src, src + n, dst.begin() + old);
+  } else {
+    VAG_CUDA(cudaMemcpyAsync(dst.data() + old, src, sizeof(T) * n, cudaMemcpyDeviceToHost, st));
+    VAG_CUDA(cudaStreamSynchronize(st));
+  }
+}
+
+void gather_wells(WellsHost &w, const vag_props &p, int mem, int nf_sys, int ff_off, cudaStream_t st) {
+  if (p.n_perf < 0) fail(VAG_EINVAL, "n_perf < 0");
+  if (p.n_perf == 0) return;
+  const size_t n = (size_t)p.n_perf, b = w.ff.size();
+  fetch(w.ff, p.well_ff, n, mem, st, "well_ff");
+  fetch(w.wi, p.well_wi, n, mem, st, "well_wi");
+  fetch(w.pw, p.well_pw, n, mem, st, "well_pw");
+  fetch(w.q, p.well_q, n, mem, st, "well_q");
+  fetch(w.cin, p.well_cin, n, mem, st, "well_cin");
+  std::vector<int> seen(w.ff.begin() + b, w.ff.end());
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) fail(VAG_EINVAL, "a fracture face is perforated twice");
+  for (size_t i = b; i < b + n; ++i) {
+    if (w.ff[i] < 0 || w.ff[i] >= nf_sys) fail(VAG_EINVAL, "well_ff out of range");
+    if (!(w.wi[i] >= 0.0) || !std::isfinite(w.wi[i])) fail(VAG_EINVAL, "well_wi must be finite and >= 0");
+    if (!std::isfinite(w.pw[i]) || !std::isfinite(w.q[i]) || !std::isfinite(w.cin[i]))
+      fail(VAG_EINVAL, "well_pw, well_q and well_cin must be finite");
+    if (w.wi[i] > 0.0) w.fixes_level = true;
+    w.ff[i] += ff_off;
+  }
+}
+
+void upload_wells(System *s, const WellsHost &w) {
+  const int n = (int)w.ff.size();
+  if (n > s->perf_cap) {
+    s->well_ff = sys_alloc<int>(s, n);
+    s->well_wi = sys_alloc<double>(s, n);
+    s->well_pw = sys_alloc<double>(s, n);
+    s->well_q = sys_alloc<double>(s, n);
+    s->well_cin = sys_alloc<double>(s, n);
+    s->Fw = sys_alloc<double>(s, n);
+    s->perf_cap = n;
+  }
+  if (!s->ff_perf) s->ff_perf = sys_alloc<int>(s, s->nf > 0 ? s->nf : 1);
+  cudaStream_t st = s->ctx->stream;
+  if (n) {
+    VAG_CUDA(cudaMemsetAsync(s->Fw, 0, sizeof(double) * n, st));   // no well rates before a solve
+    VAG_CUDA(cudaMemcpyAsync(s->well_ff, w.ff.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    VAG_CUDA(cudaMemcpyAsync(s->well_wi, w.wi.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    VAG_CUDA(cudaMemcpyAsync(s->well_pw, w.pw.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    VAG_CUDA(cudaMemcpyAsync(s->well_q, w.q.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    VAG_CUDA(cudaMemcpyAsync(s->well_cin, w.cin.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  }
+  // fracture face -> perforation (or -1), for the transport map
+  std::vector<int> fp((size_t)(s->nf > 0 ? s->nf : 1), -1);
+  for (int i = 0; i < n; ++i) fp[w.ff[i]] = i;
+  VAG_CUDA(cudaMemcpyAsync(s->ff_perf, fp.data(), sizeof(int) * fp.size(), cudaMemcpyHostToDevice, st));
+  VAG_CUDA(cudaStreamSynchronize(st));   // the host vectors go out of scope
+  s->n_perf = n;
+}
+
+// Shapes of a general mesh: keep the per-cell array only when some cell is
+// not a hexahedron (the symbolic phase then groups the cells by shape).
+void set_shapes(System *s, int8_t *shape, unsigned mask, bool tri) {
+  s->tri_ff = s->tri_ff || tri;
+  s->cell_shape = mask == (1u << topo::HEX) ? nullptr : shape;
+}
+
 template <class T>
 void copy_out(const System *s, T *dst, const T *src, size_t n, int mem) {
   if (dst && n) VAG_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * n, from_dev(mem), s->ctx->stream));
@@ -79,7 +162,7 @@ void upload_segments(System *s) {
 
 __global__ void k_add_offset(int *a, int64_t n, int off) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) a[i] += off;
+  if (i < n && a[i] >= 0) a[i] += off;   // -1 marks an unused node slot
 }
 
 void free_ctx(vag_ctx *ctx) {
@@ -198,7 +281,7 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
     if (!mesh || !props || !bc || !out) fail(VAG_EINVAL, "null argument");
     check_mem(mem);
     if (mesh->n_nodes <= 0 || mesh->n_cells <= 0 || mesh->n_ff < 0) fail(VAG_EINVAL, "bad mesh sizes");
-    if (bc->n_dir <= 0) fail(VAG_EINVAL, "at least one Dirichlet node is required");
+    if (bc->n_dir < 0) fail(VAG_EINVAL, "n_dir < 0");
     if (!(props->mu > 0.0)) fail(VAG_EINVAL, "mu must be positive");
     if ((int64_t)mesh->n_nodes + mesh->n_ff + mesh->n_cells > 0x7fffffffLL) fail(VAG_EINVAL, "mesh too large");
     use_device(&ctx->c);
@@ -225,7 +308,17 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
     } else {                  // general polyhedral descriptor
       s->cell_nodes = sys_alloc<int>(s, 8 * (size_t)s->nc);
       s->ff_nodes = sys_alloc<int>(s, 4 * (size_t)s->nf);
-      general_to_hex(s->ctx, *mesh, mem, s->cell_nodes, s->ff_nodes);
+      int8_t *shape = sys_alloc<int8_t>(s, (size_t)s->nc);
+      bool tri = false;
+      const unsigned mask = general_to_cells(s->ctx, *mesh, mem, s->cell_nodes, s->ff_nodes, shape, &tri);
+      set_shapes(s, shape, mask, tri);
+    }
+    {
+      WellsHost w;
+      gather_wells(w, *props, mem, s->nf, 0, s->ctx->stream);
+      if (s->nd == 0 && !w.fixes_level)
+        fail(VAG_EINVAL, "at least one Dirichlet node or a well perforation with WI > 0 is required");
+      upload_wells(s, w);
     }
     s->dir_nodes = upload(s, bc->nodes, (size_t)s->nd, mem, "dirichlet nodes");
     s->dir_vals = upload(s, bc->values, (size_t)s->nd, mem, "dirichlet values");
@@ -270,7 +363,7 @@ vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshe
     for (int i = 0; i < n_sys; ++i) {
       const vag_mesh &m = meshes[i];
       if (m.n_nodes <= 0 || m.n_cells <= 0 || m.n_ff < 0) fail(VAG_EINVAL, "bad mesh sizes in system " + std::to_string(i));
-      if (bcs[i].n_dir <= 0) fail(VAG_EINVAL, "system " + std::to_string(i) + " has no Dirichlet node");
+      if (bcs[i].n_dir < 0) fail(VAG_EINVAL, "system " + std::to_string(i) + ": n_dir < 0");
       if (!(props[i].mu > 0.0)) fail(VAG_EINVAL, "mu must be positive");
       if (props[i].mu != props[0].mu) fail(VAG_EINVAL, "all systems of a batch must share mu");
       nv += m.n_nodes; nc += m.n_cells; nf += m.n_ff; nd += bcs[i].n_dir;
@@ -308,6 +401,12 @@ vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshe
     s->lamf = sys_alloc<double>(s, (size_t)nf);
     s->df = sys_alloc<double>(s, (size_t)nf);
     cudaStream_t str = ctx->c.stream;
+    int8_t *shape = sys_alloc<int8_t>(s, (size_t)nc);
+    VAG_CUDA(cudaMemsetAsync(shape, 0, (size_t)nc, str));   // topo::HEX == 0
+    static_assert(topo::HEX == 0, "fast-path cells are marked by a zero fill");
+    unsigned mask = 1u << topo::HEX;
+    bool tri = false;
+    WellsHost wells;
     for (int i = 0; i < n_sys; ++i) {
       const vag_mesh &m = meshes[i];
       const int v0 = g.node_start[i], c0 = g.cell_start[i], f0 = g.ff_start[i], d0 = g.dir_start[i];
@@ -316,7 +415,19 @@ vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshe
         copy_in(s, s->cell_nodes + 8 * (size_t)c0, m.cell_nodes, 8 * (size_t)m.n_cells, mem, "cell_nodes");
         copy_in(s, s->ff_nodes + 4 * (size_t)f0, m.ff_nodes, 4 * (size_t)m.n_ff, mem, "ff_nodes");
       } else {
-        general_to_hex(s->ctx, m, mem, s->cell_nodes + 8 * (size_t)c0, s->ff_nodes + 4 * (size_t)f0);
+        bool t = false;
+        mask |= general_to_cells(s->ctx, m, mem, s->cell_nodes + 8 * (size_t)c0, s->ff_nodes + 4 * (size_t)f0,
+                                 shape + c0, &t);
+        tri = tri || t;
+      }
+      {   // each system needs its own pressure level
+        const bool had = wells.fixes_level;
+        wells.fixes_level = false;
+        gather_wells(wells, props[i], mem, m.n_ff, f0, str);
+        if (bcs[i].n_dir == 0 && !wells.fixes_level)
+          fail(VAG_EINVAL, "system " + std::to_string(i) +
+                               " has neither a Dirichlet node nor a well perforation with WI > 0");
+        wells.fixes_level = wells.fixes_level || had;
       }
       copy_in(s, s->dir_nodes + d0, bcs[i].nodes, (size_t)bcs[i].n_dir, mem, "dirichlet nodes");
       copy_in(s, s->dir_vals + d0, bcs[i].values, (size_t)bcs[i].n_dir, mem, "dirichlet values");
@@ -334,6 +445,8 @@ vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshe
         VAG_CHECK_LAUNCH();
       }
     }
+    set_shapes(s, shape, mask, tri);
+    upload_wells(s, wells);
     upload_segments(s);
     symbolic_phase(s);
     build_tiles(s);
@@ -399,11 +512,34 @@ vag_status vag_update_props(vag_system *sys, const vag_props *props, int mem) {
     copy_in(s, s->lam, props->lambda_m, 6 * (size_t)s->nc, mem, "lambda_m");
     copy_in(s, s->lamf, props->lambda_f, (size_t)s->nf, mem, "lambda_f");
     copy_in(s, s->df, props->d_f, (size_t)s->nf, mem, "d_f");
+    WellsHost w;
+    gather_wells(w, *props, mem, s->nf, 0, s->ctx->stream);
+    if (s->nd == 0 && !w.fixes_level)
+      fail(VAG_EINVAL, "at least one Dirichlet node or a well perforation with WI > 0 is required");
+    upload_wells(s, w);
     s->mu = props->mu;
     numeric_phase(s);
     s->solved = false;
     s->have_flux = false;
   });
+}
+
+vag_status vag_peaceman_wi(int32_t n, const double *dx, const double *dz, const double *d_f,
+                           const double *lambda_f, const double *r_w, double mu, double *wi_out) {
+  if (n < 0 || (n > 0 && (!dx || !dz || !d_f || !lambda_f || !r_w || !wi_out)) || !(mu > 0.0)) return VAG_EINVAL;
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> wi((size_t)n);
+  for (int32_t i = 0; i < n; ++i) {
+    const double a = dx[i], h = dz[i], w = d_f[i];
+    if (!(a > 0.0) || !(h > 0.0) || !(w > 0.0) || !(lambda_f[i] > 0.0) || !(r_w[i] > 0.0)) return VAG_EINVAL;
+    const double C = (4.0 / 3.0) * (a * h / w + a * w / h + h * w / a);
+    const double D = 0.5 * std::sqrt(a * a + w * w);
+    const double lr = std::log(D / r_w[i]) - two_pi * h / C;   // log(r_0 / r_w)
+    if (!(lr > 0.0)) return VAG_EINVAL;
+    wi[(size_t)i] = two_pi * h * lambda_f[i] / (mu * lr);
+  }
+  std::copy(wi.begin(), wi.end(), wi_out);
+  return VAG_OK;
 }
 
 void vag_system_destroy(vag_system *sys) { destroy_system(sys); }
@@ -603,6 +739,39 @@ vag_status vag_export_fluxes(const vag_system *sys, double *Fcn, double *Fcf, do
     copy_out(s, Fcn, s->Fcn, 8 * (size_t)s->nc, mem);
     copy_out(s, Fcf, s->Fcf, 6 * (size_t)s->nc, mem);
     copy_out(s, Fff, s->Fff, 4 * (size_t)s->nf, mem);
+    VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  });
+}
+
+vag_status vag_export_cells(const vag_system *sys, int32_t *cell_nodes, int8_t *shape, int32_t *ff_nodes, int mem) {
+  if (!sys) return VAG_EINVAL;
+  const System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    check_mem(mem);
+    use_device(s->ctx);
+    if (cell_nodes) copy_out(s, cell_nodes, s->cell_nodes, 8 * (size_t)s->nc, mem);
+    if (ff_nodes) copy_out(s, ff_nodes, s->ff_nodes, 4 * (size_t)s->nf, mem);
+    if (shape) {
+      if (s->cell_shape) {
+        copy_out(s, shape, s->cell_shape, (size_t)s->nc, mem);
+      } else if (mem == VAG_MEM_HOST) {
+        std::memset(shape, topo::HEX, (size_t)s->nc);
+      } else {
+        VAG_CUDA(cudaMemsetAsync(shape, topo::HEX, (size_t)s->nc, s->ctx->stream));
+      }
+    }
+    VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  });
+}
+
+vag_status vag_export_well_rates(const vag_system *sys, double *Fw, int mem) {
+  if (!sys) return VAG_EINVAL;
+  const System *s = &sys->s;
+  return guarded(s->ctx, [&] {
+    check_mem(mem);
+    if (s->n_perf && !Fw) fail(VAG_EINVAL, "null array");
+    use_device(s->ctx);
+    copy_out(s, Fw, s->Fw, (size_t)s->n_perf, mem);
     VAG_CUDA(cudaStreamSynchronize(s->ctx->stream));
   });
 }

@@ -78,7 +78,7 @@ void ctx_free(Ctx *c, void *p) {
 
 void *sys_alloc_bytes(System *s, size_t bytes) {
   Ctx *c = s->ctx;
-  bytes = (bytes + 255) & ~size_t(255);
+  bytes = (std::max<size_t>(bytes, 1) + 255) & ~size_t(255);   // a zero-size array still gets a valid pointer
   if (c->budget && c->in_use + bytes > c->budget)
     fail(VAG_EBUDGET, "device memory budget exceeded (" + std::to_string(c->in_use + bytes) +
                           " > " + std::to_string(c->budget) + " bytes)");

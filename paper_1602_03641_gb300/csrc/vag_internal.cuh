@@ -199,8 +199,19 @@ struct System {
 
   // mesh + data (device)
   double *xyz = nullptr;
-  int *cell_nodes = nullptr;
-  int *ff_nodes = nullptr;
+  int *cell_nodes = nullptr;   // [8 nc] node slots (vag_topo.h), -1 where unused
+  int *ff_nodes = nullptr;     // [4 nf] slot 3 = -1 for a triangle
+  int8_t *cell_shape = nullptr;   // [nc] shape of each cell, nullptr when all are hexahedra
+  int *shape_cells = nullptr;  // [nc] the cells grouped by shape, increasing within a shape
+  int shape_start[5] = {0, 0, 0, 0, 0};   // (host) first entry of each shape in shape_cells
+  bool tri_ff = false;         // some fracture face is a triangle
+  // Peaceman wells (Sec. 5.5): perforated fracture faces
+  int n_perf = 0;
+  int *well_ff = nullptr;      // [n_perf] fracture-face index (distinct)
+  double *well_wi = nullptr, *well_pw = nullptr, *well_q = nullptr, *well_cin = nullptr;   // [n_perf]
+  double *Fw = nullptr;        // [n_perf] rate leaving the face into the well
+  int *ff_perf = nullptr;      // [nf] perforation of each fracture face, or -1
+  int perf_cap = 0;
   int *dir_nodes = nullptr;
   double *dir_vals = nullptr;
   double *lam = nullptr, *lamf = nullptr, *df = nullptr;
@@ -281,15 +292,17 @@ struct System {
   double *Fff = nullptr;       // [4 nf]
   bool have_flux = false;
   double *phi = nullptr;       // [n_cv]
-  double *tdiag = nullptr;     // [n_cv]
-  int *trowptr = nullptr;      // [n_cv+1]
+  double *tdiag = nullptr;     // [n_cv + n_perf]
+  int *trowptr = nullptr;      // [n_cv + n_perf + 1]
   int *tcol = nullptr;         // [nnz_t]
   double *tval = nullptr;      // [nnz_t]
   int64_t t_cap = 0;
-  double *cbuf = nullptr;      // [2 n_cv]
+  double *cbuf = nullptr;      // [2 (n_cv + n_perf)]
   double *dts = nullptr;       // [2 n_sys]: per system dt_max, dt
   cudaGraphExec_t step_graph = nullptr;   // kStepChunk transport steps
   int64_t step_graph_cap = -1;
+  int step_graph_rows = 0;
+  int t_rows = 0;              // rows allocated for tdiag, trowptr and each half of cbuf
   std::vector<double> dts_host;
 
   // timing events
@@ -380,10 +393,13 @@ void trace_mark(cudaStream_t st, const char *label);
 void trace_report(const char *call);
 
 // General polyhedral descriptor (vag_mesh with cell_nodes == NULL) -> the
-// hexahedral fast path: device outputs cell_nodes [8 n_cells] and ff_nodes
-// [4 n_ff] (ids local to the mesh).  VAG_EMESH for a cell that is not a
-// hexahedron, VAG_EINVAL for an offset or id out of range.
-void general_to_hex(Ctx *c, const vag_mesh &m, int mem, int32_t *cell_nodes, int32_t *ff_nodes);
+// padded per-shape numbering (vag_topo.h): device outputs cell_nodes
+// [8 n_cells], ff_nodes [4 n_ff] and cell_shape [n_cells] (ids local to the
+// mesh); *tri_ff is set when some fracture face is a triangle.  Returns the
+// set of shapes seen (bit 1 << shape).  VAG_EMESH for a cell of none of the
+// shapes, VAG_EINVAL for an offset or id out of range.
+unsigned general_to_cells(Ctx *c, const vag_mesh &m, int mem, int32_t *cell_nodes, int32_t *ff_nodes,
+                          int8_t *cell_shape, bool *tri_ff);
 
 // ------------------------------------------------------------- phases -----
 void symbolic_phase(System *s);

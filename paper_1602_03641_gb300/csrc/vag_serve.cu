@@ -19,7 +19,7 @@
 #include <thread>
 #include <vector>
 
-#include "vag_hexmap.h"
+#include "vag_cellmap.h"
 #include "vag_internal.cuh"
 
 namespace {
@@ -31,6 +31,13 @@ struct Req {
   // copies of the caller's inputs
   std::vector<double> xyz, lam, lamf, df, dirv, phim, phif, cbar, c0;
   std::vector<int32_t> cn, ffn, dirn;
+  // the general descriptor, kept as given (validated at submit)
+  bool general = false;
+  int32_t n_cells = 0, n_ff = 0, n_faces = 0;
+  std::vector<int32_t> fptr, fidx, cptr, cidx, ffid;
+  // wells
+  std::vector<int32_t> wff;
+  std::vector<double> wwi, wpw, wq, wcin;
   double mu = 1.0, omega = 0.5, cfl = 0.9, rtol = 1e-8;
   int32_t n_steps = 0, maxit = 1000;
   int precision = VAG_FP64, precond = VAG_PC_JACOBI;
@@ -40,8 +47,8 @@ struct Req {
   bool done = false;
   vag_result res{};
   int32_t nv() const { return (int32_t)(xyz.size() / 3); }
-  int32_t nc() const { return (int32_t)(cn.size() / 8); }
-  int32_t nf() const { return (int32_t)(ffn.size() / 4); }
+  int32_t nc() const { return n_cells; }
+  int32_t nf() const { return n_ff; }
   bool same_settings(const Req &o) const {
     return precision == o.precision && precond == o.precond && rtol == o.rtol && maxit == o.maxit &&
            n_steps == o.n_steps && omega == o.omega && cfl == o.cfl && mu == o.mu;
@@ -89,8 +96,13 @@ void vag_server::run_batch(vag_ctx *ctx, std::vector<std::shared_ptr<Req>> &batc
   std::vector<vag_dirichlet> bcs(n);
   for (int i = 0; i < n; ++i) {
     Req &r = *batch[i];
-    meshes[i] = vag_mesh{r.nv(), r.xyz.data(), r.nc(), r.cn.data(), r.nf(), r.ffn.data()};
-    props[i] = vag_props{r.lam.data(), r.lamf.data(), r.df.data(), r.mu};
+    if (r.general)
+      meshes[i] = vag_mesh{r.nv(), r.xyz.data(), r.nc(), nullptr, r.nf(), nullptr, r.n_faces, r.fptr.data(),
+                           r.fidx.data(), r.cptr.data(), r.cidx.data(), r.ffid.data()};
+    else
+      meshes[i] = vag_mesh{r.nv(), r.xyz.data(), r.nc(), r.cn.data(), r.nf(), r.ffn.data()};
+    props[i] = vag_props{r.lam.data(), r.lamf.data(), r.df.data(), r.mu, (int32_t)r.wff.size(), r.wff.data(),
+                         r.wwi.data(), r.wpw.data(), r.wq.data(), r.wcin.data()};
     bcs[i] = vag_dirichlet{(int32_t)r.dirn.size(), r.dirn.data(), r.dirv.data()};
   }
   const Req &r0 = *batch[0];
@@ -239,35 +251,56 @@ vag_status vag_server_submit(vag_server *s, const vag_request *q, uint64_t *tick
   if (!s || !q || !ticket) return VAG_EINVAL;
   const vag_mesh &m = q->mesh;
   const bool general = !m.cell_nodes;
-  if (m.n_nodes <= 0 || m.n_cells <= 0 || m.n_ff < 0 || q->bc.n_dir <= 0 || !(q->props.mu > 0.0) ||
+  const vag_props &pp = q->props;
+  if (pp.n_perf < 0 || (pp.n_perf > 0 && (!pp.well_ff || !pp.well_wi || !pp.well_pw || !pp.well_q || !pp.well_cin)))
+    return VAG_EINVAL;
+  bool level = q->bc.n_dir > 0;   // the pressure level is fixed by a Dirichlet node or a producing well
+  for (int32_t i = 0; i < pp.n_perf; ++i) level = level || pp.well_wi[i] > 0.0;
+  if (m.n_nodes <= 0 || m.n_cells <= 0 || m.n_ff < 0 || q->bc.n_dir < 0 || !level || !(q->props.mu > 0.0) ||
       !m.xyz || (!general && m.n_ff && !m.ff_nodes) ||
       (general && (m.n_faces <= 0 || !m.face_node_ptr || !m.face_node_idx || !m.cell_face_ptr ||
                    !m.cell_face_idx || (m.n_ff && !m.ff_face_ids))) ||
       !q->props.lambda_m ||
-      (m.n_ff && (!q->props.lambda_f || !q->props.d_f)) || !q->bc.nodes || !q->bc.values || q->n_steps < 0 ||
-      (q->n_steps > 0 && (!q->phi_m || (m.n_ff && !q->phi_f) || !q->cbar)) || !(q->rtol > 0.0) || q->maxit <= 0)
+      (m.n_ff && (!q->props.lambda_f || !q->props.d_f)) || (q->bc.n_dir && (!q->bc.nodes || !q->bc.values)) ||
+      q->n_steps < 0 || (q->n_steps > 0 && (!q->phi_m || (m.n_ff && !q->phi_f) || (q->bc.n_dir && !q->cbar))) || !(q->rtol > 0.0) || q->maxit <= 0)
     return VAG_EINVAL;
   auto r = std::make_shared<Req>();
   const size_t nv = m.n_nodes, nc = m.n_cells, nf = m.n_ff, nd = q->bc.n_dir;
   r->xyz.assign(m.xyz, m.xyz + 3 * nv);
+  r->n_cells = m.n_cells;
+  r->n_ff = m.n_ff;
   if (!general) {
     r->cn.assign(m.cell_nodes, m.cell_nodes + 8 * nc);
     if (nf) r->ffn.assign(m.ff_nodes, m.ff_nodes + 4 * nf);
-  } else {   // the general descriptor, turned into the hexahedral fast path here
+  } else {   // the general descriptor: validated here (vag_cellmap.h), converted on the device
     const int64_t flen = m.face_node_ptr[m.n_faces], clen = m.cell_face_ptr[m.n_cells];
     if (flen < 0 || clen < 0) return VAG_EINVAL;
-    r->cn.resize(8 * nc);
-    r->ffn.resize(4 * nf);
+    int32_t out[8];
+    int sh = 0;
     for (size_t K = 0; K < nc; ++K) {
-      const int e = vag::hex_from_faces(m.face_node_ptr, m.face_node_idx, flen, m.cell_face_ptr, m.cell_face_idx,
-                                        clen, m.n_faces, m.n_nodes, (int32_t)K, r->cn.data() + 8 * K);
-      if (e != vag::HEXMAP_OK) return e == vag::HEXMAP_NOT_HEX ? VAG_EMESH : VAG_EINVAL;
+      const int e = vag::cell_from_faces(m.face_node_ptr, m.face_node_idx, flen, m.cell_face_ptr, m.cell_face_idx,
+                                         clen, m.n_faces, m.n_nodes, (int32_t)K, out, &sh);
+      if (e != vag::HEXMAP_OK) return e == vag::HEXMAP_BAD_INDEX ? VAG_EINVAL : VAG_EMESH;
     }
     for (size_t i = 0; i < nf; ++i) {
-      const int e = vag::quad_of_face(m.face_node_ptr, m.face_node_idx, flen, m.n_faces, m.n_nodes,
-                                      m.ff_face_ids[i], r->ffn.data() + 4 * i);
-      if (e != vag::HEXMAP_OK) return e == vag::HEXMAP_NOT_HEX ? VAG_EMESH : VAG_EINVAL;
+      const int e = vag::face_nodes_of(m.face_node_ptr, m.face_node_idx, flen, m.n_faces, m.n_nodes,
+                                       m.ff_face_ids[i], out);
+      if (e != vag::HEXMAP_OK) return e == vag::HEXMAP_BAD_INDEX ? VAG_EINVAL : VAG_EMESH;
     }
+    r->general = true;
+    r->n_faces = m.n_faces;
+    r->fptr.assign(m.face_node_ptr, m.face_node_ptr + m.n_faces + 1);
+    r->fidx.assign(m.face_node_idx, m.face_node_idx + flen);
+    r->cptr.assign(m.cell_face_ptr, m.cell_face_ptr + m.n_cells + 1);
+    r->cidx.assign(m.cell_face_idx, m.cell_face_idx + clen);
+    r->ffid.assign(m.ff_face_ids, m.ff_face_ids + nf);
+  }
+  if (pp.n_perf > 0) {
+    r->wff.assign(pp.well_ff, pp.well_ff + pp.n_perf);
+    r->wwi.assign(pp.well_wi, pp.well_wi + pp.n_perf);
+    r->wpw.assign(pp.well_pw, pp.well_pw + pp.n_perf);
+    r->wq.assign(pp.well_q, pp.well_q + pp.n_perf);
+    r->wcin.assign(pp.well_cin, pp.well_cin + pp.n_perf);
   }
   r->lam.assign(q->props.lambda_m, q->props.lambda_m + 6 * nc);
   if (nf) {

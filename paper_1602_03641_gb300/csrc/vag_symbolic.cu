@@ -8,7 +8,7 @@
 #include <algorithm>
 
 #include "vag_internal.cuh"
-#include "vag_hex.cuh"
+#include "vag_topo.h"
 
 namespace vag {
 namespace {
@@ -43,26 +43,38 @@ __global__ void k_mark_dirichlet(int nd, const int *__restrict__ dir_nodes, int 
   if (old != -1) flag(status, ST_DUP_DIRICHLET);
 }
 
-__global__ void k_check_cells(int nc, const int *__restrict__ cn, int nv, int *n2c_cnt, int *status) {
+// Node slot l of cell K holds a node id when l < n_nodes(shape) and -1
+// otherwise.
+__global__ void k_check_cells(int nc, const int8_t *__restrict__ shape, const int *__restrict__ cn, int nv,
+                              int *n2c_cnt, int *status) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)nc * 8) return;
+  const int K = (int)(i >> 3), l = (int)(i & 7);
+  const int sh = shape ? shape[K] : topo::HEX;
   int s = cn[i];
+  if (sh < 0 || sh >= topo::N_SHAPES) { flag(status, ST_BAD_INDEX); return; }
+  if (l >= topo::n_nodes(sh)) {
+    if (s != -1) flag(status, ST_BAD_INDEX);
+    return;
+  }
   if (s < 0 || s >= nv) { flag(status, ST_BAD_INDEX); return; }
   atomicAdd(&n2c_cnt[s], 1);
 }
 
-__global__ void k_ff_prep(int nf, const int *__restrict__ ffn, int nv, int *ffs, int *node_isfrac,
+__global__ void k_ff_prep(int nf, const int *__restrict__ ffn, int nv, bool tri_ok, int *ffs, int *node_isfrac,
                           int *n2f_cnt, int *status) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
   int a = ffn[4 * f], b = ffn[4 * f + 1], c = ffn[4 * f + 2], d = ffn[4 * f + 3];
-  if (a < 0 || a >= nv || b < 0 || b >= nv || c < 0 || c >= nv || d < 0 || d >= nv) {
+  // a quadrilateral, or a triangle with d = -1 (general meshes only)
+  const bool tri = d == -1 && tri_ok;
+  if (a < 0 || a >= nv || b < 0 || b >= nv || c < 0 || c >= nv || (!tri && (d < 0 || d >= nv))) {
     flag(status, ST_BAD_INDEX);
     a = b = c = d = -1;
   } else {
-    node_isfrac[a] = 1; node_isfrac[b] = 1; node_isfrac[c] = 1; node_isfrac[d] = 1;
-    atomicAdd(&n2f_cnt[a], 1); atomicAdd(&n2f_cnt[b], 1);
-    atomicAdd(&n2f_cnt[c], 1); atomicAdd(&n2f_cnt[d], 1);
+    node_isfrac[a] = 1; node_isfrac[b] = 1; node_isfrac[c] = 1;
+    atomicAdd(&n2f_cnt[a], 1); atomicAdd(&n2f_cnt[b], 1); atomicAdd(&n2f_cnt[c], 1);
+    if (!tri) { node_isfrac[d] = 1; atomicAdd(&n2f_cnt[d], 1); }
   }
   sort4(a, b, c, d);
   ffs[4 * f] = a; ffs[4 * f + 1] = b; ffs[4 * f + 2] = c; ffs[4 * f + 3] = d;
@@ -72,7 +84,7 @@ __global__ void k_ff_insert(int nf, const int *__restrict__ ffs, int *table, uin
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
   int a = ffs[4 * f], b = ffs[4 * f + 1], c = ffs[4 * f + 2], d = ffs[4 * f + 3];
-  if (a < 0) return;
+  if (b < 0) return;   // rejected face (a = -1 is a triangle's padding after sorting)
   uint32_t h = hash4(a, b, c, d) & mask;
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     int old = atomicCAS(&table[h], -1, f);
@@ -86,16 +98,18 @@ __global__ void k_ff_insert(int nf, const int *__restrict__ ffs, int *table, uin
   flag(status, ST_HASH_FULL);
 }
 
-__global__ void k_cell_face_lookup(int nc, const int *__restrict__ cn, const int *__restrict__ ffs,
-                                   const int *__restrict__ table, uint32_t mask, int nf, int *cell_ff,
-                                   int *ff_cnt, int *ff_cells, int *ff_lface, int *status) {
+__global__ void k_cell_face_lookup(int nc, const int8_t *__restrict__ shape, const int *__restrict__ cn,
+                                   const int *__restrict__ ffs, const int *__restrict__ table, uint32_t mask, int nf,
+                                   int *cell_ff, int *ff_cnt, int *ff_cells, int *ff_lface, int *status) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)nc * 6) return;
   int K = (int)(i / 6), lf = (int)(i % 6);
+  const int sh = shape ? shape[K] : topo::HEX;
   int res = -1;
-  if (nf > 0) {
-    int a = cn[8 * K + hex::face(lf, 0)], b = cn[8 * K + hex::face(lf, 1)];
-    int c = cn[8 * K + hex::face(lf, 2)], d = cn[8 * K + hex::face(lf, 3)];
+  if (nf > 0 && lf < topo::n_faces(sh)) {
+    const int t3 = topo::face(sh, lf, 3);
+    int a = cn[8 * K + topo::face(sh, lf, 0)], b = cn[8 * K + topo::face(sh, lf, 1)];
+    int c = cn[8 * K + topo::face(sh, lf, 2)], d = t3 >= 0 ? cn[8 * K + t3] : -1;
     sort4(a, b, c, d);
     uint32_t h = hash4(a, b, c, d) & mask;
     for (uint32_t probe = 0; probe <= mask; ++probe) {
@@ -131,6 +145,18 @@ __global__ void k_ff_finish(int nf, const int *__restrict__ ff_cnt, int *ff_cell
     int t = ff_cells[2 * f]; ff_cells[2 * f] = ff_cells[2 * f + 1]; ff_cells[2 * f + 1] = t;
     t = ff_lface[2 * f]; ff_lface[2 * f] = ff_lface[2 * f + 1]; ff_lface[2 * f + 1] = t;
   }
+}
+
+__global__ void k_shape_flag(int nc, const int8_t *__restrict__ shape, int sh, int *flagv) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K < nc) flagv[K] = shape[K] == sh;
+}
+
+// cells of shape sh at out[scan[K]] (scan: exclusive scan of the flags)
+__global__ void k_shape_fill(int nc, const int8_t *__restrict__ shape, int sh, const int *__restrict__ scan,
+                             int *out) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K < nc && shape[K] == sh) out[scan[K]] = K;
 }
 
 __global__ void k_fc_flag(int nc, const int *__restrict__ cell_ff, int *flagv) {
@@ -242,7 +268,7 @@ __device__ void row_add_cell(const PatView &p, RowSet &rs, int K) {
 #pragma unroll
   for (int l = 0; l < 8; ++l) {
     int s = p.cn[8 * K + l];
-    if (p.node_dir[s] < 0) rs.insert(s);
+    if (s >= 0 && p.node_dir[s] < 0) rs.insert(s);
   }
 #pragma unroll
   for (int lf = 0; lf < 6; ++lf) {
@@ -256,7 +282,7 @@ __device__ void row_add_ff(const PatView &p, RowSet &rs, int f) {
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     int s = p.ffn[4 * f + t];
-    if (p.node_dir[s] < 0) rs.insert(s);
+    if (s >= 0 && p.node_dir[s] < 0) rs.insert(s);
   }
 }
 
@@ -345,9 +371,11 @@ void symbolic_phase(System *s) {
   VAG_CUDA(cudaMemsetAsync(ff_cnt, 0, sizeof(int) * (size_t)(nf > 0 ? nf : 1), st));
 
   k_mark_dirichlet<<<grid_for(nd, TB), TB, 0, st>>>(nd, s->dir_nodes, nv, s->node_dir, s->status); note_launches(1);
-  k_check_cells<<<grid_for((int64_t)nc * 8, TB), TB, 0, st>>>(nc, s->cell_nodes, nv, n2c_cnt, s->status); note_launches(1);
+  k_check_cells<<<grid_for((int64_t)nc * 8, TB), TB, 0, st>>>(nc, s->cell_shape, s->cell_nodes, nv, n2c_cnt,
+                                                               s->status); note_launches(1);
   if (nf) {
-    k_ff_prep<<<grid_for(nf, TB), TB, 0, st>>>(nf, s->ff_nodes, nv, ffs, s->node_isfrac, n2f_cnt, s->status); note_launches(1);
+    k_ff_prep<<<grid_for(nf, TB), TB, 0, st>>>(nf, s->ff_nodes, nv, s->tri_ff, ffs, s->node_isfrac, n2f_cnt,
+                                               s->status); note_launches(1);
     k_ff_insert<<<grid_for(nf, TB), TB, 0, st>>>(nf, ffs, table, H - 1, s->status); note_launches(1);
   }
   VAG_CHECK_LAUNCH();
@@ -359,12 +387,29 @@ void symbolic_phase(System *s) {
   if (st0 & ST_HASH_FULL) fail(VAG_EMESH, "fracture-face table overflow");
 
   k_cell_face_lookup<<<grid_for((int64_t)nc * 6, TB), TB, 0, st>>>(
-      nc, s->cell_nodes, ffs, table, H - 1, nf, s->cell_ff, ff_cnt, s->ff_cells, s->ff_lface, s->status); note_launches(1);
+      nc, s->cell_shape, s->cell_nodes, ffs, table, H - 1, nf, s->cell_ff, ff_cnt, s->ff_cells, s->ff_lface,
+      s->status); note_launches(1);
   if (nf) {
     k_ff_finish<<<grid_for(nf, TB), TB, 0, st>>>(nf, ff_cnt, s->ff_cells, s->ff_lface, s->status);
     note_launches(1);
   }
   VAG_CHECK_LAUNCH();
+
+  // cells grouped by shape (general meshes with some non-hexahedral cell)
+  if (s->cell_shape) {
+    s->shape_cells = sys_alloc<int>(s, nc);
+    s->shape_start[0] = 0;
+    for (int sh = 0; sh < topo::N_SHAPES; ++sh) {
+      k_shape_flag<<<grid_for(nc, TB), TB, 0, st>>>(nc, s->cell_shape, sh, flagv);
+      const int cnt = scan_exclusive(flagv, scanv, nc, st);
+      k_shape_fill<<<grid_for(nc, TB), TB, 0, st>>>(nc, s->cell_shape, sh, scanv,
+                                                    s->shape_cells + s->shape_start[sh]);
+      note_launches(2);
+      s->shape_start[sh + 1] = s->shape_start[sh] + cnt;
+    }
+    VAG_CHECK_LAUNCH();
+    if (s->shape_start[topo::N_SHAPES] != nc) fail(VAG_EMESH, "a cell has no known shape");
+  }
 
   // fracture cells
   k_fc_flag<<<grid_for(nc, TB), TB, 0, st>>>(nc, s->cell_ff, flagv); note_launches(1);

@@ -16,9 +16,16 @@
 //                Dirichlet rows keep c = cbar (d = 1, no inflow).
 //  k_cfl         Eq. (eq_CFL): min over non-Dirichlet CVs of phi / outflow.
 //  k_step        c' = d c + W c (one thread per control volume).
+//
+// Wells (Sec. 5.5): perforation p exchanges the rate Fw[p] =
+// WI (u_sigma - p_w) - q between its fracture face and the well.  The well
+// side is one extra state entry n_cv + p held at the injected concentration
+// (a fixed row like a Dirichlet node), so a production rate is outflow of
+// the face and an injection rate an inflow edge from that entry; k_step is
+// unchanged.  The extra entries live only in the library's buffers.
 #include "vag_internal.cuh"
 #include "vag_reduce.cuh"
-#include "vag_hex.cuh"
+#include "vag_topo.h"
 
 namespace vag {
 namespace {
@@ -26,7 +33,7 @@ namespace {
 constexpr int TB = 256;
 
 __device__ __forceinline__ double mcK(const double *Mc, int nc, int i, int j, int K) {
-  return Mc[(size_t)hex::pidx(i, j) * nc + K];
+  return Mc[(size_t)topo::pidx(i, j) * nc + K];
 }
 __device__ __forceinline__ double mfcK(const double *Mfc, int n_fc, int lf, int k, int fi) {
   return Mfc[(size_t)(lf * 6 + k) * n_fc + fi];
@@ -39,7 +46,10 @@ __global__ void k_recover(int nc, int nv, const int *__restrict__ cn, const int 
   if (K >= nc) return;
   double s = 0.0;
 #pragma unroll
-  for (int b = 0; b < 8; ++b) s = fma(mcK(Mc, nc, 0, 1 + b, K), u[cn[8 * (size_t)K + b]], s);
+  for (int b = 0; b < 8; ++b) {
+    const int nb = cn[8 * (size_t)K + b];
+    if (nb >= 0) s = fma(mcK(Mc, nc, 0, 1 + b, K), u[nb], s);
+  }
   const int fi = fc_index[K];
   if (fi >= 0) {
     for (int lf = 0; lf < 6; ++lf) {
@@ -50,16 +60,22 @@ __global__ void k_recover(int nc, int nv, const int *__restrict__ cn, const int 
   u[(size_t)nv + nf + K] = -s / mcK(Mc, nc, 0, 0, K);
 }
 
-__global__ void k_cell_flux(int nc, int nv, int nf, const int *__restrict__ cn, const int *__restrict__ cell_ff,
-                            const int *__restrict__ fc_index, int n_fc, const double *__restrict__ Mc,
-                            const double *__restrict__ Mfc, const double *__restrict__ u, double *__restrict__ Fcn,
-                            double *__restrict__ Fcf) {
+// GEN: cells of any shape (shape[K]); otherwise hexahedra only.
+template <bool GEN>
+__global__ void k_cell_flux(int nc, int nv, int nf, const int8_t *__restrict__ shape, const int *__restrict__ cn,
+                            const int *__restrict__ cell_ff, const int *__restrict__ fc_index, int n_fc,
+                            const double *__restrict__ Mc, const double *__restrict__ Mfc,
+                            const double *__restrict__ u, double *__restrict__ Fcn, double *__restrict__ Fcf) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   if (K >= nc) return;
+  const int sh = GEN ? shape[K] : topo::HEX;
   const double uK = u[(size_t)nv + nf + K];
   double du[8];
 #pragma unroll
-  for (int b = 0; b < 8; ++b) du[b] = uK - u[cn[8 * (size_t)K + b]];
+  for (int b = 0; b < 8; ++b) {
+    const int nb = cn[8 * (size_t)K + b];
+    du[b] = (!GEN || nb >= 0) ? uK - u[nb] : 0.0;
+  }
   const int fi = fc_index[K];
   double dus[6];
   int ffid[6];
@@ -76,7 +92,7 @@ __global__ void k_cell_flux(int nc, int nv, int nf, const int *__restrict__ cn, 
     if (fi >= 0) {
 #pragma unroll
       for (int lf = 0; lf < 6; ++lf) {
-        const int t = hex::pos_on_face(lf, a);
+        const int t = topo::pos_on_face(sh, lf, a);
         if (t >= 0 && ffid[lf] >= 0) F = fma(mfcK(Mfc, n_fc, lf, 2 + t, fi), dus[lf], F);
       }
     }
@@ -87,7 +103,10 @@ __global__ void k_cell_flux(int nc, int nv, int nf, const int *__restrict__ cn, 
     double F = 0.0;
     if (ffid[lf] >= 0) {
 #pragma unroll
-      for (int t = 0; t < 4; ++t) F = fma(mfcK(Mfc, n_fc, lf, 2 + t, fi), du[hex::face(lf, t)], F);
+      for (int t = 0; t < 4; ++t) {
+        const int b = topo::face(sh, lf, t);
+        if (b >= 0) F = fma(mfcK(Mfc, n_fc, lf, 2 + t, fi), du[b], F);
+      }
       F = fma(mfcK(Mfc, n_fc, lf, 0, fi), dus[lf], F);
     }
     Fcf[6 * (size_t)K + lf] = F;
@@ -101,7 +120,10 @@ __global__ void k_ff_flux(int nf, int nv, const int *__restrict__ ffn, const dou
   const double us = u[nv + f];
   double du[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) du[t] = us - u[ffn[4 * (size_t)f + t]];
+  for (int t = 0; t < 4; ++t) {
+    const int nb = ffn[4 * (size_t)f + t];   // -1: a triangle's unused slot
+    du[t] = nb >= 0 ? us - u[nb] : 0.0;
+  }
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     double F = 0.0;
@@ -111,9 +133,22 @@ __global__ void k_ff_flux(int nf, int nv, const int *__restrict__ ffn, const dou
   }
 }
 
+// Fw[p] = WI (u_sigma - p_w) - q: the rate leaving the perforated face into
+// the well.
+__global__ void k_well_flux(int n_perf, int nv, const int *__restrict__ ff, const double *__restrict__ wi,
+                            const double *__restrict__ pw, const double *__restrict__ q,
+                            const double *__restrict__ u, double *__restrict__ Fw) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_perf) return;
+  Fw[p] = fma(wi[p], u[nv + ff[p]] - pw[p], -q[p]);
+}
+
 struct TView {
   int nv, nf, nc;
+  const int8_t *shape;   // nullptr: every cell is a hexahedron
   const int *cn, *ffn, *cell_ff, *ff_cells, *ff_lface, *node_dir, *node_isfrac;
+  const int *ff_perf;    // [nf] perforation of each fracture face or -1 (nullptr: no wells)
+  const double *Fw;      // [n_perf]
   const int *n2c_ptr, *n2c, *n2f_ptr, *n2f;
   const double *cvol, *ffarea, *df, *phi_m, *phi_f;
   const double *Fcn, *Fcf, *Fff;
@@ -128,32 +163,42 @@ __global__ void k_porous(TView t, double *__restrict__ phi, int *status) {
   if (mu < t.nv) {
     const int s = mu;
     if (t.node_dir[s] >= 0) { phi[mu] = 0.0; return; }
+    // alpha = omega / |V_sigma| (fracture nodes) or omega / |V_K| (others)
     if (t.node_isfrac[s]) {
       for (int e = t.n2f_ptr[s]; e < t.n2f_ptr[s + 1]; ++e) {
         const int f = t.n2f[e] >> 2;
-        p += (t.omega * 0.25) * t.df[f] * t.ffarea[f] * t.phi_f[f];
+        const int q = t.ffn[4 * (size_t)f + 3] < 0 ? 3 : 4;
+        p += (t.omega / q) * t.df[f] * t.ffarea[f] * t.phi_f[f];
       }
     } else {
       for (int e = t.n2c_ptr[s]; e < t.n2c_ptr[s + 1]; ++e) {
         const int K = t.n2c[e] >> 3;
-        p += (t.omega * 0.125) * t.cvol[K] * t.phi_m[K];
+        const int nK = topo::n_nodes(t.shape ? t.shape[K] : topo::HEX);
+        p += (t.omega / nK) * t.cvol[K] * t.phi_m[K];
       }
     }
   } else if (mu < t.nv + t.nf) {
     const int f = mu - t.nv;
-    int cnt = 0;
+    int cnt = 0, q = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) cnt += t.node_dir[t.ffn[4 * (size_t)f + q]] < 0;
-    p = (1.0 - t.omega * 0.25 * cnt) * t.df[f] * t.ffarea[f] * t.phi_f[f];
+    for (int k = 0; k < 4; ++k) {
+      const int s = t.ffn[4 * (size_t)f + k];
+      if (s < 0) continue;
+      ++q;
+      cnt += t.node_dir[s] < 0;
+    }
+    p = (1.0 - (t.omega / q) * cnt) * t.df[f] * t.ffarea[f] * t.phi_f[f];
   } else {
     const int K = mu - t.nv - t.nf;
+    const int nK = topo::n_nodes(t.shape ? t.shape[K] : topo::HEX);
     int cnt = 0;
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
       const int s = t.cn[8 * (size_t)K + l];
+      if (s < 0) continue;
       cnt += (t.node_dir[s] < 0) && !t.node_isfrac[s];
     }
-    p = (1.0 - t.omega * 0.125 * cnt) * t.cvol[K] * t.phi_m[K];
+    p = (1.0 - (t.omega / nK) * cnt) * t.cvol[K] * t.phi_m[K];
   }
   if (!(p > 0.0)) atomicOr(status, ST_NONPOSITIVE);
   phi[mu] = p;
@@ -177,16 +222,26 @@ __device__ __forceinline__ void for_edges(const TView &t, int mu, Fn &&fn) {
   } else if (mu < t.nv + t.nf) {
     const int f = mu - t.nv;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) fn(-t.Fff[4 * (size_t)f + q], t.ffn[4 * (size_t)f + q]);
+    for (int q = 0; q < 4; ++q) {
+      const int s = t.ffn[4 * (size_t)f + q];
+      if (s >= 0) fn(-t.Fff[4 * (size_t)f + q], s);
+    }
     for (int c = 0; c < 2; ++c) {                                // F_{K,sigma} > 0: K -> sigma
       const int K = t.ff_cells[2 * f + c];
       if (K < 0) continue;
       fn(t.Fcf[6 * (size_t)K + t.ff_lface[2 * f + c]], t.nv + t.nf + K);
     }
+    if (t.ff_perf) {                                             // Fw > 0: sigma -> well
+      const int p = t.ff_perf[f];
+      if (p >= 0) fn(-t.Fw[p], t.nv + t.nf + t.nc + p);
+    }
   } else {
     const int K = mu - t.nv - t.nf;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) fn(-t.Fcn[8 * (size_t)K + a], t.cn[8 * (size_t)K + a]);
+    for (int a = 0; a < 8; ++a) {
+      const int s = t.cn[8 * (size_t)K + a];
+      if (s >= 0) fn(-t.Fcn[8 * (size_t)K + a], s);
+    }
 #pragma unroll
     for (int lf = 0; lf < 6; ++lf) {
       const int f = t.cell_ff[6 * (size_t)K + lf];
@@ -195,14 +250,18 @@ __device__ __forceinline__ void for_edges(const TView &t, int mu, Fn &&fn) {
   }
 }
 
-__device__ __forceinline__ bool is_dir(const TView &t, int mu) { return mu < t.nv && t.node_dir[mu] >= 0; }
+// rows held fixed: Dirichlet nodes and the wells' entries past the n_cv
+// control volumes
+__device__ __forceinline__ bool is_dir(const TView &t, int mu) {
+  return (mu < t.nv && t.node_dir[mu] >= 0) || mu >= t.nv + t.nf + t.nc;
+}
 
 // Per CV: number of inflow edges and the CFL ratio phi / outflow; the ratio
 // is min-reduced per system with atomicMin on the bit pattern of a positive
 // double (order-independent, hence deterministic).
-__global__ void __launch_bounds__(TB) k_map_count(TView t, const double *__restrict__ phi, const int *__restrict__ cv_sys,
-                                                  int *__restrict__ cnt, unsigned long long *dt_bits) {
-  const int n = t.nv + t.nf + t.nc;
+__global__ void __launch_bounds__(TB) k_map_count(TView t, int n, const double *__restrict__ phi,
+                                                  const int *__restrict__ cv_sys, int *__restrict__ cnt,
+                                                  unsigned long long *dt_bits) {
   const int mu = blockIdx.x * TB + threadIdx.x;
   if (mu >= n) return;
   if (is_dir(t, mu)) { cnt[mu] = 0; return; }
@@ -230,10 +289,9 @@ __global__ void k_pick_dt(int n_sys, const unsigned long long *__restrict__ dt_b
   dts[2 * g + 1] = h;
 }
 
-__global__ void k_map_fill(TView t, const double *__restrict__ phi, const int *__restrict__ cv_sys,
+__global__ void k_map_fill(TView t, int n, const double *__restrict__ phi, const int *__restrict__ cv_sys,
                            const int *__restrict__ rowptr, const double *__restrict__ dts, double *__restrict__ diag,
                            int *__restrict__ col, double *__restrict__ w) {
-  const int n = t.nv + t.nf + t.nc;
   const int mu = blockIdx.x * blockDim.x + threadIdx.x;
   if (mu >= n) return;
   if (is_dir(t, mu)) { diag[mu] = 1.0; return; }
@@ -309,7 +367,7 @@ __global__ void k_set_dir(int nd, const int *__restrict__ dn, const double *__re
 double time_transport_step(System *s, int reps) {
   if (!s->trowptr || !s->cbuf || !s->tdiag) fail(VAG_EINVAL, "no upwind map: run vag_transport first");
   cudaStream_t st = s->ctx->stream;
-  const int n = s->n_cv;
+  const int n = s->n_cv + s->n_perf;
   const int gs = grid_for(n, TB);
   double *a = s->cbuf, *b = s->cbuf + n;
   auto step = [&](const double *c, double *cn) {
@@ -339,10 +397,22 @@ void recover_cells_and_fluxes(System *s) {
   }
   k_recover<<<grid_for(s->nc, TB), TB, 0, st>>>(s->nc, s->nv, s->cell_nodes, s->cell_ff, s->fc_index, s->n_fc,
                                                 s->Mc, s->Mfc, s->u, s->nf); note_launches(1);
-  k_cell_flux<<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, s->nv, s->nf, s->cell_nodes, s->cell_ff, s->fc_index,
-                                                    s->n_fc, s->Mc, s->Mfc, s->u, s->Fcn, s->Fcf); note_launches(1);
+  if (s->cell_shape)
+    k_cell_flux<true><<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, s->nv, s->nf, s->cell_shape, s->cell_nodes,
+                                                            s->cell_ff, s->fc_index, s->n_fc, s->Mc, s->Mfc, s->u,
+                                                            s->Fcn, s->Fcf);
+  else
+    k_cell_flux<false><<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, s->nv, s->nf, nullptr, s->cell_nodes,
+                                                             s->cell_ff, s->fc_index, s->n_fc, s->Mc, s->Mfc, s->u,
+                                                             s->Fcn, s->Fcf);
+  note_launches(1);
   if (s->nf) {
     k_ff_flux<<<grid_for(s->nf, TB), TB, 0, st>>>(s->nf, s->nv, s->ff_nodes, s->Mff, s->u, s->Fff);
+    note_launches(1);
+  }
+  if (s->n_perf) {
+    k_well_flux<<<grid_for(s->n_perf, TB), TB, 0, st>>>(s->n_perf, s->nv, s->well_ff, s->well_wi, s->well_pw,
+                                                         s->well_q, s->u, s->Fw);
     note_launches(1);
   }
   VAG_CHECK_LAUNCH();
@@ -354,35 +424,39 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
                    const double *phi_m, const double *phi_f, const double *cbar) {
   cudaStream_t st = s->ctx->stream;
   const int n = s->n_cv;
+  const int nt = n + s->n_perf;   // rows of the step: control volumes, then the wells' entries
   const int ns = s->seg.n_sys;
   if (!s->phi) {
     s->phi = sys_alloc<double>(s, n);
-    s->tdiag = sys_alloc<double>(s, n);
-    s->trowptr = sys_alloc<int>(s, (size_t)n + 1);
-    s->cbuf = sys_alloc<double>(s, 2 * (size_t)n);
     s->dts = sys_alloc<double>(s, 2 * (size_t)ns);
     s->seg.cv_sys = sys_alloc<int>(s, n);
     k_cv_sys<<<grid_for(n, TB), TB, 0, st>>>(s->nv, s->nf, s->nc, ns, s->seg.d_node_start, s->seg.d_ff_start,
                                              s->seg.d_cell_start, s->seg.cv_sys);
     note_launches(1);
   }
-  TView t{s->nv, s->nf, s->nc, s->cell_nodes, s->ff_nodes, s->cell_ff, s->ff_cells, s->ff_lface,
-          s->node_dir, s->node_isfrac, s->n2c_ptr, s->n2c, s->n2f_ptr, s->n2f, s->cvol, s->ffarea, s->df,
-          phi_m, phi_f, s->Fcn, s->Fcf, s->Fff, o->omega};
+  if (nt > s->t_rows) {
+    s->tdiag = sys_alloc<double>(s, nt);
+    s->trowptr = sys_alloc<int>(s, (size_t)nt + 1);
+    s->cbuf = sys_alloc<double>(s, 2 * (size_t)nt);
+    s->t_rows = nt;
+  }
+  TView t{s->nv, s->nf, s->nc, s->cell_shape, s->cell_nodes, s->ff_nodes, s->cell_ff, s->ff_cells, s->ff_lface,
+          s->node_dir, s->node_isfrac, s->n_perf ? s->ff_perf : nullptr, s->Fw, s->n2c_ptr, s->n2c, s->n2f_ptr,
+          s->n2f, s->cvol, s->ffarea, s->df, phi_m, phi_f, s->Fcn, s->Fcf, s->Fff, o->omega};
   VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   k_porous<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->status);
   note_launches(1);
   int *cnt;
   unsigned long long *dt_bits;
-  VAG_CUDA(cudaMallocAsync(&cnt, sizeof(int) * ((size_t)n + 1), st));
+  VAG_CUDA(cudaMallocAsync(&cnt, sizeof(int) * ((size_t)nt + 1), st));
   VAG_CUDA(cudaMallocAsync(&dt_bits, sizeof(unsigned long long) * ns, st));
   VAG_CUDA(cudaMemsetAsync(dt_bits, 0x7f, sizeof(unsigned long long) * ns, st));   // > every finite ratio
-  k_map_count<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->seg.cv_sys, cnt, dt_bits);
+  k_map_count<<<grid_for(nt, TB), TB, 0, st>>>(t, nt, s->phi, s->seg.cv_sys, cnt, dt_bits);
   note_launches(1);
   k_pick_dt<<<grid_for(ns, TB), TB, 0, st>>>(ns, dt_bits, s->dts, o->cfl, o->dt);
   note_launches(1);
   VAG_CHECK_LAUNCH();
-  const int64_t nnz_t = scan_exclusive(cnt, s->trowptr, n, st);
+  const int64_t nnz_t = scan_exclusive(cnt, s->trowptr, nt, st);
   VAG_CUDA(cudaFreeAsync(cnt, st));
   VAG_CUDA(cudaFreeAsync(dt_bits, st));
   if (read_status(s) & ST_NONPOSITIVE) fail(VAG_EINVAL, "a control volume has a non-positive porous volume");
@@ -393,32 +467,34 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     s->t_cap = nnz_t;
   }
   s->nnz_t = nnz_t;
-  k_map_fill<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->seg.cv_sys, s->trowptr, s->dts, s->tdiag, s->tcol,
-                                             s->tval);
+  k_map_fill<<<grid_for(nt, TB), TB, 0, st>>>(t, nt, s->phi, s->seg.cv_sys, s->trowptr, s->dts, s->tdiag, s->tcol,
+                                              s->tval);
   note_launches(1);
-  // c^0 with the Dirichlet values
-  double *c0 = s->cbuf, *c1 = s->cbuf + n;
+  // c^0 with the Dirichlet values and the injected concentrations
+  double *c0 = s->cbuf, *c1 = s->cbuf + nt;
   VAG_CUDA(cudaMemcpyAsync(c0, c_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  if (s->n_perf)
+    VAG_CUDA(cudaMemcpyAsync(c0 + n, s->well_cin, sizeof(double) * s->n_perf, cudaMemcpyDeviceToDevice, st));
   k_set_dir<<<grid_for(s->nd, TB), TB, 0, st>>>(s->nd, s->dir_nodes, cbar, c0);
   note_launches(1);
   VAG_CHECK_LAUNCH();
   trace_mark(st, "porous volumes + CFL + upwind map");
   VAG_CUDA(cudaEventRecord(s->ev0, st));
-  const int gs = grid_for(n, TB);
+  const int gs = grid_for(nt, TB);
   // steps in CUDA graphs of kStepChunk launches (an even count: the chunk
   // starts and ends in the same buffer), the remainder launched directly
   constexpr int kStepChunk = 20;
   const int chunks = o->n_steps / kStepChunk;
   if (chunks > 0) {
-    if (!s->step_graph || s->step_graph_cap != s->t_cap) {
+    if (!s->step_graph || s->step_graph_cap != s->t_cap || s->step_graph_rows != nt) {
       if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
       s->step_graph = nullptr;
       cudaGraph_t graph;
       VAG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       set_capturing(true);
-      double *a = s->cbuf, *b = s->cbuf + n;
+      double *a = s->cbuf, *b = s->cbuf + nt;
       for (int k = 0; k < kStepChunk; ++k) {
-        launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
+        launch_pdl(k_step, gs, TB, 0, st, nt, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
                    (const double *)s->tdiag, (const double *)a, b);
         std::swap(a, b);
       }
@@ -427,6 +503,7 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
       VAG_CUDA(cudaGraphInstantiate(&s->step_graph, graph, 0));
       cudaGraphDestroy(graph);
       s->step_graph_cap = s->t_cap;
+      s->step_graph_rows = nt;
     }
     for (int c = 0; c < chunks; ++c) {
       VAG_CUDA(cudaGraphLaunch(s->step_graph, st));
@@ -434,7 +511,7 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     }
   }
   for (int k = chunks * kStepChunk; k < o->n_steps; ++k) {
-    launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
+    launch_pdl(k_step, gs, TB, 0, st, nt, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
                (const double *)s->tdiag, (const double *)c0, c1);
     note_launches(1);
     std::swap(c0, c1);

@@ -25,6 +25,14 @@ VAG_FP64, VAG_MIXED, VAG_MIXED_F16, VAG_FP64_PC32 = 0, 1, 2, 3
 VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG, VAG_PC_AMG_RS = 0, 1, 2, 3
 VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB, VAG_KRYLOV_GMRES = 0, 1, 2
 VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP, VAG_KERNEL_SPMV32 = 0, 1, 2, 3
+VAG_SHAPE_HEX, VAG_SHAPE_TET, VAG_SHAPE_PRISM, VAG_SHAPE_PYRAMID = 0, 1, 2, 3
+# local faces of each shape, each cyclic (the library's tables, include/vag.h)
+SHAPE_FACES = {
+    0: [(0, 2, 6, 4), (1, 3, 7, 5), (0, 1, 5, 4), (2, 3, 7, 6), (0, 1, 3, 2), (4, 5, 7, 6)],
+    1: [(1, 2, 3), (0, 3, 2), (0, 1, 3), (0, 2, 1)],
+    2: [(0, 1, 2), (3, 4, 5), (0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5)],
+    3: [(0, 1, 2, 3), (0, 1, 4), (1, 2, 4), (2, 3, 4), (3, 0, 4)],
+}
 
 STATUS_NAMES = {0: "VAG_OK", 1: "VAG_EINVAL", 2: "VAG_ENOMEM", 3: "VAG_EBUDGET", 4: "VAG_ENOTCONVERGED",
                 5: "VAG_EBREAKDOWN", 6: "VAG_ETIMEOUT", 7: "VAG_ECUDA", 8: "VAG_EMESH"}
@@ -38,7 +46,9 @@ class vag_mesh(C.Structure):
 
 
 class vag_props(C.Structure):
-    _fields_ = [("lambda_m", C.c_void_p), ("lambda_f", C.c_void_p), ("d_f", C.c_void_p), ("mu", C.c_double)]
+    _fields_ = [("lambda_m", C.c_void_p), ("lambda_f", C.c_void_p), ("d_f", C.c_void_p), ("mu", C.c_double),
+                ("n_perf", C.c_int32), ("well_ff", C.c_void_p), ("well_wi", C.c_void_p), ("well_pw", C.c_void_p),
+                ("well_q", C.c_void_p), ("well_cin", C.c_void_p)]
 
 
 class vag_dirichlet(C.Structure):
@@ -129,6 +139,9 @@ _SIGS = {
     "vag_export_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
     "vag_set_fluxes": (C.c_int, [P, P, P, P, C.c_int]),
     "vag_export_porous_volumes": (C.c_int, [P, P, C.c_int]),
+    "vag_export_well_rates": (C.c_int, [P, P, C.c_int]),
+    "vag_export_cells": (C.c_int, [P, P, P, P, C.c_int]),
+    "vag_peaceman_wi": (C.c_int, [C.c_int32, P, P, P, P, P, C.c_double, P]),
 }
 
 _LIB = None
@@ -198,6 +211,38 @@ def _general_mesh(xyz, face_node_ptr, face_node_idx, cell_face_ptr, cell_face_id
                     _ptr(cell_face_ptr, np.int32), _ptr(cell_face_idx, np.int32), _ptr(ff_face_ids, np.int32))
 
 
+WELL_KEYS = ("ff", "wi", "pw", "q", "cin")
+
+
+def _wells_arrays(wells):
+    """wells: None or a dict with per-perforation arrays ff (fracture-face
+    index), wi, pw, q, cin (see vag_props); numpy host or CUDA tensors."""
+    if wells is None:
+        return []
+    return [wells[k] for k in WELL_KEYS]
+
+
+def _props(lambda_m, lambda_f, d_f, mu, wells=None):
+    w = _wells_arrays(wells)
+    if not w:
+        return vag_props(_ptr(lambda_m, np.float64), _ptr(lambda_f, np.float64), _ptr(d_f, np.float64), float(mu))
+    return vag_props(_ptr(lambda_m, np.float64), _ptr(lambda_f, np.float64), _ptr(d_f, np.float64), float(mu),
+                     _size(w[0]), _ptr(w[0], np.int32), _ptr(w[1], np.float64), _ptr(w[2], np.float64),
+                     _ptr(w[3], np.float64), _ptr(w[4], np.float64))
+
+
+def peaceman_wi(dx, dz, d_f, lambda_f, r_w, mu=1.0):
+    """vag_peaceman_wi: Peaceman well indices (host arrays, broadcast)."""
+    dx, dz, d_f, lambda_f, r_w = [np.ascontiguousarray(a, np.float64) for a in
+                                  np.broadcast_arrays(dx, dz, d_f, lambda_f, r_w)]
+    out = np.empty(dx.size)
+    st = lib().vag_peaceman_wi(dx.size, _ptr(dx), _ptr(dz), _ptr(d_f), _ptr(lambda_f), _ptr(r_w), float(mu),
+                               _ptr(out))
+    if st != VAG_OK:
+        raise VagError(st, "vag_peaceman_wi: an input is not positive or r_0 <= r_w")
+    return out
+
+
 def _mem_of(*xs):
     kinds = set()
     for x in xs:
@@ -241,15 +286,16 @@ class Context:
         except Exception:
             pass
 
-    def assemble(self, xyz, cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values):
+    def assemble(self, xyz, cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values, wells=None):
         """Arrays: numpy (host) or CUDA tensors (device), float64 / int32."""
-        mem = _mem_of(xyz, cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, dir_nodes, dir_values)
+        mem = _mem_of(xyz, cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, dir_nodes, dir_values,
+                      *_wells_arrays(wells))
         m = vag_mesh(int(len(xyz) // 3 if xyz.ndim == 1 else xyz.shape[0]), _ptr(xyz, np.float64),
                      int(cell_nodes.numel() // 8 if _is_torch(cell_nodes) else cell_nodes.size // 8),
                      _ptr(cell_nodes, np.int32),
                      int(ff_nodes.numel() // 4 if _is_torch(ff_nodes) else ff_nodes.size // 4),
                      _ptr(ff_nodes, np.int32))
-        p = vag_props(_ptr(lambda_m, np.float64), _ptr(lambda_f, np.float64), _ptr(d_f, np.float64), float(mu))
+        p = _props(lambda_m, lambda_f, d_f, mu, wells)
         nd = int(dir_nodes.numel() if _is_torch(dir_nodes) else dir_nodes.size)
         b = vag_dirichlet(nd, _ptr(dir_nodes, np.int32), _ptr(dir_values, np.float64))
         h = P()
@@ -257,14 +303,14 @@ class Context:
         return System(self, h)
 
     def assemble_general(self, xyz, face_node_ptr, face_node_idx, cell_face_ptr, cell_face_idx, ff_face_ids,
-                         lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values):
+                         lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values, wells=None):
         """The general polyhedral descriptor (faces as cyclic node lists,
         cells as face lists, fracture faces as face ids); numpy (host) or CUDA
         tensors (device), float64 / int32."""
         mem = _mem_of(xyz, face_node_ptr, face_node_idx, cell_face_ptr, cell_face_idx, ff_face_ids, lambda_m,
-                      lambda_f, d_f, dir_nodes, dir_values)
+                      lambda_f, d_f, dir_nodes, dir_values, *_wells_arrays(wells))
         m = _general_mesh(xyz, face_node_ptr, face_node_idx, cell_face_ptr, cell_face_idx, ff_face_ids)
-        p = vag_props(_ptr(lambda_m, np.float64), _ptr(lambda_f, np.float64), _ptr(d_f, np.float64), float(mu))
+        p = _props(lambda_m, lambda_f, d_f, mu, wells)
         nd = _size(dir_nodes)
         b = vag_dirichlet(nd, _ptr(dir_nodes, np.int32), _ptr(dir_values, np.float64))
         h = P()
@@ -283,7 +329,8 @@ class Context:
             general = "face_node_ptr" in q
             topo = ([q[k] for k in ("face_node_ptr", "face_node_idx", "cell_face_ptr", "cell_face_idx",
                                     "ff_face_ids")] if general else [q["cell_nodes"], q["ff_nodes"]])
-            arrs = [q["xyz"], *topo, q["lambda_m"], q["lambda_f"], q["d_f"], q["dir_nodes"], q["dir_values"]]
+            arrs = [q["xyz"], *topo, q["lambda_m"], q["lambda_f"], q["d_f"], q["dir_nodes"], q["dir_values"],
+                    *_wells_arrays(q.get("wells"))]
             keep.append(arrs)
             mm = _mem_of(*arrs)
             if mem is None:
@@ -297,8 +344,7 @@ class Context:
                 ms[i] = vag_mesh(size(q["xyz"]) // 3, _ptr(q["xyz"], np.float64), size(q["cell_nodes"]) // 8,
                                  _ptr(q["cell_nodes"], np.int32), size(q["ff_nodes"]) // 4,
                                  _ptr(q["ff_nodes"], np.int32))
-            ps[i] = vag_props(_ptr(q["lambda_m"], np.float64), _ptr(q["lambda_f"], np.float64),
-                              _ptr(q["d_f"], np.float64), float(q["mu"]))
+            ps[i] = _props(q["lambda_m"], q["lambda_f"], q["d_f"], q["mu"], q.get("wells"))
             bs[i] = vag_dirichlet(size(q["dir_nodes"]), _ptr(q["dir_nodes"], np.int32),
                                   _ptr(q["dir_values"], np.float64))
         h = P()
@@ -352,10 +398,16 @@ class System:
         self.ctx.check(self._L.vag_transport_get_dts(self.h, _ptr(dmax), _ptr(dt)))
         return dmax, dt
 
-    def update_props(self, lambda_m, lambda_f, d_f, mu):
-        mem = _mem_of(lambda_m, lambda_f, d_f)
-        p = vag_props(_ptr(lambda_m, np.float64), _ptr(lambda_f, np.float64), _ptr(d_f, np.float64), float(mu))
+    def update_props(self, lambda_m, lambda_f, d_f, mu, wells=None):
+        mem = _mem_of(lambda_m, lambda_f, d_f, *_wells_arrays(wells))
+        p = _props(lambda_m, lambda_f, d_f, mu, wells)
         self.ctx.check(self._L.vag_update_props(self.h, C.byref(p), mem))
+
+    def well_rates(self, n_perf):
+        """Rates leaving each perforated face into its well (last solve)."""
+        out = np.empty(max(int(n_perf), 1))
+        self.ctx.check(self._L.vag_export_well_rates(self.h, _ptr(out), VAG_MEM_HOST))
+        return out[:n_perf]
 
     def solve(self, out=None, precision=VAG_FP64, precond=VAG_PC_JACOBI, rtol=1e-12, maxit=20000,
               raise_on_error=True, krylov=VAG_KRYLOV_CG, inner_rtol=0.0):
@@ -417,6 +469,16 @@ class System:
                                                  _ptr(row_dof), VAG_MEM_HOST))
         return dict(rowptr=rowptr, col=col, val=val, rhs=rhs, row_dof=row_dof)
 
+    def export_cells(self):
+        """(cell_nodes [n_cells, 8], shape [n_cells], ff_nodes [n_ff, 4]): the
+        numbering the kernels run on (-1 in unused slots)."""
+        i = self.info()
+        cn = np.empty(8 * i.n_cells, np.int32)
+        sh = np.empty(i.n_cells, np.int8)
+        ffn = np.empty(max(4 * i.n_ff, 1), np.int32)
+        self.ctx.check(self._L.vag_export_cells(self.h, _ptr(cn), _ptr(sh), _ptr(ffn), VAG_MEM_HOST))
+        return cn.reshape(-1, 8), sh, ffn[:4 * i.n_ff].reshape(-1, 4)
+
     def export_fluxes(self):
         i = self.info()
         Fcn = np.empty(8 * i.n_cells)
@@ -438,8 +500,33 @@ class System:
         return phi
 
 
+def _wells_of(pb):
+    w = getattr(pb, "wells", None)
+    if not w:
+        return None
+    return dict(ff=np.ascontiguousarray(w["ff"], np.int32), wi=np.ascontiguousarray(w["wi"], np.float64),
+                pw=np.ascontiguousarray(w["pw"], np.float64), q=np.ascontiguousarray(w["q"], np.float64),
+                cin=np.ascontiguousarray(w["cin"], np.float64))
+
+
+def _to_device(q):
+    import torch
+    out = {}
+    for k, v in q.items():
+        out[k] = ({kk: torch.from_numpy(vv).cuda() for kk, vv in v.items()} if isinstance(v, dict)
+                  else torch.from_numpy(v).cuda())
+    return out
+
+
+def is_hex_problem(pb):
+    """True when every cell is a hexahedron given by 8 node slots (the fast path)."""
+    cn = np.asarray(pb.cell_nodes)
+    return cn.ndim == 2 and cn.shape[1] == 8 and bool((cn >= 0).all())
+
+
 def problem_arrays(pb, device=False):
-    """The ABI arrays of a ``vag_inputs.Problem``-like object as a dict."""
+    """The ABI arrays of a ``vag_inputs.Problem``-like object as a dict (the
+    hexahedral fast path; ``general_arrays`` for other cells)."""
     q = dict(xyz=np.ascontiguousarray(pb.xyz, np.float64).ravel(),
              cell_nodes=np.ascontiguousarray(pb.cell_nodes, np.int32).ravel(),
              ff_nodes=np.ascontiguousarray(pb.ff_nodes, np.int32).ravel(),
@@ -447,52 +534,61 @@ def problem_arrays(pb, device=False):
              lambda_f=np.ascontiguousarray(pb.lambda_f, np.float64), d_f=np.ascontiguousarray(pb.d_f, np.float64),
              dir_nodes=np.ascontiguousarray(pb.dir_nodes, np.int32),
              dir_values=np.ascontiguousarray(pb.dir_values, np.float64))
+    w = _wells_of(pb)
+    if w is not None:
+        q["wells"] = w
     if device:
-        import torch
-        q = {k: torch.from_numpy(v).cuda() for k, v in q.items()}
+        q = _to_device(q)
     q["mu"] = pb.mu
     return q
 
 
+def _ragged(a):
+    """CSR (ptr, idx) of a -1-padded 2-D id array (padding after the ids)."""
+    a = np.ascontiguousarray(a, np.int32)
+    cnt = (a >= 0).sum(axis=1)
+    ptr = np.zeros(a.shape[0] + 1, np.int32)
+    np.cumsum(cnt, out=ptr[1:])
+    return ptr, np.ascontiguousarray(a[a >= 0], np.int32)
+
+
 def general_arrays(pb, device=False):
     """The general polyhedral descriptor of a ``vag_inputs.Problem``-like
-    object (attributes faces [n_faces, q], cell_faces [n_cells, f], ff_faces
-    and the physical data) as a dict for ``Context.assemble_general`` or
-    ``Context.assemble_batch``."""
-    faces = np.ascontiguousarray(pb.faces, np.int32)
-    cf = np.ascontiguousarray(pb.cell_faces, np.int32)
+    object (attributes faces [n_faces, q_max] and cell_faces [n_cells, f_max],
+    -1-padded, ff_faces and the physical data) as a dict for
+    ``Context.assemble_general`` or ``Context.assemble_batch``."""
+    fptr, fidx = _ragged(pb.faces)
+    cptr, cidx = _ragged(pb.cell_faces)
     q = dict(xyz=np.ascontiguousarray(pb.xyz, np.float64).ravel(),
-             face_node_ptr=np.arange(0, faces.size + 1, faces.shape[1], dtype=np.int32),
-             face_node_idx=faces.ravel(),
-             cell_face_ptr=np.arange(0, cf.size + 1, cf.shape[1], dtype=np.int32),
-             cell_face_idx=cf.ravel(),
+             face_node_ptr=fptr, face_node_idx=fidx, cell_face_ptr=cptr, cell_face_idx=cidx,
              ff_face_ids=np.ascontiguousarray(pb.ff_faces, np.int32),
              lambda_m=np.ascontiguousarray(pb.lambda_m, np.float64).ravel(),
              lambda_f=np.ascontiguousarray(pb.lambda_f, np.float64), d_f=np.ascontiguousarray(pb.d_f, np.float64),
              dir_nodes=np.ascontiguousarray(pb.dir_nodes, np.int32),
              dir_values=np.ascontiguousarray(pb.dir_values, np.float64))
+    w = _wells_of(pb)
+    if w is not None:
+        q["wells"] = w
     if device:
-        import torch
-        q = {k: torch.from_numpy(v).cuda() for k, v in q.items()}
+        q = _to_device(q)
     q["mu"] = pb.mu
     return q
 
 
-def assemble_problem(ctx: Context, pb, device=False):
-    """Marshal a ``vag_inputs.Problem``-like object (attributes xyz,
-    cell_nodes, ff_nodes, lambda_m, lambda_f, d_f, mu, dir_nodes, dir_values)."""
-    arrs = [np.ascontiguousarray(pb.xyz, np.float64).ravel(), np.ascontiguousarray(pb.cell_nodes, np.int32).ravel(),
-            np.ascontiguousarray(pb.ff_nodes, np.int32).ravel(), np.ascontiguousarray(pb.lambda_m, np.float64).ravel(),
-            np.ascontiguousarray(pb.lambda_f, np.float64), np.ascontiguousarray(pb.d_f, np.float64)]
-    dn = np.ascontiguousarray(pb.dir_nodes, np.int32)
-    dv = np.ascontiguousarray(pb.dir_values, np.float64)
-    if device:
-        import torch
-        arrs = [torch.from_numpy(a).cuda() for a in arrs]
-        dn = torch.from_numpy(dn).cuda()
-        dv = torch.from_numpy(dv).cuda()
-    xyz, cn, ffn, lam, lamf, df = arrs
-    return ctx.assemble(xyz, cn, ffn, lam, lamf, df, pb.mu, dn, dv)
+def assemble_problem(ctx: Context, pb, device=False, general=None):
+    """Marshal a ``vag_inputs.Problem``-like object.  The hexahedral fast
+    path is used when every cell is a hexahedron (attributes xyz, cell_nodes,
+    ff_nodes, ...), the general descriptor otherwise or with general=True."""
+    if general is None:
+        general = not is_hex_problem(pb)
+    if general:
+        q = general_arrays(pb, device)
+        return ctx.assemble_general(q["xyz"], q["face_node_ptr"], q["face_node_idx"], q["cell_face_ptr"],
+                                    q["cell_face_idx"], q["ff_face_ids"], q["lambda_m"], q["lambda_f"], q["d_f"],
+                                    q["mu"], q["dir_nodes"], q["dir_values"], q.get("wells"))
+    q = problem_arrays(pb, device)
+    return ctx.assemble(q["xyz"], q["cell_nodes"], q["ff_nodes"], q["lambda_m"], q["lambda_f"], q["d_f"], q["mu"],
+                        q["dir_nodes"], q["dir_values"], q.get("wells"))
 
 
 class Server:
@@ -510,8 +606,11 @@ class Server:
         self._out = {}
 
     def submit(self, pb, n_steps=0, precision=VAG_FP64, precond=VAG_PC_JACOBI, rtol=1e-8, maxit=20000,
-               cfl=0.9, omega=0.5, general=False):
-        """general: pass the mesh in the general polyhedral form."""
+               cfl=0.9, omega=0.5, general=None):
+        """general: pass the mesh in the general polyhedral form (default:
+        when some cell is not a hexahedron)."""
+        if general is None:
+            general = not is_hex_problem(pb)
         a = general_arrays(pb) if general else problem_arrays(pb)
         n_cv = pb.n_nodes + pb.n_ff + pb.n_cells
         u = np.empty(n_cv)
@@ -524,7 +623,7 @@ class Server:
         else:
             m = vag_mesh(pb.n_nodes, _ptr(a["xyz"]), pb.n_cells, _ptr(a["cell_nodes"]), pb.n_ff,
                          _ptr(a["ff_nodes"]))
-        pr = vag_props(_ptr(a["lambda_m"]), _ptr(a["lambda_f"]), _ptr(a["d_f"]), float(pb.mu))
+        pr = _props(a["lambda_m"], a["lambda_f"], a["d_f"], pb.mu, a.get("wells"))
         bc = vag_dirichlet(len(a["dir_nodes"]), _ptr(a["dir_nodes"]), _ptr(a["dir_values"]))
         q = vag_request(m, pr, bc, _ptr(keep[1]), _ptr(keep[2]), _ptr(keep[3]), None, float(omega), float(cfl),
                         int(n_steps), precision, precond, float(rtol), int(maxit), _ptr(u), _ptr(c))

@@ -12,10 +12,14 @@ conforming to the fracture network):
 
 * ``xyz``        float64 [n_nodes, 3]
 * ``cell_nodes`` int32   [n_cells, 8]   hexahedron, node ``l`` sits at the
-  lattice offset ``(l & 1, (l >> 1) & 1, (l >> 2) & 1)`` of the cell.
+  lattice offset ``(l & 1, (l >> 1) & 1, (l >> 2) & 1)`` of the cell (the
+  tetrahedral, prismatic and pyramidal generators list their own node
+  counts, -1-padded to 8 where shapes mix).
 * ``faces``      int32   [n_faces, 4]   every face of the mesh once, nodes in
-  cyclic order (consecutive entries share an edge).
-* ``cell_faces`` int32   [n_cells, 6]   face ids of each cell.
+  cyclic order (consecutive entries share an edge); a triangle has -1 in
+  its last slot (a tetrahedral mesh has [n_faces, 3]).
+* ``cell_faces`` int32   [n_cells, 6]   face ids of each cell, -1 after the
+  last face of a cell with fewer than six.
 * ``ff_faces``   int32   [n_ff]         ids (into ``faces``) of the fracture
   faces, sorted; ``ff_nodes = faces[ff_faces]``.
 * ``lambda_m``   float64 [n_cells, 6]   symmetric matrix permeability tensor
@@ -26,6 +30,10 @@ conforming to the fracture network):
   Dirichlet pressure; every other boundary node is a no-flow node.
 * ``phi_m`` [n_cells], ``phi_f`` [n_ff]: porosities; ``cbar`` [n_dir]: the
   Dirichlet concentrations.
+* ``wells`` (optional, ``well_arrays``): per perforation the fracture face
+  ``ff``, well index ``wi``, well pressure ``pw``, imposed rate ``q`` and
+  injected concentration ``cin``; ``meta["well_geometry"]`` holds what the
+  Peaceman index is computed from.
 
 All random draws come from ``numpy.random.default_rng(seed)`` in a fixed order.
 """
@@ -39,7 +47,8 @@ import numpy as np
 __all__ = [
     "Problem", "hex_lattice", "axis_fracture_faces", "build_problem",
     "config_plain16", "config_scale64", "config_mixed128", "random_dfn_problem",
-    "one_fracture_problem", "four_fracture_problem", "batch_problems",
+    "one_fracture_problem", "four_fracture_problem", "batch_problems", "tet_problem", "prism_problem",
+    "pyramid_problem", "well_problem", "well_arrays",
 ]
 
 
@@ -63,6 +72,7 @@ class Problem:
     phi_f: np.ndarray
     cbar: np.ndarray
     meta: dict = field(default_factory=dict)
+    wells: Optional[dict] = None
 
     @property
     def n_nodes(self) -> int:
@@ -452,3 +462,412 @@ def four_fracture_problem(nx, tan1=5.0 / 8.0, tan2=0.25, lam_f1=200.0, lam_f3=40
                          meta={"name": f"fourfrac{nx}", "tan1": tan1, "tan2": tan2,
                                "lam_f1": lam_f1, "lam_f3": lam_f3, "d_f": d_f,
                                "jf": jf, "if": i_f})
+
+
+# ----------------------------------------------------------------------------
+# tetrahedral meshes (Sec. 3.1 admits any polyhedral cells)
+# ----------------------------------------------------------------------------
+
+def tet_problem(dims, fractures: Sequence[Tuple] = (), *, jitter=0.0, seed=0, lam_m="identity", ratio=1e4,
+                d_f=1e-2, phi_m=0.2, phi_f=0.4, meta=None) -> Problem:
+    """A conforming tetrahedral mesh of the unit box: every cell of an
+    nx*ny*nz hexahedral lattice cut into the six tetrahedra around its
+    diagonal from lattice offset (0,0,0) to (1,1,1) (one per order of the
+    three axes), so neighbouring cells cut their shared square the same way.
+    ``faces`` are the unique triangles [n_faces, 3], ``cell_faces``
+    [n_cells, 4], ``cell_nodes`` [n_cells, 4].  ``fractures``: axis-aligned
+    rectangles (axis, plane, lo_a, hi_a, lo_b, hi_b) on lattice node planes,
+    as for the hexahedral lattice; their fracture faces are the triangles
+    lying in them.  Interior nodes are jittered by U(-jitter h, jitter h) per
+    coordinate with fracture-normal coordinates frozen; p = 1 - x on x = 0 and
+    x = 1 (inflow c = 1 on x = 0), no-flow elsewhere."""
+    import itertools
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    hex_nodes, _, _, _, _ = hex_lattice(dims)
+    tets = []
+    for perm in itertools.permutations((1, 2, 4)):
+        loc = [0, perm[0], perm[0] | perm[1], 7]
+        tets.append(hex_nodes[:, loc])
+    cell_nodes = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)   # the 6 tets of a hex stay together
+    n_cells = cell_nodes.shape[0]
+    tri = np.concatenate([cell_nodes[:, [1, 2, 3]], cell_nodes[:, [0, 2, 3]], cell_nodes[:, [0, 1, 3]],
+                          cell_nodes[:, [0, 1, 2]]])
+    key = np.sort(tri, axis=1)
+    faces, inv = np.unique(key, axis=0, return_inverse=True)
+    faces = faces.astype(np.int32)
+    cell_faces = inv.reshape(4, n_cells).T.astype(np.int32)
+    # lattice index of every node
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+    ids, owner = [], []
+    frozen = np.zeros((ijk.shape[0], 3), bool)
+    for f_idx, (axis, plane, lo_a, hi_a, lo_b, hi_b) in enumerate(fractures):
+        oa, ob = [a for a in range(3) if a != axis]
+        fi = ijk[faces]                                          # [n_faces, 3 nodes, 3 axes]
+        on = np.all(fi[:, :, axis] == plane, axis=1)
+        ina = np.all((fi[:, :, oa] >= lo_a) & (fi[:, :, oa] <= hi_a), axis=1)
+        inb = np.all((fi[:, :, ob] >= lo_b) & (fi[:, :, ob] <= hi_b), axis=1)
+        fid = np.nonzero(on & ina & inb)[0]
+        ids.append(fid)
+        owner.append(np.full(fid.shape, f_idx))
+        frozen[np.unique(faces[fid].ravel()), axis] = True
+    if ids:
+        allid = np.concatenate(ids)
+        allown = np.concatenate(owner)
+        ff_faces, first = np.unique(allid, return_index=True)
+        ff_frac = allown[first].astype(np.int32)
+    else:
+        ff_faces = np.zeros(0, np.int64)
+        ff_frac = np.zeros(0, np.int32)
+    ff_faces = ff_faces.astype(np.int32)
+    xyz = _lattice_xyz(dims)
+    if jitter > 0:
+        h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+        d = rng.uniform(-jitter, jitter, size=xyz.shape) * h[None, :]
+        boundary = ((ijk[:, 0] == 0) | (ijk[:, 0] == nx) | (ijk[:, 1] == 0) | (ijk[:, 1] == ny) |
+                    (ijk[:, 2] == 0) | (ijk[:, 2] == nz))
+        d[boundary] = 0.0
+        d[frozen] = 0.0
+        xyz = xyz + d
+    if isinstance(lam_m, np.ndarray):
+        lam = lam_m
+    elif lam_m == "identity":
+        lam = np.zeros((n_cells, 6)); lam[:, :3] = 1.0
+    elif lam_m == "lognormal":
+        lam = _lognormal_aniso(n_cells, rng)
+    else:
+        raise ValueError(lam_m)
+    nff = ff_faces.shape[0]
+    left = np.nonzero(ijk[:, 0] == 0)[0]
+    right = np.nonzero(ijk[:, 0] == nx)[0]
+    dir_nodes = np.sort(np.concatenate([left, right])).astype(np.int32)
+    dir_values = 1.0 - xyz[dir_nodes, 0]
+    cbar = np.where(np.isin(dir_nodes, left), 1.0, 0.0)
+    return Problem(
+        dims=tuple(dims), xyz=np.ascontiguousarray(xyz, np.float64), cell_nodes=cell_nodes, faces=faces,
+        cell_faces=cell_faces, ff_faces=ff_faces, ff_nodes=np.ascontiguousarray(faces[ff_faces]).astype(np.int32),
+        ff_frac=ff_frac, lambda_m=np.ascontiguousarray(lam, np.float64), lambda_f=np.full(nff, float(ratio)),
+        d_f=np.full(nff, float(d_f)), mu=1.0, dir_nodes=dir_nodes, dir_values=np.asarray(dir_values, np.float64),
+        phi_m=np.full(n_cells, float(phi_m)), phi_f=np.full(nff, float(phi_f)), cbar=np.asarray(cbar, np.float64),
+        meta=dict(meta or {}, name=f"tet{nx}x{ny}x{nz}", seed=seed))
+
+
+# ----------------------------------------------------------------------------
+# extruded triangular meshes: prisms (the mesh type of Sec. 5.5), optionally
+# mixed with hexahedral columns
+# ----------------------------------------------------------------------------
+
+# local faces, cyclic (the library's tables list the same faces)
+_PRISM_FACES = [(0, 1, 2), (3, 4, 5), (0, 1, 4, 3), (1, 2, 5, 4), (2, 0, 3, 5)]
+_HEX_FACES = [(0, 2, 6, 4), (1, 3, 7, 5), (0, 1, 5, 4), (2, 3, 7, 6), (0, 1, 3, 2), (4, 5, 7, 6)]
+
+
+def _faces_of_cells(cell_nodes, kinds, tables):
+    """Unique faces (padded [n_faces, 4], -1 after the nodes, each in the
+    cyclic order of its first cell) and the padded cell -> face table
+    [n_cells, 6] of cells given as -1-padded node rows; cell K uses the
+    local faces tables[kinds[K]]."""
+    cells_l, slot_l, rows_l = [], [], []
+    for k, table in enumerate(tables):
+        C = np.nonzero(kinds == k)[0]
+        for f, lf in enumerate(table):
+            r = -np.ones((C.size, 4), np.int64)
+            r[:, :len(lf)] = cell_nodes[C][:, list(lf)]
+            cells_l.append(C); slot_l.append(np.full(C.size, f)); rows_l.append(r)
+    cell = np.concatenate(cells_l); slot = np.concatenate(slot_l); rows = np.concatenate(rows_l)
+    order = np.lexsort((slot, cell))              # by cell, then local face
+    cell, slot, rows = cell[order], slot[order], rows[order]
+    key = np.sort(rows, axis=1)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    faces = rows[first].astype(np.int32)
+    cell_faces = -np.ones((cell_nodes.shape[0], 6), np.int32)
+    cell_faces[cell, slot] = inv.ravel()
+    return faces, cell_faces
+
+
+def prism_problem(nxy, nz, fractures: Sequence[Tuple] = (), *, split="all", jitter=0.0, seed=0,
+                  lam_m="identity", ratio=1e4, d_f=1e-2, phi_m=0.2, phi_f=0.4, dirichlet="x",
+                  lengths=(1.0, 1.0, 1.0), meta=None) -> Problem:
+    """The tensor product of a triangular mesh of the rectangle with a
+    uniform vertical mesh of nz layers, as in Sec. 5.5: the nx*ny lattice
+    squares are cut into the triangles (00, 10, 11) and (00, 11, 01) and
+    each triangle times each layer is a prism (nodes: the bottom triangle,
+    then the nodes above it).  ``split``: "all" (prisms only), "half"
+    (columns with i < nx/2 are cut, the others stay hexahedra) or "checker"
+    (columns with i + j even are cut) for meshes that mix both shapes.
+    ``cell_nodes`` is [n_cells, 8] with -1 after a prism's 6 nodes, ``faces``
+    [n_faces, 4] with -1 after a triangle's 3 nodes, ``cell_faces``
+    [n_cells, 6] with -1 after a prism's 5 faces.
+
+    ``fractures``: vertical rectangles made of lattice faces, each
+    ("x", i, j0, j1, k0, k1) on the plane of node column i for squares
+    j0 <= j < j1 and layers k0 <= k < k1, ("y", j, i0, i1, k0, k1), or
+    ("d", d, i0, i1, k0, k1) on the diagonals (i, i - d) -> (i + 1, i + 1 - d)
+    of cut squares i0 <= i < i1.  Interior nodes are jittered by
+    U(-jitter h, jitter h) per coordinate with the coordinates normal to a
+    fracture plane frozen.  ``dirichlet="x"``: p = 1 - x/Lx on the x = 0 and
+    x = Lx node planes (inflow c = 1 at x = 0); None: no Dirichlet nodes
+    (wells fix the pressure).  ``lengths``: the box (Lx, Ly, Lz)."""
+    rng = np.random.default_rng(seed)
+    nx, ny = nxy
+    dims = (nx, ny, nz)
+    cut = np.zeros((nx, ny), bool)
+    for i in range(nx):
+        for j in range(ny):
+            cut[i, j] = split == "all" or (split == "half" and i < nx // 2) or (split == "checker" and (i + j) % 2 == 0)
+    # columns in (k, j, i) order; a cut column holds two prisms, the others a hexahedron
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    kk, jj, ii = kk.ravel(), jj.ravel(), ii.ravel()
+    iscut = cut[ii, jj]
+    per = np.where(iscut, 2, 1)
+    start = np.concatenate([[0], np.cumsum(per)[:-1]])
+    n_cells = int(per.sum())
+    up = (nx + 1) * (ny + 1)
+    n00, n10 = _nid(dims, ii, jj, kk), _nid(dims, ii + 1, jj, kk)
+    n01, n11 = _nid(dims, ii, jj + 1, kk), _nid(dims, ii + 1, jj + 1, kk)
+    cell_nodes = -np.ones((n_cells, 8), np.int64)
+    kinds = np.zeros(n_cells, np.int64)
+    c = np.nonzero(iscut)[0]
+    for t, tri in enumerate(((n00, n10, n11), (n00, n11, n01))):
+        rows = start[c] + t
+        bot = np.stack([v[c] for v in tri], axis=1)
+        cell_nodes[rows, :6] = np.concatenate([bot, bot + up], axis=1)
+        kinds[rows] = 0
+    h = np.nonzero(~iscut)[0]
+    bot = np.stack([n00[h], n10[h], n01[h], n11[h]], axis=1)
+    cell_nodes[start[h]] = np.concatenate([bot, bot + up], axis=1)
+    kinds[start[h]] = 1
+    faces, cell_faces = _faces_of_cells(cell_nodes, kinds, [_PRISM_FACES, _HEX_FACES])
+    cell_nodes = cell_nodes.astype(np.int32)
+    k3, j3, i3 = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    ijk = np.stack([i3.ravel(), j3.ravel(), k3.ravel()], axis=1)
+    quad = faces[:, 3] >= 0
+    fi = ijk[np.where(faces >= 0, faces, 0)]                     # [n_faces, 4, 3]
+    ids, owner = [], []
+    frozen = np.zeros((ijk.shape[0], 3), bool)
+    for f_idx, (kind, plane, a0, a1, k0, k1) in enumerate(fractures):
+        ii, jj, kk = fi[:, :, 0], fi[:, :, 1], fi[:, :, 2]
+        inz = np.all((kk >= k0) & (kk <= k1), axis=1)
+        if kind == "x":
+            sel = np.all(ii == plane, axis=1) & np.all((jj >= a0) & (jj <= a1), axis=1)
+            fr = (0,)
+        elif kind == "y":
+            sel = np.all(jj == plane, axis=1) & np.all((ii >= a0) & (ii <= a1), axis=1)
+            fr = (1,)
+        elif kind == "d":
+            sel = np.all(ii - jj == plane, axis=1) & np.all((ii >= a0) & (ii <= a1), axis=1)
+            fr = (0, 1)
+        else:
+            raise ValueError(kind)
+        fid = np.nonzero(sel & inz & quad)[0]
+        ids.append(fid)
+        owner.append(np.full(fid.shape, f_idx))
+        for ax in fr:
+            frozen[np.unique(faces[fid].ravel()), ax] = True
+    if ids:
+        allid = np.concatenate(ids)
+        allown = np.concatenate(owner)
+        ff_faces, first = np.unique(allid, return_index=True)
+        ff_frac = allown[first].astype(np.int32)
+    else:
+        ff_faces = np.zeros(0, np.int64)
+        ff_frac = np.zeros(0, np.int32)
+    ff_faces = ff_faces.astype(np.int32)
+    L = np.asarray(lengths, np.float64)
+    xyz = _lattice_xyz(dims) * L[None, :]
+    if jitter > 0:
+        h = L / np.array([nx, ny, nz])
+        d = rng.uniform(-jitter, jitter, size=xyz.shape) * h[None, :]
+        boundary = ((ijk[:, 0] == 0) | (ijk[:, 0] == nx) | (ijk[:, 1] == 0) | (ijk[:, 1] == ny) |
+                    (ijk[:, 2] == 0) | (ijk[:, 2] == nz))
+        d[boundary] = 0.0
+        d[frozen] = 0.0
+        xyz = xyz + d
+    if isinstance(lam_m, np.ndarray):
+        lam = lam_m
+    elif lam_m == "identity":
+        lam = np.zeros((n_cells, 6)); lam[:, :3] = 1.0
+    elif lam_m == "lognormal":
+        lam = _lognormal_aniso(n_cells, rng)
+    else:
+        raise ValueError(lam_m)
+    nff = ff_faces.shape[0]
+    if dirichlet == "x":
+        left = np.nonzero(ijk[:, 0] == 0)[0]
+        right = np.nonzero(ijk[:, 0] == nx)[0]
+        dir_nodes = np.sort(np.concatenate([left, right])).astype(np.int32)
+        dir_values = 1.0 - xyz[dir_nodes, 0] / L[0]
+        cbar = np.where(np.isin(dir_nodes, left), 1.0, 0.0)
+    elif dirichlet is None:
+        dir_nodes = np.zeros(0, np.int32); dir_values = np.zeros(0); cbar = np.zeros(0)
+    else:
+        raise ValueError(dirichlet)
+    return Problem(
+        dims=tuple(dims), xyz=np.ascontiguousarray(xyz, np.float64), cell_nodes=cell_nodes, faces=faces,
+        cell_faces=cell_faces, ff_faces=ff_faces, ff_nodes=np.ascontiguousarray(faces[ff_faces]).astype(np.int32),
+        ff_frac=ff_frac, lambda_m=np.ascontiguousarray(lam, np.float64), lambda_f=np.full(nff, float(ratio)),
+        d_f=np.full(nff, float(d_f)), mu=1.0, dir_nodes=dir_nodes, dir_values=np.asarray(dir_values, np.float64),
+        phi_m=np.full(n_cells, float(phi_m)), phi_f=np.full(nff, float(phi_f)), cbar=np.asarray(cbar, np.float64),
+        meta=dict(meta or {}, name=f"prism{nx}x{ny}x{nz}_{split}", seed=seed))
+
+
+def pyramid_problem(dims, fractures: Sequence[Tuple] = (), *, jitter=0.0, seed=0, lam_m="identity", ratio=1e4,
+                    d_f=1e-2, phi_m=0.2, phi_f=0.4, meta=None) -> Problem:
+    """Every cell of an nx*ny*nz hexahedral lattice cut into six pyramids,
+    one on each of its faces, with a common apex at an added node in the
+    middle of the cell (node ids after the lattice nodes).  Neighbouring
+    cells share the square between them as the base of two pyramids, so the
+    mesh is conforming.  ``fractures`` as for ``build_problem`` (their faces
+    are lattice squares, i.e. pyramid bases).  Lattice nodes are jittered as
+    in ``build_problem``; the apexes sit at the mean of their cell's eight
+    corners plus U(-jitter h/4, jitter h/4).  p = 1 - x on x = 0 and x = 1
+    (inflow c = 1 at x = 0), no-flow elsewhere."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    hex_nodes, hfaces, hcell_faces, face_axis, _ = hex_lattice(dims)
+    nlat = (nx + 1) * (ny + 1) * (nz + 1)
+    ids, owner = [], []
+    for f_idx, fr in enumerate(fractures):
+        fid = axis_fracture_faces(dims, *fr)
+        ids.append(fid)
+        owner.append(np.full(fid.shape, f_idx))
+    if ids:
+        allid = np.concatenate(ids)
+        allown = np.concatenate(owner)
+        ff_lat, first = np.unique(allid, return_index=True)
+        ff_frac = allown[first].astype(np.int32)
+    else:
+        ff_lat = np.zeros(0, np.int64)
+        ff_frac = np.zeros(0, np.int32)
+    xyz = _lattice_xyz(dims)
+    if jitter > 0:
+        xyz = _jitter(dims, xyz, hfaces, ff_lat, face_axis, jitter, rng)
+    n_hex = hex_nodes.shape[0]
+    apex = nlat + np.arange(n_hex)
+    h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+    xa = xyz[hex_nodes].mean(axis=1)
+    if jitter > 0:
+        xa = xa + rng.uniform(-jitter / 4, jitter / 4, size=xa.shape) * h[None, :]
+    xyz = np.concatenate([xyz, xa])
+    # cells: pyramid (base = lattice face in cyclic order, apex) for each hex face
+    n_cells = 6 * n_hex
+    cell_nodes = -np.ones((n_cells, 8), np.int64)
+    cell_nodes[:, :4] = hfaces[hcell_faces].reshape(n_cells, 4)     # six pyramids per cube, in face order
+    cell_nodes[:, 4] = np.repeat(apex, 6)
+    PYR = [(0, 1, 2, 3), (0, 1, 4), (1, 2, 4), (2, 3, 4), (3, 0, 4)]
+    faces, cell_faces = _faces_of_cells(cell_nodes, np.zeros(n_cells, np.int64), [PYR])
+    cell_nodes = cell_nodes.astype(np.int32)
+    # fracture faces: the lattice squares among the new faces
+    key = {tuple(sorted(f[f >= 0].tolist())): i for i, f in enumerate(faces)}
+    ff_faces = np.array([key[tuple(sorted(hfaces[f].tolist()))] for f in ff_lat], np.int64)
+    order = np.argsort(ff_faces)
+    ff_faces = ff_faces[order].astype(np.int32)
+    ff_frac = ff_frac[order]
+    if isinstance(lam_m, np.ndarray):
+        lam = lam_m
+    elif lam_m == "identity":
+        lam = np.zeros((n_cells, 6)); lam[:, :3] = 1.0
+    elif lam_m == "lognormal":
+        lam = _lognormal_aniso(n_cells, rng)
+    else:
+        raise ValueError(lam_m)
+    nff = ff_faces.shape[0]
+    k3, j3, i3 = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    ii = i3.ravel()
+    left = np.nonzero(ii == 0)[0]
+    right = np.nonzero(ii == nx)[0]
+    dir_nodes = np.sort(np.concatenate([left, right])).astype(np.int32)
+    dir_values = 1.0 - xyz[dir_nodes, 0]
+    cbar = np.where(np.isin(dir_nodes, left), 1.0, 0.0)
+    return Problem(
+        dims=tuple(dims), xyz=np.ascontiguousarray(xyz, np.float64), cell_nodes=cell_nodes, faces=faces,
+        cell_faces=cell_faces, ff_faces=ff_faces, ff_nodes=np.ascontiguousarray(faces[ff_faces]).astype(np.int32),
+        ff_frac=ff_frac, lambda_m=np.ascontiguousarray(lam, np.float64), lambda_f=np.full(nff, float(ratio)),
+        d_f=np.full(nff, float(d_f)), mu=1.0, dir_nodes=dir_nodes, dir_values=np.asarray(dir_values, np.float64),
+        phi_m=np.full(n_cells, float(phi_m)), phi_f=np.full(nff, float(phi_f)), cbar=np.asarray(cbar, np.float64),
+        meta=dict(meta or {}, name=f"pyramid{nx}x{ny}x{nz}", seed=seed))
+
+
+def well_problem(nxy=(12, 8), nz=6, *, split="all", lengths=(600.0, 400.0, 60.0), jitter=0.15, seed=0,
+                 lam_m=1e-15, lam_f=1e-11, d_f=1.0, phi=0.1, mu=1e-3, r_w=0.1, q_inj=0.16, dirichlet=None,
+                 meta=None) -> Problem:
+    """A prism mesh with vertical fractures and vertical wells in the manner
+    of Sec. 5.5: isotropic Lambda_m and Lambda_f, aperture d_f, porosity phi
+    in both media, viscosity mu, no Dirichlet node (the producers fix the
+    pressure level).  Three fractures: the planes of node column i = nx/3
+    and of node row j = ny/2 (partly) and a diagonal.  Each well is vertical
+    at the middle of one fracture edge of the triangular mesh and perforates
+    the fracture faces of that edge in the central half of the layers: the
+    injector (total rate q_inj, concentration 1, split evenly over its
+    perforations) on the first fracture, two producers (p_w = 0) on the
+    others.  ``meta["well_geometry"]`` gives per perforation the face, its
+    well, dx (the face's horizontal edge), dz (its height), d_f, Lambda_f and
+    r_w, and ``meta["wells"]`` the wells; ``well_arrays`` turns them into the
+    per-perforation arrays once the well indices are known."""
+    nx, ny = nxy
+    i_f, j_f = nx // 3, ny // 2
+    fr = [("x", i_f, 0, ny, 0, nz), ("y", j_f, i_f, nx, 0, nz), ("d", 0, 0, min(nx, ny) // 2, 0, nz)]
+    pb = prism_problem(nxy, nz, fr, split=split, jitter=jitter, seed=seed, ratio=lam_f, d_f=d_f, phi_m=phi,
+                       phi_f=phi, dirichlet=dirichlet, lengths=lengths, meta=meta)
+    lam = np.zeros((pb.n_cells, 6)); lam[:, :3] = lam_m
+    pb.lambda_m = lam
+    pb.mu = float(mu)
+    dims = (nx, ny, nz)
+    k0, k1 = nz // 4, nz - nz // 4          # perforated layers k0 <= k < k1
+
+    def edge_faces(a, b):
+        """fracture faces of the vertical strip over lattice nodes a -> b"""
+        out = []
+        for k in range(k0, k1):
+            want = sorted([_nid(dims, *a, k), _nid(dims, *b, k), _nid(dims, *a, k + 1), _nid(dims, *b, k + 1)])
+            for i, f in enumerate(pb.ff_nodes):
+                if sorted(f.tolist()) == want:
+                    out.append(i)
+        return out
+
+    specs = [("injector", (i_f, ny // 4), (i_f, ny // 4 + 1)),
+             ("producer", (nx - 2, j_f), (nx - 1, j_f)),
+             ("producer", (1, 1), (2, 2))]
+    ff, well, dx, dz = [], [], [], []
+    wells = []
+    for w, (kind, a, b) in enumerate(specs):
+        perf = edge_faces(a, b)
+        if not perf:
+            raise ValueError(f"well {w}: no fracture face on its edge")
+        for i in perf:
+            n = pb.ff_nodes[i]
+            p = pb.xyz[n]
+            bot = np.argsort(p[:, 2])[:2]
+            dx.append(float(np.linalg.norm(p[bot[0], :2] - p[bot[1], :2])))
+            dz.append(float(p[:, 2].max() - p[:, 2].min()))
+            ff.append(i)
+            well.append(w)
+        wells.append(dict(kind=kind, pw=0.0, rate=q_inj if kind == "injector" else 0.0,
+                          cin=1.0 if kind == "injector" else 0.0))
+    pb.meta["well_geometry"] = dict(ff=np.array(ff, np.int32), well=np.array(well, np.int32), dx=np.array(dx),
+                                    dz=np.array(dz), d_f=np.full(len(ff), float(d_f)),
+                                    lam_f=np.full(len(ff), float(lam_f)), r_w=np.full(len(ff), float(r_w)))
+    pb.meta["wells"] = wells
+    pb.meta["name"] = f"wells{nx}x{ny}x{nz}_{split}"
+    return pb
+
+
+def well_arrays(pb, wi):
+    """Per-perforation arrays (ff, wi, pw, q, cin) of ``pb.meta["wells"]``
+    given the Peaceman well index of every perforation: a producer keeps
+    its WI and p_w; an injector has WI = 0 and its rate split evenly over
+    its perforations."""
+    g = pb.meta["well_geometry"]
+    wells = pb.meta["wells"]
+    n = g["ff"].size
+    out = dict(ff=g["ff"].copy(), wi=np.zeros(n), pw=np.zeros(n), q=np.zeros(n), cin=np.zeros(n))
+    for w, spec in enumerate(wells):
+        sel = g["well"] == w
+        if spec["kind"] == "producer":
+            out["wi"][sel] = np.asarray(wi)[sel]
+            out["pw"][sel] = spec["pw"]
+        else:
+            out["q"][sel] = spec["rate"] / sel.sum()
+            out["cin"][sel] = spec["cin"]
+    return out
