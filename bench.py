@@ -18,7 +18,8 @@ variants (their ratio to the headline), the ratios 1e2 and 1e6, the hot
 kernels timed live, and the oracle timed on the host cores.
 --workload scale64: the 64^3 FP64 workload (four fractures, AMG-CG to 1e-10,
 200 steps).  --workload batch / serve / solvers: the batched, served and
-solver-comparison workloads.
+solver-comparison workloads.  --workload tet54 / prism55: the tetrahedral
+mesh of Sec. 5.4 and the prism mesh with wells of Sec. 5.5 at their sizes.
 
 `value` times steps whose inputs already sit in HBM (torch CUDA tensors);
 `e2e` times the same steps from pinned host buffers with the copies in and the
@@ -88,9 +89,10 @@ def parse():
                     help="only the headline step (profiling runs): no solver variants, ratios or kernel timings")
     ap.add_argument("--n", type=int, default=0, help="mesh edge (profiling cases only; 0: the workload's)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=["mixed128", "scale64", "batch", "serve", "solvers"],
+                    choices=["mixed128", "scale64", "batch", "serve", "solvers", "tet54", "prism55"],
                     help="mixed128 (default): the headline line; scale64: the 64^3 FP64 line; batch / serve / "
-                         "solvers: the batched and served workloads and the solver comparison")
+                         "solvers: the batched and served workloads and the solver comparison; tet54 / prism55: "
+                         "the general-cell workloads at the sizes of Sec. 5.4 and Sec. 5.5")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--requests", type=int, default=400)
     return ap.parse_args()
@@ -861,6 +863,187 @@ def headline_arm(args):
         dist.destroy_process_group()
 
 
+SHAPE_WORKLOADS = {
+    "tet54": {
+        "metric": "Darcy solves/s (assemble + solve to 1e-8 rel. residual + 1000 transport steps), Sec. 5.4-size "
+                  "tetrahedral DFN",
+        "desc": ("tet54: 100^3 lattice cubes cut into 6 tetrahedra (6000000 cells, 1030301 nodes), DFN of 30 seeded "
+                 "rectangles (74806 fracture triangles), the physics of Sec. 5.3 (Lambda_m = 1, Lambda_f = 20, "
+                 "phi = 1); FP64 iterative refinement around FP32 CG with the FP32 classical-AMG V-cycle to 1e-8; "
+                 "1000 upwind steps at CFL 0.9"),
+    },
+    "prism55": {
+        "metric": "Darcy solves/s (assemble + solve to 1e-8 rel. residual + 1000 transport steps), Sec. 5.5-size "
+                  "prism mesh with wells",
+        "desc": ("prism55: 5888.75 x 3157.5 x 250 m, 695 x 372 squares cut in two x 24 layers (12409920 prisms, "
+                 "6490200 nodes), 600 vertical fractures (494592 fracture faces), Lambda_f = 1e-11, Lambda_m = 1e-15, "
+                 "phi = 0.1, d_f = 1 m, mu = 1e-3; one injector and two producers with Peaceman indices on 12 "
+                 "perforated layers each, no Dirichlet node; FP64 iterative refinement around FP32 CG with the FP32 "
+                 "classical-AMG V-cycle to 1e-8; 1000 upwind steps at CFL 0.9"),
+    },
+}
+
+
+def shapes_arm(args):
+    """The general-cell workloads at the sizes of the paper's Sec. 5.4
+    (tetrahedra) and Sec. 5.5 (prisms with wells): the step of the headline
+    (assemble through the general descriptor, mixed classical-AMG solve to
+    1e-8, 1000 transport steps) timed on one GPU, with the hot kernels' live
+    timings and the end-to-end leg from pinned host buffers."""
+    import torch
+    import vag_inputs as vi
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_1602_03641_gb300 as pkg
+
+    w = SHAPE_WORKLOADS[args.workload]
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t0 = time.time()
+    if args.workload == "tet54":
+        pb = vi.config_tet54()
+    else:
+        pb = vi.config_prism55()
+        g = pb.meta["well_geometry"]
+        pb.wells = vi.well_arrays(pb, pkg.peaceman_wi(g["dx"], g["dz"], g["d_f"], g["lam_f"], g["r_w"], mu=pb.mu))
+    gen_s = time.time() - t0
+    RTOL, NSTEPS = 1e-8, 1000
+    q = pkg.general_arrays(pb)
+    extra = {"phm": np.ascontiguousarray(pb.phi_m), "phf": np.ascontiguousarray(pb.phi_f),
+             "cb": np.ascontiguousarray(pb.cbar), "c0": pb.c0()}
+
+    def to(v, pinned):
+        if isinstance(v, dict):
+            return {k: to(x, pinned) for k, x in v.items()}
+        if not isinstance(v, np.ndarray):
+            return v
+        t = torch.from_numpy(np.ascontiguousarray(v))
+        if pinned:
+            return t.pin_memory().numpy()
+        return t.to(dev)
+    d = to({**q, **extra}, False)
+    pin = to({**q, **extra}, True)
+    n_cv = pb.n_nodes + pb.n_ff + pb.n_cells
+    ctx = pkg.Context(0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.set_stream(stream.cuda_stream)
+    u_dev = torch.empty(n_cv, dtype=torch.float64, device=dev)
+    c_dev = torch.empty(n_cv, dtype=torch.float64, device=dev)
+    u_pin = torch.empty(n_cv, dtype=torch.float64, pin_memory=True).numpy()
+    c_pin = torch.empty(n_cv, dtype=torch.float64, pin_memory=True).numpy()
+    flush_buf = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
+
+    def assemble(a):
+        return ctx.assemble_general(a["xyz"], a["face_node_ptr"], a["face_node_idx"], a["cell_face_ptr"],
+                                    a["cell_face_idx"], a["ff_face_ids"], a["lambda_m"], a["lambda_f"], a["d_f"],
+                                    a["mu"], a["dir_nodes"], a["dir_values"], a.get("wells"))
+
+    def step(a, u, c, keep=False):
+        s = assemble(a)
+        _, info = s.solve(out=u, precision=pkg.VAG_MIXED, precond=pkg.VAG_PC_AMG_RS, rtol=RTOL, maxit=100000,
+                          raise_on_error=False)
+        if isinstance(c, np.ndarray):
+            c[:] = a["c0"]
+        else:
+            with torch.cuda.stream(stream):
+                c.copy_(a["c0"])
+        tinf = s.transport(c, a["phm"], a["phf"], a["cb"], n_steps=NSTEPS, cfl=0.9)
+        if keep:
+            return info, tinf, s
+        s.close()
+        return info, tinf
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        infos = []
+        for i in range(k):
+            with torch.cuda.stream(stream):
+                flush_buf.zero_()
+            evs[i][0].record(stream)
+            infos.append(fn())
+            evs[i][1].record(stream)
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in evs], infos
+
+    for _ in range(args.warmup):
+        step(d, u_dev, c_dev)
+    torch.cuda.synchronize()
+    gpu_uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    sampler = ClockSampler(str(gpu_uuid) if gpu_uuid is not None else None, 0)
+    lc0 = pkg.launch_count()
+    ms, infos = timed(lambda: step(d, u_dev, c_dev), args.steps)
+    lc1 = pkg.launch_count()
+    clocks = sampler.stop()
+    for i in infos:
+        if i[0].ret != pkg.VAG_OK or i[0].rel_residual > RTOL:
+            raise RuntimeError(f"timed solve did not converge: status {i[0].ret}, residual {i[0].rel_residual:.3e}")
+    e2e = None
+    if not args.no_e2e:
+        step(pin, u_pin, c_pin)
+        ms_h, _ = timed(lambda: step(pin, u_pin, c_pin), args.steps)
+        h2d = sum(v.nbytes for k, v in pin.items() if isinstance(v, np.ndarray)) + \
+            sum(v.nbytes for v in (pin.get("wells") or {}).values())
+        e2e = {"value": args.steps / (sum(ms_h) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(u_pin.nbytes + c_pin.nbytes), "ms_per_step": sum(ms_h) / args.steps}
+    peak, peak_kind = measured_peaks()
+    fp64_peak = fp64_peak_gflops()
+    info0, tinf0, s = step(d, u_dev, c_dev, keep=True)
+    inf = s.info()
+    its, outer = info0.iterations, info0.outer
+    nr, nnz, ncv, nnzt = inf.n_rows, inf.nnz, inf.n_cv, inf.nnz_transport
+    step_ms = sum(ms) / args.steps
+    kern = {}
+
+    def add(name, kid, per_step, nbytes, flops):
+        t = s.kernel_time(kid, 50)
+        kern[name] = {"ms": t, "launches_per_step": per_step, "share_of_step": per_step * t / step_ms,
+                      "bytes": nbytes, "gbs": nbytes / t / 1e6, "frac_hbm": nbytes / t / 1e6 / peak,
+                      "fp64_gflops": flops / t / 1e6, "frac_fp64": flops / t / 1e6 / fp64_peak}
+    n_perf = len(pb.wells["ff"]) if pb.wells else 0
+    add("k_step (upwind transport step)", pkg.VAG_KERNEL_TRANSPORT_STEP, NSTEPS,
+        (ncv + n_perf) * 28 + nnzt * 12, 2 * nnzt + ncv)
+    add("k_spmv32 (FP32 SELL q = A p of the inner CG)", pkg.VAG_KERNEL_SPMV32, its, nnz * 8 + (nr + 1) * 4 + nr * 8, 0)
+    add("k_jac_sell<float> (finest-level l1-Jacobi sweep; x2 with k_resid_sell<float>)", pkg.VAG_KERNEL_SMOOTH,
+        2 * (its + outer), nnz * 8 + (nr + 1) * 4 + nr * 16, 0)
+    # the local matrices: inputs (nodes, coordinates, tensor, face flags) and
+    # the 45 packed entries and the volume written per cell
+    cell_bytes = pb.n_cells * (8 * 4 + 6 * 8 + 6 * 4 + 46 * 8) + pb.n_nodes * 24
+    add("k_cell_local<shape> (local VAG matrices, all cells)", pkg.VAG_KERNEL_CELL_LOCAL, 1, cell_bytes, 0)
+    cn, sh, _ = s.export_cells()
+    shapes = {name: int((sh == k).sum()) for k, name in enumerate(["hexahedra", "tetrahedra", "prisms", "pyramids"])
+              if (sh == k).any()}
+    rates = s.well_rates(n_perf).tolist() if n_perf else []
+    s.close()
+    dom = max(kern, key=lambda k: kern[k]["share_of_step"])
+    kd = kern[dom]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kd["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kd["frac_hbm"], "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": ncu_traffic(dom.split(" ")[0] + "@" + args.workload), "bytes_per_launch": kd["bytes"],
+            "launch_ms": kd["ms"], "share_of_step": kd["share_of_step"]}
+    line = {
+        "metric": w["metric"], "value": args.steps / (sum(ms) / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": w["desc"], "cells": pb.n_cells, "shapes": shapes, "nodes": pb.n_nodes,
+                   "fracture_faces": pb.n_ff, "perforations": n_perf, "n_rows": nr, "nnz": nnz, "n_cv": ncv,
+                   "precision": "mixed", "precond": "classical AMG", "rtol": RTOL, "transport_steps": NSTEPS,
+                   "l2": "flushed before every timed step (256 MiB write)", "generator_s": gen_s},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "iterations": infos[-1][0].iterations, "refinements": infos[-1][0].outer,
+        "rel_residual": infos[-1][0].rel_residual,
+        "phases_ms": {"of_which_precond_setup": infos[-1][0].ms_setup,
+                      "of_which_krylov_recovery_fluxes": infos[-1][0].ms_solve,
+                      "of_which_transport_steps": infos[-1][1].ms},
+        "kernels": kern, "kernel_share_of_step": sum(k["share_of_step"] for k in kern.values()), "roofline": roof,
+        "gpu_launches": int(lc1 - lc0), "clocks": clocks, "e2e": e2e,
+    }
+    if n_perf:
+        line["well_rates_m3_per_s"] = {"injected": -sum(r for r in rates if r < 0),
+                                       "produced": sum(r for r in rates if r > 0)}
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -874,6 +1057,9 @@ def main():
         return
     if args.workload == "solvers":
         solvers_arm(args)
+        return
+    if args.workload in SHAPE_WORKLOADS:
+        shapes_arm(args)
         return
     headline_arm(args)
 

@@ -418,8 +418,11 @@ enum {
                                      last AMG hierarchy (FP64, or FP32 after a
                                      mixed-precision AMG solve)                    */
   VAG_KERNEL_TRANSPORT_STEP = 2,  /* one explicit upwind step c' = d c + W c          */
-  VAG_KERNEL_SPMV32 = 3           /* q = A p and p.q in FP32, sliced ELL (the inner
+  VAG_KERNEL_SPMV32 = 3,          /* q = A p and p.q in FP32, sliced ELL (the inner
                                      CG product of a VAG_MIXED AMG solve)          */
+  VAG_KERNEL_CELL_LOCAL = 4       /* the local VAG matrices of every cell (one
+                                     launch per cell shape present; the time is
+                                     that of all of them)                          */
 };
 
 /*
@@ -429,7 +432,8 @@ enum {
  * VAG_KERNEL_SMOOTH needs the AMG hierarchy of a previous vag_solve with
  * VAG_PC_AMG (VAG_MIXED_F16's FP16 finest level excepted);
  * VAG_KERNEL_SPMV32 needs a previous VAG_MIXED or VAG_MIXED_F16 solve with
- * VAG_PC_AMG and CG; VAG_KERNEL_TRANSPORT_STEP needs the upwind map of a
+ * VAG_PC_AMG and CG; VAG_KERNEL_CELL_LOCAL rewrites the system's local
+ * matrices with the same values; VAG_KERNEL_TRANSPORT_STEP needs the upwind map of a
  * previous vag_transport; VAG_EINVAL otherwise, or for reps < 1.  The kernels
  * run on the system's Krylov and transport work vectors, whose contents are
  * overwritten (the solution and the concentrations already returned are not

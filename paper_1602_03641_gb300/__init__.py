@@ -10,5 +10,5 @@ from .vag import (  # noqa: F401
     VAG_OK, VAG_EINVAL, VAG_ENOMEM, VAG_EBUDGET, VAG_ENOTCONVERGED, VAG_EBREAKDOWN, VAG_ETIMEOUT,
     VAG_ECUDA, VAG_EMESH, VAG_MEM_HOST, VAG_MEM_DEVICE, VAG_FP64, VAG_MIXED, VAG_MIXED_F16, VAG_FP64_PC32,
     VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG, VAG_PC_AMG_RS, VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP,
-    VAG_KERNEL_SPMV32, VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB, VAG_KRYLOV_GMRES,
+    VAG_KERNEL_SPMV32, VAG_KERNEL_CELL_LOCAL, VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB, VAG_KRYLOV_GMRES,
 )

@@ -365,7 +365,44 @@ __global__ void k_wells(int n_perf, int nv, const int *__restrict__ ff, const do
   dinv[r] = 1.0 / d;
 }
 
+// The local matrices of every cell: one launch for a mesh of hexahedra, one
+// launch per shape over its cell list otherwise.
+void launch_cell_local(System *s, double inv_mu) {
+  cudaStream_t st = s->ctx->stream;
+  if (!s->cell_shape) {
+    k_cell_local<topo::HEX><<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, nullptr, s->nc, s->cell_nodes, s->xyz,
+                                                                   s->lam, inv_mu, s->cell_ff, s->fc_index, s->n_fc,
+                                                                   s->Mc, s->Mfc, s->cvol, s->status);
+    note_launches(1);
+    return;
+  }
+  decltype(&k_cell_local<topo::HEX>) kern[topo::N_SHAPES] = {k_cell_local<topo::HEX>, k_cell_local<topo::TET>,
+                                                             k_cell_local<topo::PRISM>, k_cell_local<topo::PYRAMID>};
+  for (int sh = 0; sh < topo::N_SHAPES; ++sh) {
+    const int n = s->shape_start[sh + 1] - s->shape_start[sh];
+    if (!n) continue;
+    kern[sh]<<<grid_for(n, 128), 128, 0, st>>>(n, s->shape_cells + s->shape_start[sh], s->nc, s->cell_nodes,
+                                               s->xyz, s->lam, inv_mu, s->cell_ff, s->fc_index, s->n_fc, s->Mc,
+                                               s->Mfc, s->cvol, s->status);
+    note_launches(1);
+  }
+}
+
 }  // namespace
+
+double time_cell_local(System *s, int reps) {
+  if (!s->Mc) fail(VAG_EINVAL, "no local matrices: assemble first");
+  cudaStream_t st = s->ctx->stream;
+  const double inv_mu = 1.0 / s->mu;
+  launch_cell_local(s, inv_mu);   // warm-up
+  VAG_CUDA(cudaEventRecord(s->ev0, st));
+  for (int r = 0; r < reps; ++r) launch_cell_local(s, inv_mu);
+  VAG_CUDA(cudaEventRecord(s->ev1, st));
+  VAG_CUDA(cudaEventSynchronize(s->ev1));
+  float ms = 0.f;
+  VAG_CUDA(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  return (double)ms / reps;
+}
 
 void numeric_phase(System *s) {
   cudaStream_t st = s->ctx->stream;
@@ -381,23 +418,7 @@ void numeric_phase(System *s) {
   }
   VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   const double inv_mu = 1.0 / s->mu;
-  if (!s->cell_shape) {
-    k_cell_local<topo::HEX><<<grid_for(s->nc, 128), 128, 0, st>>>(s->nc, nullptr, s->nc, s->cell_nodes, s->xyz,
-                                                                   s->lam, inv_mu, s->cell_ff, s->fc_index, s->n_fc,
-                                                                   s->Mc, s->Mfc, s->cvol, s->status);
-    note_launches(1);
-  } else {   // one launch per shape over its cell list
-    decltype(&k_cell_local<topo::HEX>) kern[topo::N_SHAPES] = {k_cell_local<topo::HEX>, k_cell_local<topo::TET>,
-                                                               k_cell_local<topo::PRISM>, k_cell_local<topo::PYRAMID>};
-    for (int sh = 0; sh < topo::N_SHAPES; ++sh) {
-      const int n = s->shape_start[sh + 1] - s->shape_start[sh];
-      if (!n) continue;
-      kern[sh]<<<grid_for(n, 128), 128, 0, st>>>(n, s->shape_cells + s->shape_start[sh], s->nc, s->cell_nodes,
-                                                 s->xyz, s->lam, inv_mu, s->cell_ff, s->fc_index, s->n_fc, s->Mc,
-                                                 s->Mfc, s->cvol, s->status);
-      note_launches(1);
-    }
-  }
+  launch_cell_local(s, inv_mu);
   VAG_CHECK_LAUNCH();
   if (s->nf) {
     k_ff_local<<<grid_for(s->nf, 128), 128, 0, st>>>(s->nf, s->ff_nodes, s->xyz, s->lamf, s->df, inv_mu, s->Mff,

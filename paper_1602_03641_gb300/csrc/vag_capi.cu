@@ -625,6 +625,7 @@ vag_status vag_kernel_time(vag_system *sys, int kernel, int32_t reps, double *ms
       case VAG_KERNEL_SMOOTH: *ms_per_launch = time_smoother(s, reps); break;
       case VAG_KERNEL_TRANSPORT_STEP: *ms_per_launch = time_transport_step(s, reps); break;
       case VAG_KERNEL_SPMV32: *ms_per_launch = time_spmv32(s, reps); break;
+      case VAG_KERNEL_CELL_LOCAL: *ms_per_launch = time_cell_local(s, reps); break;
       default: fail(VAG_EINVAL, "unknown kernel");
     }
     VAG_CHECK_LAUNCH();
@@ -676,7 +677,7 @@ vag_status vag_transport(vag_system *sys, const vag_transport_opts *o, double *c
     trace_mark(st, "start");
     const size_t n = s->n_cv;
     // stage porosities, cbar and c
-    if (!o->phi_m || (s->nf && !o->phi_f) || !o->cbar) fail(VAG_EINVAL, "null porosity or cbar");
+    if (!o->phi_m || (s->nf && !o->phi_f) || (s->nd && !o->cbar)) fail(VAG_EINVAL, "null porosity or cbar");
     double *stage;
     const size_t tot = (size_t)s->nc + s->nf + s->nd + (o->mem == VAG_MEM_HOST ? n : 0);
     VAG_CUDA(cudaMallocAsync(&stage, sizeof(double) * (tot ? tot : 1), st));

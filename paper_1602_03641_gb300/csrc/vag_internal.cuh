@@ -404,6 +404,7 @@ unsigned general_to_cells(Ctx *c, const vag_mesh &m, int mem, int32_t *cell_node
 // ------------------------------------------------------------- phases -----
 void symbolic_phase(System *s);
 void numeric_phase(System *s);
+double time_cell_local(System *s, int reps);   // mean ms of the local-matrix launches of one numeric phase
 void pcg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void bicgstab_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);
 void gmres_solve(System *s, const vag_solve_opts *o, vag_solve_info *info);

@@ -25,6 +25,7 @@ VAG_FP64, VAG_MIXED, VAG_MIXED_F16, VAG_FP64_PC32 = 0, 1, 2, 3
 VAG_PC_JACOBI, VAG_PC_CHEBYSHEV, VAG_PC_AMG, VAG_PC_AMG_RS = 0, 1, 2, 3
 VAG_KRYLOV_CG, VAG_KRYLOV_BICGSTAB, VAG_KRYLOV_GMRES = 0, 1, 2
 VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP, VAG_KERNEL_SPMV32 = 0, 1, 2, 3
+VAG_KERNEL_CELL_LOCAL = 4
 VAG_SHAPE_HEX, VAG_SHAPE_TET, VAG_SHAPE_PRISM, VAG_SHAPE_PYRAMID = 0, 1, 2, 3
 # local faces of each shape, each cyclic (the library's tables, include/vag.h)
 SHAPE_FACES = {
@@ -433,7 +434,8 @@ class System:
 
     def kernel_time(self, kernel, reps=100):
         """Mean ms of one launch of a hot kernel on this system's data
-        (VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP, VAG_KERNEL_SPMV32)."""
+        (VAG_KERNEL_SPMV, VAG_KERNEL_SMOOTH, VAG_KERNEL_TRANSPORT_STEP, VAG_KERNEL_SPMV32,
+        VAG_KERNEL_CELL_LOCAL)."""
         ms = C.c_double()
         self.ctx.check(self._L.vag_kernel_time(self.h, int(kernel), int(reps), C.byref(ms)))
         return ms.value

@@ -48,7 +48,7 @@ __all__ = [
     "Problem", "hex_lattice", "axis_fracture_faces", "build_problem",
     "config_plain16", "config_scale64", "config_mixed128", "random_dfn_problem",
     "one_fracture_problem", "four_fracture_problem", "batch_problems", "tet_problem", "prism_problem",
-    "pyramid_problem", "well_problem", "well_arrays",
+    "pyramid_problem", "well_problem", "well_arrays", "config_tet54", "config_prism55",
 ]
 
 
@@ -493,8 +493,14 @@ def tet_problem(dims, fractures: Sequence[Tuple] = (), *, jitter=0.0, seed=0, la
     n_cells = cell_nodes.shape[0]
     tri = np.concatenate([cell_nodes[:, [1, 2, 3]], cell_nodes[:, [0, 2, 3]], cell_nodes[:, [0, 1, 3]],
                           cell_nodes[:, [0, 1, 2]]])
-    key = np.sort(tri, axis=1)
-    faces, inv = np.unique(key, axis=0, return_inverse=True)
+    key = np.sort(tri, axis=1).astype(np.int64)
+    nn = (nx + 1) * (ny + 1) * (nz + 1)
+    if nn < (1 << 21):   # one int64 per triangle: the same order as the rows, much faster
+        code = (key[:, 0] << 42) | (key[:, 1] << 21) | key[:, 2]
+        ucode, inv = np.unique(code, return_inverse=True)
+        faces = np.stack([ucode >> 42, (ucode >> 21) & ((1 << 21) - 1), ucode & ((1 << 21) - 1)], axis=1)
+    else:
+        faces, inv = np.unique(key, axis=0, return_inverse=True)
     faces = faces.astype(np.int32)
     cell_faces = inv.reshape(4, n_cells).T.astype(np.int32)
     # lattice index of every node
@@ -502,13 +508,20 @@ def tet_problem(dims, fractures: Sequence[Tuple] = (), *, jitter=0.0, seed=0, la
     ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
     ids, owner = [], []
     frozen = np.zeros((ijk.shape[0], 3), bool)
+    # the triangles lying on a lattice plane of each axis, with their nodes' lattice indices
+    on_plane = {}
+    if len(fractures):
+        fi = ijk[faces]                                          # [n_faces, 3 nodes, 3 axes]
+        for ax in range(3):
+            sel = np.nonzero((fi[:, 0, ax] == fi[:, 1, ax]) & (fi[:, 0, ax] == fi[:, 2, ax]))[0]
+            on_plane[ax] = (sel, fi[sel])
     for f_idx, (axis, plane, lo_a, hi_a, lo_b, hi_b) in enumerate(fractures):
         oa, ob = [a for a in range(3) if a != axis]
-        fi = ijk[faces]                                          # [n_faces, 3 nodes, 3 axes]
-        on = np.all(fi[:, :, axis] == plane, axis=1)
-        ina = np.all((fi[:, :, oa] >= lo_a) & (fi[:, :, oa] <= hi_a), axis=1)
-        inb = np.all((fi[:, :, ob] >= lo_b) & (fi[:, :, ob] <= hi_b), axis=1)
-        fid = np.nonzero(on & ina & inb)[0]
+        sel, fs = on_plane[axis]
+        on = fs[:, 0, axis] == plane
+        ina = np.all((fs[:, :, oa] >= lo_a) & (fs[:, :, oa] <= hi_a), axis=1)
+        inb = np.all((fs[:, :, ob] >= lo_b) & (fs[:, :, ob] <= hi_b), axis=1)
+        fid = sel[np.nonzero(on & ina & inb)[0]]
         ids.append(fid)
         owner.append(np.full(fid.shape, f_idx))
         frozen[np.unique(faces[fid].ravel()), axis] = True
@@ -642,34 +655,67 @@ def prism_problem(nxy, nz, fractures: Sequence[Tuple] = (), *, split="all", jitt
     cell_nodes = cell_nodes.astype(np.int32)
     k3, j3, i3 = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
     ijk = np.stack([i3.ravel(), j3.ravel(), k3.ravel()], axis=1)
-    quad = faces[:, 3] >= 0
-    fi = ijk[np.where(faces >= 0, faces, 0)]                     # [n_faces, 4, 3]
-    ids, owner = [], []
-    frozen = np.zeros((ijk.shape[0], 3), bool)
-    for f_idx, (kind, plane, a0, a1, k0, k1) in enumerate(fractures):
-        ii, jj, kk = fi[:, :, 0], fi[:, :, 1], fi[:, :, 2]
-        inz = np.all((kk >= k0) & (kk <= k1), axis=1)
-        if kind == "x":
-            sel = np.all(ii == plane, axis=1) & np.all((jj >= a0) & (jj <= a1), axis=1)
-            fr = (0,)
-        elif kind == "y":
-            sel = np.all(jj == plane, axis=1) & np.all((ii >= a0) & (ii <= a1), axis=1)
-            fr = (1,)
-        elif kind == "d":
-            sel = np.all(ii - jj == plane, axis=1) & np.all((ii >= a0) & (ii <= a1), axis=1)
-            fr = (0, 1)
+    # fracture faces: vertical quadrilaterals over listed edges of the 2-D mesh
+    up2 = (nx + 1) * (ny + 1)
+
+    def n2(i, j):
+        return np.asarray(i, np.int64) + (nx + 1) * np.asarray(j, np.int64)
+
+    fkeys, fown, fz = [], [], []
+    for f_idx, spec in enumerate(fractures):
+        kind = spec[0]
+        if kind == "e":                  # ("e", edges [m, 2] of 2-D node ids, k0, k1)
+            _, e2, k0, k1 = spec
+            a, b = np.asarray(e2, np.int64)[:, 0], np.asarray(e2, np.int64)[:, 1]
+            frz = (0, 1)
         else:
-            raise ValueError(kind)
-        fid = np.nonzero(sel & inz & quad)[0]
-        ids.append(fid)
-        owner.append(np.full(fid.shape, f_idx))
-        for ax in fr:
-            frozen[np.unique(faces[fid].ravel()), ax] = True
-    if ids:
-        allid = np.concatenate(ids)
-        allown = np.concatenate(owner)
-        ff_faces, first = np.unique(allid, return_index=True)
-        ff_frac = allown[first].astype(np.int32)
+            _, plane, a0, a1, k0, k1 = spec
+            t = np.arange(a0, a1)
+            if kind == "x":
+                a, b, frz = n2(plane, t), n2(plane, t + 1), (0,)
+            elif kind == "y":
+                a, b, frz = n2(t, plane), n2(t + 1, plane), (1,)
+            elif kind == "d":
+                t = t[(t - plane >= 0) & (t + 1 - plane <= ny)]
+                a, b, frz = n2(t, t - plane), n2(t + 1, t + 1 - plane), (0, 1)
+            else:
+                raise ValueError(kind)
+        e = np.minimum(a, b) * up2 + np.maximum(a, b)
+        for k in range(k0, k1):
+            fkeys.append(e * nz + k)
+            fown.append(np.full(e.shape, f_idx))
+            fz.append((np.stack([a, b], 1), k, frz))
+    quad = faces[:, 3] >= 0
+    f64 = np.where(faces >= 0, faces, 0).astype(np.int64)
+    f2 = np.sort(f64 % up2, axis=1)                                # 2-D nodes of each face
+    fk = f64 // up2                                                # layers of each face
+    # a vertical quadrilateral: two 2-D nodes, each twice, on layers k and k + 1
+    vertical = (quad & (f2[:, 0] == f2[:, 1]) & (f2[:, 2] == f2[:, 3]) & (f2[:, 1] != f2[:, 2]) &
+                (fk.min(axis=1) + 1 == fk.max(axis=1)))
+    lo2, hi2 = f2[:, 0], f2[:, 2]
+    face_key = np.where(vertical, (lo2 * up2 + hi2) * nz + fk.min(axis=1), -1)
+    frozen = np.zeros((ijk.shape[0], 3), bool)
+    if fkeys:
+        K_ = np.concatenate(fkeys)
+        O_ = np.concatenate(fown)
+        order = np.lexsort((O_, K_))
+        K_, O_ = K_[order], O_[order]
+        keep = np.ones(K_.size, bool)
+        keep[1:] = K_[1:] != K_[:-1]
+        K_, O_ = K_[keep], O_[keep]                                # each face once, its first fracture
+        pos = np.searchsorted(K_, face_key)
+        pos = np.minimum(pos, K_.size - 1)
+        hit = vertical & (K_[pos] == face_key)
+        ff_faces = np.nonzero(hit)[0]
+        ff_frac = O_[pos[ff_faces]].astype(np.int32)
+        for (e2, k, frz) in fz:
+            nodes = np.concatenate([e2.ravel() + k * up2, e2.ravel() + (k + 1) * up2])
+            for ax in frz:
+                frozen[nodes, ax] = True
+        # freeze only nodes of faces that exist as fracture faces
+        used = np.zeros(ijk.shape[0], bool)
+        used[faces[ff_faces].ravel()] = True
+        frozen &= used[:, None]
     else:
         ff_faces = np.zeros(0, np.int64)
         ff_frac = np.zeros(0, np.int32)
@@ -789,6 +835,43 @@ def pyramid_problem(dims, fractures: Sequence[Tuple] = (), *, jitter=0.0, seed=0
         meta=dict(meta or {}, name=f"pyramid{nx}x{ny}x{nz}", seed=seed))
 
 
+def _place_wells(pb, nxy, nz, specs, k0, k1, lam_f, d_f, r_w, q_inj):
+    """Wells at fracture edges of an extruded mesh: specs lists (kind, 2-D
+    node a, 2-D node b) with a -> b an edge of the triangular mesh carrying
+    a fracture; each well perforates that edge's fracture faces in layers
+    k0 <= k < k1.  Fills meta["well_geometry"] and meta["wells"]."""
+    nx, ny = nxy
+    up2 = (nx + 1) * (ny + 1)
+    fn = np.sort(pb.ff_nodes.astype(np.int64), axis=1)         # vertical quads: [a, b, a', b'] sorted
+    f2 = np.sort(fn % up2, axis=1)
+    fkey = (f2[:, 0] * up2 + f2[:, 2]) * nz + (fn // up2).min(axis=1)
+    order = np.argsort(fkey)
+    ff, well, dx, dz = [], [], [], []
+    wells = []
+    for w, (kind, a, b) in enumerate(specs):
+        e = min(a, b) * up2 + max(a, b)
+        want = e * nz + np.arange(k0, k1)
+        pos = np.searchsorted(fkey[order], want)
+        pos = np.minimum(pos, fkey.size - 1)
+        hit = fkey[order][pos] == want
+        perf = order[pos[hit]]
+        if not perf.size:
+            raise ValueError(f"well {w}: no fracture face on its edge")
+        for i in perf:
+            p = pb.xyz[pb.ff_nodes[i]]
+            bot = np.argsort(p[:, 2])[:2]
+            dx.append(float(np.linalg.norm(p[bot[0], :2] - p[bot[1], :2])))
+            dz.append(float(p[:, 2].max() - p[:, 2].min()))
+            ff.append(int(i))
+            well.append(w)
+        wells.append(dict(kind=kind, pw=0.0, rate=q_inj if kind == "injector" else 0.0,
+                          cin=1.0 if kind == "injector" else 0.0))
+    pb.meta["well_geometry"] = dict(ff=np.array(ff, np.int32), well=np.array(well, np.int32), dx=np.array(dx),
+                                    dz=np.array(dz), d_f=np.full(len(ff), float(d_f)),
+                                    lam_f=np.full(len(ff), float(lam_f)), r_w=np.full(len(ff), float(r_w)))
+    pb.meta["wells"] = wells
+
+
 def well_problem(nxy=(12, 8), nz=6, *, split="all", lengths=(600.0, 400.0, 60.0), jitter=0.15, seed=0,
                  lam_m=1e-15, lam_f=1e-11, d_f=1.0, phi=0.1, mu=1e-3, r_w=0.1, q_inj=0.16, dirichlet=None,
                  meta=None) -> Problem:
@@ -813,44 +896,81 @@ def well_problem(nxy=(12, 8), nz=6, *, split="all", lengths=(600.0, 400.0, 60.0)
     lam = np.zeros((pb.n_cells, 6)); lam[:, :3] = lam_m
     pb.lambda_m = lam
     pb.mu = float(mu)
-    dims = (nx, ny, nz)
-    k0, k1 = nz // 4, nz - nz // 4          # perforated layers k0 <= k < k1
 
-    def edge_faces(a, b):
-        """fracture faces of the vertical strip over lattice nodes a -> b"""
-        out = []
-        for k in range(k0, k1):
-            want = sorted([_nid(dims, *a, k), _nid(dims, *b, k), _nid(dims, *a, k + 1), _nid(dims, *b, k + 1)])
-            for i, f in enumerate(pb.ff_nodes):
-                if sorted(f.tolist()) == want:
-                    out.append(i)
-        return out
-
-    specs = [("injector", (i_f, ny // 4), (i_f, ny // 4 + 1)),
-             ("producer", (nx - 2, j_f), (nx - 1, j_f)),
-             ("producer", (1, 1), (2, 2))]
-    ff, well, dx, dz = [], [], [], []
-    wells = []
-    for w, (kind, a, b) in enumerate(specs):
-        perf = edge_faces(a, b)
-        if not perf:
-            raise ValueError(f"well {w}: no fracture face on its edge")
-        for i in perf:
-            n = pb.ff_nodes[i]
-            p = pb.xyz[n]
-            bot = np.argsort(p[:, 2])[:2]
-            dx.append(float(np.linalg.norm(p[bot[0], :2] - p[bot[1], :2])))
-            dz.append(float(p[:, 2].max() - p[:, 2].min()))
-            ff.append(i)
-            well.append(w)
-        wells.append(dict(kind=kind, pw=0.0, rate=q_inj if kind == "injector" else 0.0,
-                          cin=1.0 if kind == "injector" else 0.0))
-    pb.meta["well_geometry"] = dict(ff=np.array(ff, np.int32), well=np.array(well, np.int32), dx=np.array(dx),
-                                    dz=np.array(dz), d_f=np.full(len(ff), float(d_f)),
-                                    lam_f=np.full(len(ff), float(lam_f)), r_w=np.full(len(ff), float(r_w)))
-    pb.meta["wells"] = wells
+    def n2(i, j):
+        return i + (nx + 1) * j
+    specs = [("injector", n2(i_f, ny // 4), n2(i_f, ny // 4 + 1)),
+             ("producer", n2(nx - 2, j_f), n2(nx - 1, j_f)),
+             ("producer", n2(1, 1), n2(2, 2))]
+    _place_wells(pb, nxy, nz, specs, nz // 4, nz - nz // 4, lam_f, d_f, r_w, q_inj)
     pb.meta["name"] = f"wells{nx}x{ny}x{nz}_{split}"
     return pb
+
+
+def config_prism55(nxy=(695, 372), nz=24, n_frac=600, seed=5505, jitter=0.15) -> Problem:
+    """The complex fracture network of Sec. 5.5 at its size, synthetic: the
+    domain 5888.75 x 3157.5 x 250 m, the tensor product of a triangular mesh
+    (nxy squares cut in two: 517 080 triangles) with 24 uniform layers
+    (12.4 M prisms, 6.5 M nodes); n_frac vertical fractures through the whole
+    height, each a run of U{10..60} consecutive mesh edges along a lattice
+    line or a cut diagonal (about 21 000 edges, 5.1e5 fracture faces);
+    Lambda_f = 1e-11, Lambda_m = 1e-15 m^2, phi = 0.1, d_f = 1 m, mu = 1e-3;
+    one injector (5e6 m^3 a year, c = 1) and two producers (p_w = 0), each at
+    the middle of a fracture edge nearest to (0.2, 0.5), (0.8, 0.25) and
+    (0.8, 0.75) of the plan, perforating the 12 central layers; no Dirichlet
+    node."""
+    rng = np.random.default_rng(seed)
+    nx, ny = nxy
+    L = (5888.75, 3157.5, 250.0)
+
+    def n2(i, j):
+        return np.asarray(i, np.int64) + (nx + 1) * np.asarray(j, np.int64)
+    edges = []
+    for _ in range(n_frac):
+        kind = int(rng.integers(0, 3))
+        m = int(rng.integers(10, 61))
+        i0 = int(rng.integers(0, nx - m)) if kind != 1 else int(rng.integers(0, nx))
+        j0 = int(rng.integers(0, ny - m)) if kind != 0 else int(rng.integers(0, ny))
+        t = np.arange(m)
+        if kind == 0:        # along x
+            a, b = n2(i0 + t, j0), n2(i0 + t + 1, j0)
+        elif kind == 1:      # along y
+            a, b = n2(i0, j0 + t), n2(i0, j0 + t + 1)
+        else:                # along the cut diagonal
+            a, b = n2(i0 + t, j0 + t), n2(i0 + t + 1, j0 + t + 1)
+        edges.append(("e", np.stack([a, b], 1), 0, nz))
+    pb = prism_problem(nxy, nz, edges, split="all", jitter=jitter, seed=seed + 1, ratio=1e-11, d_f=1.0,
+                       phi_m=0.1, phi_f=0.1, dirichlet=None, lengths=L)
+    lam = np.zeros((pb.n_cells, 6)); lam[:, :3] = 1e-15
+    pb.lambda_m = lam
+    pb.mu = 1e-3
+    # well edges: the fracture edge (bottom layer) whose midpoint is nearest each target
+    up2 = (nx + 1) * (ny + 1)
+    fn = pb.ff_nodes.astype(np.int64)
+    bottom = fn[(fn // up2).max(axis=1) == 1]
+    e2 = np.sort(np.sort(bottom % up2, axis=1)[:, [0, 2]], axis=1)
+    xy = np.stack([(e2 % (nx + 1)) / nx * L[0], (e2 // (nx + 1)) / ny * L[1]], axis=-1).mean(axis=1)
+    specs = []
+    for kind, (tx, ty) in (("injector", (0.2, 0.5)), ("producer", (0.8, 0.25)), ("producer", (0.8, 0.75))):
+        i = int(np.argmin(np.hypot(xy[:, 0] - tx * L[0], xy[:, 1] - ty * L[1])))
+        specs.append((kind, int(e2[i, 0]), int(e2[i, 1])))
+    _place_wells(pb, nxy, nz, specs, 6, 18, 1e-11, 1.0, 0.1, 5.0e6 / (365.0 * 86400.0))
+    pb.meta["name"] = f"prism55_{nx}x{ny}x{nz}"
+    pb.meta["seed"] = seed
+    return pb
+
+
+def config_tet54(n=100, n_frac=30, seed=5404) -> Problem:
+    """The tetrahedral test case of Sec. 5.4 at its size, synthetic: n^3
+    lattice cubes cut into six tetrahedra each (6.0 M cells, 1.03 M nodes at
+    n = 100) with a DFN of n_frac seeded lattice rectangles (about 7e4
+    fracture triangles); the physics of Sec. 5.3: Lambda_m = 1, Lambda_f = 20,
+    phi_m = phi_f = 1, mu = 1, d_f = 1e-2."""
+    rng = np.random.default_rng(seed)
+    fr = random_rectangles(n, n_frac, rng)
+    sub = int(rng.integers(0, 2**31 - 1))
+    return tet_problem((n, n, n), fr, jitter=0.2, seed=sub, lam_m="identity", ratio=20.0, d_f=1e-2,
+                       phi_m=1.0, phi_f=1.0, meta={"name": f"tet54_{n}", "seed": seed})
 
 
 def well_arrays(pb, wi):
