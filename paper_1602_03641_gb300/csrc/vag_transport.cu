@@ -258,21 +258,37 @@ __device__ __forceinline__ bool is_dir(const TView &t, int mu) {
 
 // Per CV: number of inflow edges and the CFL ratio phi / outflow; the ratio
 // is min-reduced per system with atomicMin on the bit pattern of a positive
-// double (order-independent, hence deterministic).
+// double (order-independent, hence deterministic).  A warp whose control
+// volumes all belong to one system reduces first and makes one atomic.
 __global__ void __launch_bounds__(TB) k_map_count(TView t, int n, const double *__restrict__ phi,
                                                   const int *__restrict__ cv_sys, int *__restrict__ cnt,
                                                   unsigned long long *dt_bits) {
   const int mu = blockIdx.x * TB + threadIdx.x;
-  if (mu >= n) return;
-  if (is_dir(t, mu)) { cnt[mu] = 0; return; }
-  int c = 0;
-  double out = 0.0;
-  for_edges(t, mu, [&](double Fin, int) {
-    if (Fin > 0.0) ++c;
-    else out -= Fin;
-  });
-  cnt[mu] = c;
-  if (out > 0.0) atomicMin(&dt_bits[cv_sys[mu]], (unsigned long long)__double_as_longlong(phi[mu] / out));
+  unsigned long long bits = ~0ull;   // no bound
+  int sys = -1;
+  if (mu < n) {
+    if (is_dir(t, mu)) {
+      cnt[mu] = 0;
+    } else {
+      int c = 0;
+      double out = 0.0;
+      for_edges(t, mu, [&](double Fin, int) {
+        if (Fin > 0.0) ++c;
+        else out -= Fin;
+      });
+      cnt[mu] = c;
+      sys = cv_sys[mu];
+      if (out > 0.0) bits = (unsigned long long)__double_as_longlong(phi[mu] / out);
+    }
+  }
+  const int s0 = __shfl_sync(0xffffffffu, sys, 0);
+  if (__all_sync(0xffffffffu, sys == s0 || sys < 0) && s0 >= 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bits = min(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+    if ((threadIdx.x & 31) == 0 && bits != ~0ull) atomicMin(&dt_bits[s0], bits);
+  } else if (sys >= 0 && bits != ~0ull) {
+    atomicMin(&dt_bits[sys], bits);
+  }
 }
 
 // Per system: dts[2g] = CFL bound (bits -> double), dts[2g+1] = the step
