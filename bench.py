@@ -830,7 +830,8 @@ def headline_arm(args):
             "frac": kd["frac_hbm"], "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
             "secondary": {"bound": "alu", "achieved": kd["fp64_gflops"] / 1e3, "peak": fp64_peak / 1e3,
                           "unit": "TFLOP/s (FP64)", "frac": kd["frac_fp64"]},
-            "traffic": ncu_traffic(dom.split(" ")[0] + ("@" + workload)), "bytes_per_launch": kd["bytes"],
+            "traffic": ncu_traffic(dom.split(" ")[0] + ("@" + workload)) if full_size else None,
+            "bytes_per_launch": kd["bytes"],
             "launch_ms": kd["ms"], "share_of_step": kd["share_of_step"]}
     explained = sum(k["share_of_step"] for k in kern.values())
 

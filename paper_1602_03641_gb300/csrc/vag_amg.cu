@@ -468,15 +468,17 @@ __device__ __forceinline__ T row_csr(int i, bool valid, int lane, const int *__r
 }
 
 // The same row product split in two for programmatic dependent launch: the
-// first kPF entries of each lane (matrix data, written by no kernel of the
+// first pf<T>() entries of each lane (matrix data, written by no kernel of the
 // cycle) are loaded before pdl_wait(), the x gathers after it.  Entries are
-// multiplied in the same order as row_csr, so the sum is identical.
-constexpr int kPF = 4;
+// multiplied in the same order as row_csr, so the sum is identical.  (Eight
+// entries a lane for FP32 was measured slower on the classical levels.)
+template <class T>
+__host__ __device__ constexpr int pf() { return 4; }
 template <class T>
 struct RowPF {
   int k, ke;
-  int c[kPF];
-  T v[kPF];
+  int c[pf<T>()];
+  T v[pf<T>()];
 };
 template <int LN, class T>
 __device__ __forceinline__ void row_prefetch(RowPF<T> &f, int i, bool valid, int lane, const int *__restrict__ rowptr,
@@ -484,7 +486,7 @@ __device__ __forceinline__ void row_prefetch(RowPF<T> &f, int i, bool valid, int
   f.k = valid ? rowptr[i] + lane : 0;
   f.ke = valid ? rowptr[i + 1] : 0;
 #pragma unroll
-  for (int u = 0; u < kPF; ++u) {
+  for (int u = 0; u < pf<T>(); ++u) {
     const int k = f.k + LN * u;
     f.c[u] = k < f.ke ? col[k] : 0;
     f.v[u] = k < f.ke ? val[k] : (T)0;
@@ -495,9 +497,9 @@ __device__ __forceinline__ T row_finish(const RowPF<T> &f, const int *__restrict
                                         const T *__restrict__ x) {
   T s = 0;
 #pragma unroll
-  for (int u = 0; u < kPF; ++u)
+  for (int u = 0; u < pf<T>(); ++u)
     if (f.k + LN * u < f.ke) s = fma(f.v[u], x[f.c[u]], s);
-  for (int k = f.k + LN * kPF; k < f.ke; k += LN) s = fma(val[k], x[col[k]], s);
+  for (int k = f.k + LN * pf<T>(); k < f.ke; k += LN) s = fma(val[k], x[col[k]], s);
   return lane_reduce<LN>(s);
 }
 
@@ -529,8 +531,9 @@ __global__ void __launch_bounds__(256) k_resid_csr(int n, const int *__restrict_
   row_prefetch<LN>(f, i, valid, lane, rowptr, col, val);
   pdl_wait();
   pdl_trigger();
+  const T bi = valid && lane == 0 ? b[i] : (T)0;   // in flight with the gathers
   const T s = row_finish<LN>(f, col, val, x);
-  if (valid && lane == 0) r[i] = b[i] - s;
+  if (valid && lane == 0) r[i] = bi - s;
 }
 
 // x_out = x_in + omega D_l1^-1 (b - A x_in) on a coarse level, row_lanes<T>()
@@ -551,8 +554,9 @@ __global__ void __launch_bounds__(256) k_jac_csr(int n, const int *__restrict__ 
   const T si = own ? sinv[i] : (T)0;
   pdl_wait();
   pdl_trigger();
+  const T bi = own ? b[i] : (T)0, xi = own ? xin[i] : (T)0;   // in flight with the gathers
   const T s = row_finish<LN>(f, col, val, xin);
-  if (own) xout[i] = jac_row(xin[i], si, b[i], s);
+  if (own) xout[i] = jac_row(xi, si, bi, s);
 }
 
 // same sweep in the sliced-ELL layout (level 0), one thread per row
@@ -757,20 +761,21 @@ __global__ void __launch_bounds__(256) k_prolong_jac8(int n, const int *__restri
   const bool valid = i < n;
   RowPF<T> f;
   row_prefetch<8>(f, i, valid, lane, rowptr, col, val);
-  int fa[kPF];
+  constexpr int PF = pf<T>();
+  int fa[PF];
 #pragma unroll
-  for (int u = 0; u < kPF; ++u) fa[u] = f.k + 8 * u < f.ke ? agg[f.c[u]] : -1;
+  for (int u = 0; u < PF; ++u) fa[u] = f.k + 8 * u < f.ke ? agg[f.c[u]] : -1;
   pdl_wait();
   pdl_trigger();
   T s = 0;
 #pragma unroll
-  for (int u = 0; u < kPF; ++u)
+  for (int u = 0; u < PF; ++u)
     if (f.k + 8 * u < f.ke) {
       const int j = f.c[u], J = fa[u];
       const T xj = J >= 0 ? x[j] + xc[J] : x[j];
       s = fma(f.v[u], xj, s);
     }
-  for (int k = f.k + 8 * kPF; k < f.ke; k += 8) {
+  for (int k = f.k + 8 * PF; k < f.ke; k += 8) {
     const int j = col[k];
     const int J = agg[j];
     const T xj = J >= 0 ? x[j] + xc[J] : x[j];

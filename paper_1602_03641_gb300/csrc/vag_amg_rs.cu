@@ -27,10 +27,10 @@
 //             strong connections interpolate from nothing (the smoother
 //             handles them);
 //  R = P^T    transposed with its rows sorted by fine index;
-//  Galerkin   A_c = R (A P): two row-by-row sparse products, each row summed
-//             in a fixed sequence order (deterministic: a system's hierarchy
-//             depends on that system alone, so it is bitwise the same in a
-//             batch), columns sorted.
+//  Galerkin   A_c = R A P, one coarse row per warp, every entry summed in a
+//             fixed sequence order and the row's columns in the order they
+//             first appear (deterministic: a system's hierarchy depends on
+//             that system alone, so it is bitwise the same in a batch).
 #include <climits>
 #include <functional>
 #include <vector>
@@ -80,21 +80,29 @@ __device__ __forceinline__ bool rs_strong(double a, double maxneg_row) {
 __global__ void k_rs_init(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
                           const double *__restrict__ val, const double *__restrict__ maxneg,
                           const uint8_t *__restrict__ skip, const int *__restrict__ sys_start, int n_sys,
-                          unsigned long long *__restrict__ key, int8_t *__restrict__ state) {
+                          unsigned long long *__restrict__ key, int8_t *__restrict__ state,
+                          uint8_t *__restrict__ sflag) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (skip[i]) {
     key[i] = 0;
     state[i] = -3;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) sflag[k] = 0;
     return;
   }
   bool depends = false;
   unsigned infl = 0;
   for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
     const int j = col[k];
-    if (j == i) continue;
-    depends |= rs_strong(val[k], maxneg[i]);
-    infl += rs_strong(val[k], maxneg[j]);   // j depends on i
+    uint8_t f = 0;
+    if (j != i) {
+      const bool dij = rs_strong(val[k], maxneg[i]);   // i depends on j
+      const bool dji = rs_strong(val[k], maxneg[j]);   // j depends on i
+      depends |= dij;
+      infl += dji;
+      f = (uint8_t)(dij | (dji << 1));
+    }
+    sflag[k] = f;   // the strength of the entry, both ways, for the PMIS rounds
   }
   const int loc = i - sys_start[rs_sys_of_row(i, sys_start, n_sys)];
   key[i] = ((unsigned long long)(infl < 65535u ? infl : 65535u) << 48) |
@@ -105,9 +113,8 @@ __global__ void k_rs_init(int n, const int *__restrict__ rowptr, const int *__re
 // PMIS round, first half: undecided rows that are the largest among their
 // undecided strong neighbours become coarse
 __global__ void k_rs_pmis_c(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                            const double *__restrict__ val, const double *__restrict__ maxneg,
-                            const unsigned long long *__restrict__ key, const int8_t *__restrict__ st_in,
-                            int8_t *__restrict__ st_out) {
+                            const uint8_t *__restrict__ sflag, const unsigned long long *__restrict__ key,
+                            const int8_t *__restrict__ st_in, int8_t *__restrict__ st_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int8_t s = st_in[i];
@@ -118,9 +125,9 @@ __global__ void k_rs_pmis_c(int n, const int *__restrict__ rowptr, const int *__
   const unsigned long long ki = key[i];
   bool top = true;
   for (int k = rowptr[i]; k < rowptr[i + 1] && top; ++k) {
+    if (!sflag[k]) continue;   // not strong either way (or the diagonal)
     const int j = col[k];
-    if (j == i || st_in[j] != 0) continue;
-    if ((rs_strong(val[k], maxneg[i]) || rs_strong(val[k], maxneg[j])) && key[j] > ki) top = false;
+    if (st_in[j] == 0 && key[j] > ki) top = false;
   }
   st_out[i] = top ? 1 : 0;
 }
@@ -128,23 +135,26 @@ __global__ void k_rs_pmis_c(int n, const int *__restrict__ rowptr, const int *__
 // second half: undecided rows that depend on a coarse row become fine; the
 // rest are counted
 __global__ void k_rs_pmis_f(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                            const double *__restrict__ val, const double *__restrict__ maxneg,
-                            const int8_t *__restrict__ st_in, int8_t *__restrict__ st_out, int *undecided) {
+                            const uint8_t *__restrict__ sflag, const int8_t *__restrict__ st_in,
+                            int8_t *__restrict__ st_out, int *undecided) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int8_t s = st_in[i];
-  int8_t o = s;
-  if (s == 0) {
-    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-      const int j = col[k];
-      if (j != i && st_in[j] == 1 && rs_strong(val[k], maxneg[i])) {
-        o = -1;
-        break;
+  int8_t o = 1;
+  if (i < n) {
+    const int8_t s = st_in[i];
+    o = s;
+    if (s == 0) {
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        if ((sflag[k] & 1) && st_in[col[k]] == 1) {   // i depends on a coarse row
+          o = -1;
+          break;
+        }
       }
     }
-    if (o == 0) atomicAdd(undecided, 1);
+    st_out[i] = o;
   }
-  st_out[i] = o;
+  // one atomic per warp for the rows still undecided
+  const unsigned m = __ballot_sync(0xffffffffu, o == 0);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(undecided, __popc(m));
 }
 
 // second pass: a fine row that depends on rows but on no coarse one becomes
@@ -307,11 +317,13 @@ __global__ void k_rs_r_sort(int nc, const int *__restrict__ rrow, int *rcol, dou
 // shared-memory hash keyed by J, lanes that hit the same slot are grouped
 // and the lowest adds their values in lane order, so every entry is summed in
 // the order (entry of R, chunk of A's row, entry of P, lane), fixed by the
-// data.  A row may use at most HASH/2 slots (ST_ROW_OVERFLOW otherwise).  The
-// slots a row claims are listed; afterwards its (column, sum) pairs are moved
-// out through that list (clearing the table for the next row), sorted by
-// column (bitonic) and written to the row's padded slot zcol/zval[I*HASH/2 ..]
-// with its count in zcnt[I] and 1/z_II in zdinv; k_rs_compact packs them.
+// data.  A column enters the row's list when it first appears, the columns
+// new in one round in the order of their lowest lane (a ballot prefix), so
+// the list order is fixed by the data too.  A row may use at most HASH/2
+// slots (ST_ROW_OVERFLOW otherwise).  Its (column, sum) pairs are written in
+// list order to the row's padded slot zcol/zval[I*HASH/2 ..], the table is
+// cleared through the list, the count goes to zcnt[I] and 1/z_II to zdinv;
+// k_rs_compact packs the rows.
 template <int HASH, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS) k_rs_rap(int nrows, const int *__restrict__ rrow,
                                                        const int *__restrict__ rcol, const double *__restrict__ rval,
@@ -324,12 +336,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_rs_rap(int nrows, const int *__r
   constexpr int CAP = HASH / 2;
   __shared__ int keys[WARPS][HASH];
   __shared__ double sums[WARPS][HASH];
-  __shared__ int used[WARPS][CAP + 32];
-  __shared__ int pk[WARPS][CAP];
-  __shared__ double ps[WARPS][CAP];
+  __shared__ int used[WARPS][CAP];
   __shared__ double vals[WARPS][32];
-  __shared__ int nuniq[WARPS];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
   int *K = keys[w];
   double *S = sums[w];
   int *U = used[w];
@@ -340,12 +350,12 @@ __global__ void __launch_bounds__(32 * WARPS) k_rs_rap(int nrows, const int *__r
   __syncwarp();
   const int stride = gridDim.x * WARPS;
   for (int I = blockIdx.x * WARPS + w; I < nrows; I += stride) {   // a whole warp takes each row
-    if (lane == 0) nuniq[w] = 0;
-    __syncwarp();
+    int nu = 0;                 // columns listed so far (the same in every lane)
     bool overflow = false;
     // one round: each lane offers (J, v) (J < 0: nothing)
     auto add = [&](int J, double v) {
       int slot = -1;
+      bool claimed = false;
       if (J >= 0) {
         unsigned h = ((unsigned)J * 2654435761u) & (HASH - 1);
         for (int probe = 0; probe < HASH; ++probe, h = (h + 1) & (HASH - 1)) {
@@ -353,12 +363,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_rs_rap(int nrows, const int *__r
           if (cur == J) { slot = (int)h; break; }
           if (cur == -1) {
             const int old = atomicCAS(&K[h], -1, J);
-            if (old == -1) {
-              const int q = atomicAdd(&nuniq[w], 1);
-              if (q < CAP + 32) U[q] = (int)h;
-              slot = (int)h;
-              break;
-            }
+            if (old == -1) { slot = (int)h; claimed = true; break; }
             if (old == J) { slot = (int)h; break; }
           }
         }
@@ -367,7 +372,15 @@ __global__ void __launch_bounds__(32 * WARPS) k_rs_rap(int nrows, const int *__r
       vals[w][lane] = v;
       __syncwarp();
       const unsigned grp = __match_any_sync(0xffffffffu, slot >= 0 ? slot : -1 - lane);
-      if (slot >= 0 && lane == __ffs(grp) - 1) {
+      const bool is_new = (grp & __ballot_sync(0xffffffffu, claimed)) != 0;
+      const bool leader = slot >= 0 && lane == __ffs(grp) - 1;
+      const unsigned lead_new = __ballot_sync(0xffffffffu, leader && is_new);
+      if (leader && is_new) {
+        const int q = nu + __popc(lead_new & below);
+        if (q < CAP) U[q] = slot;
+      }
+      nu += __popc(lead_new);
+      if (leader) {
         double acc = S[slot];
         for (unsigned m = grp; m; m &= m - 1) acc += vals[w][__ffs(m) - 1];
         S[slot] = acc;
@@ -393,26 +406,13 @@ __global__ void __launch_bounds__(32 * WARPS) k_rs_rap(int nrows, const int *__r
       }
     }
     __syncwarp();
-    const int nu = nuniq[w];
     const bool bad = __any_sync(0xffffffffu, overflow) || nu > CAP;
-    const int nl = nu < CAP + 32 ? nu : CAP + 32;   // listed slots
-    // move the pairs out through the list and clear the table
-    for (int q = lane; q < nl; q += 32) {
-      const int h = U[q];
-      if (q < CAP) {
-        pk[w][q] = K[h];
-        ps[w][q] = S[h];
-      }
-      K[h] = -1;
-      S[h] = 0.0;
-    }
-    __syncwarp();
     if (bad) {
       if (lane == 0) {
         atomicOr(status, ST_ROW_OVERFLOW);
         zcnt[I] = 0;
       }
-      // a table that overflowed may hold slots missing from the list
+      // the list is incomplete: clear the whole table
       for (int h = lane; h < HASH; h += 32) {
         K[h] = -1;
         S[h] = 0.0;
@@ -421,40 +421,20 @@ __global__ void __launch_bounds__(32 * WARPS) k_rs_rap(int nrows, const int *__r
       continue;
     }
     if (lane == 0) zcnt[I] = nu;
-    int n2 = 32;
-    while (n2 < nu) n2 <<= 1;   // <= CAP
-    int *PK = pk[w];
-    double *PS = ps[w];
-    for (int q = nu + lane; q < n2; q += 32) PK[q] = INT_MAX;
-    __syncwarp();
-    for (int size = 2; size <= n2; size <<= 1) {
-      for (int sd = size >> 1; sd > 0; sd >>= 1) {
-        for (int q = lane; q < n2; q += 32) {
-          const int o = q ^ sd;
-          if (o > q) {
-            const bool up = (q & size) == 0;
-            const int a = PK[q], b = PK[o];
-            if ((a > b) == up) {
-              PK[q] = b;
-              PK[o] = a;
-              const double t = PS[q];
-              PS[q] = PS[o];
-              PS[o] = t;
-            }
-          }
-        }
-        __syncwarp();
-      }
-    }
     const size_t base = (size_t)I * CAP;   // the row's padded slot; compacted afterwards
     bool diag = false;
     for (int q = lane; q < nu; q += 32) {
-      zcol[base + q] = PK[q];
-      zval[base + q] = PS[q];
-      if (zdinv && PK[q] == I) {
+      const int h = U[q];
+      const int J = K[h];
+      const double z = S[h];
+      zcol[base + q] = J;
+      zval[base + q] = z;
+      K[h] = -1;
+      S[h] = 0.0;
+      if (zdinv && J == I) {
         diag = true;
-        if (!(PS[q] > 0.0)) atomicOr(status, ST_NONPOSITIVE);
-        zdinv[I] = 1.0 / PS[q];
+        if (!(z > 0.0)) atomicOr(status, ST_NONPOSITIVE);
+        zdinv[I] = 1.0 / z;
       }
     }
     if (zdinv && !__any_sync(0xffffffffu, diag) && lane == 0) {
@@ -519,7 +499,8 @@ void rs_coarsen(System *s, AmgLevel &L, AmgLevel &C, const std::function<void *(
   int *undecided = static_cast<int *>(tmp(sizeof(int)));
   const int g = grid_for(n, TB);
   k_rs_maxneg<<<g, TB, 0, st>>>(n, L.rowptr, L.col, L.val, maxneg);
-  k_rs_init<<<g, TB, 0, st>>>(n, L.rowptr, L.col, L.val, maxneg, L.skip, L.d_sys_start, ns, key, sa);
+  uint8_t *sflag = static_cast<uint8_t *>(tmp((size_t)std::max<int64_t>(L.nnz, 1)));
+  k_rs_init<<<g, TB, 0, st>>>(n, L.rowptr, L.col, L.val, maxneg, L.skip, L.d_sys_start, ns, key, sa, sflag);
   note_launches(2);
   VAG_CHECK_LAUNCH();
   trace_mark(st, "  classical: strength + measure");
@@ -528,8 +509,8 @@ void rs_coarsen(System *s, AmgLevel &L, AmgLevel &C, const std::function<void *(
   bool finished = false;
   for (int r = 0; r < kMaxRounds; ++r) {
     VAG_CUDA(cudaMemsetAsync(undecided, 0, sizeof(int), st));
-    k_rs_pmis_c<<<g, TB, 0, st>>>(n, L.rowptr, L.col, L.val, maxneg, key, sa, sb);
-    k_rs_pmis_f<<<g, TB, 0, st>>>(n, L.rowptr, L.col, L.val, maxneg, sb, sa, undecided);
+    k_rs_pmis_c<<<g, TB, 0, st>>>(n, L.rowptr, L.col, sflag, key, sa, sb);
+    k_rs_pmis_f<<<g, TB, 0, st>>>(n, L.rowptr, L.col, sflag, sb, sa, undecided);
     note_launches(2);
     if ((r & 3) != 3) continue;
     VAG_CUDA(cudaMemcpyAsync(und_host, undecided, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -41,41 +41,25 @@ __device__ __forceinline__ V3 ldv(const double *__restrict__ xyz, int n) {
 __host__ __device__ constexpr int p6(int i, int j) {
   return i <= j ? i * 6 - (i * (i - 1)) / 2 + (j - i) : j * 6 - (j * (j - 1)) / 2 + (i - j);
 }
-// packed index in a 4x4 symmetric matrix
-__host__ __device__ constexpr int p4(int i, int j) {
-  return i <= j ? i * 4 - (i * (i - 1)) / 2 + (j - i) : j * 4 - (j * (j - 1)) / 2 + (i - j);
+// L v for the symmetric tensor L = (xx, yy, zz, xy, xz, yz)
+__device__ __forceinline__ V3 lmul(const double (&L)[6], V3 v) {
+  return {L[0] * v.x + L[3] * v.y + L[4] * v.z, L[3] * v.x + L[1] * v.y + L[5] * v.z,
+          L[4] * v.x + L[5] * v.y + L[2] * v.z};
 }
-
-// P1 stiffness S_ij = |T| grad l_i . L grad l_j on the tetrahedron (p0..p3).
-// With e_k = p_k - p0, the area vectors n1 = e2 x e3, n2 = e3 x e1,
-// n3 = e1 x e2 satisfy grad l_k = n_k / det (det = e1 . n1) and
-// n0 = -(n1 + n2 + n3); hence S_ij = n_i . L n_j / (6 |det|).
-__device__ __forceinline__ void tet_stiffness(V3 p0, V3 p1, V3 p2, V3 p3, const double (&L)[6],
-                                              double (&S)[10], double &vol) {
-  const V3 e1 = p1 - p0, e2 = p2 - p0, e3 = p3 - p0;
-  V3 n[4];
-  n[1] = cross(e2, e3);
-  n[2] = cross(e3, e1);
-  n[3] = cross(e1, e2);
-  n[0] = {-(n[1].x + n[2].x + n[3].x), -(n[1].y + n[2].y + n[3].y), -(n[1].z + n[2].z + n[3].z)};
-  const double ad = fabs(dot(e1, n[1]));
-  vol = ad * (1.0 / 6.0);
-  const double inv = 1.0 / (6.0 * ad);
-  V3 Ln[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    Ln[j].x = L[0] * n[j].x + L[3] * n[j].y + L[4] * n[j].z;
-    Ln[j].y = L[3] * n[j].x + L[1] * n[j].y + L[5] * n[j].z;
-    Ln[j].z = L[4] * n[j].x + L[5] * n[j].y + L[2] * n[j].z;
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = i; j < 4; ++j) S[p4(i, j)] = dot(n[i], Ln[j]) * inv;
-}
+__device__ __forceinline__ V3 neg(V3 a) { return {-a.x, -a.y, -a.z}; }
 
 // The local matrix of one cell of shape SH: M over (K, node slots 0..7)
 // packed, Mfc over (sigma sigma, sigma K, sigma n_t) for each fracture face.
+//
+// Each face's tetrahedra T_{K,sigma,e} = (x_K, x_sigma, q_e, q_e+1) add their
+// P1 stiffness to F (packed 6x6 over (K, sigma, q0..q3)).  For a tetrahedron
+// (p0..p3) with e_k = p_k - p0, the area vectors n1 = e2 x e3, n2 = e3 x e1,
+// n3 = e1 x e2 and n0 = -(n1 + n2 + n3) give grad l_k = n_k / det
+// (det = e1 . n1) and S_ij = |T| grad l_i . L grad l_j = n_i . L n_j / (6 |det|).
+// Here e1 = x_sigma - x_K for the whole face and, with d_t = q_t - x_K,
+// n1 = d_e x d_e+1, n2 = -(e1 x d_e+1), n3 = e1 x d_e: the corner vectors
+// c_t = e1 x d_t and L c_t are formed once and shared by the two tetrahedra
+// at corner t.
 template <int SH>
 __device__ __forceinline__ void cell_local(int K, int nc, const int *__restrict__ cn, const double *__restrict__ xyz,
                                            const double (&L)[6], const int *__restrict__ cell_ff, int fi, int n_fc,
@@ -110,19 +94,38 @@ __device__ __forceinline__ void cell_local(int K, int nc, const int *__restrict_
     double F[21];
 #pragma unroll
     for (int k = 0; k < 21; ++k) F[k] = 0.0;
+    const V3 ev = xs - xK;
+    V3 d[Q4], c[Q4], Lc[Q4];
+#pragma unroll
+    for (int t = 0; t < Q4; ++t) {
+      if (t >= Q) break;
+      d[t] = q[t] - xK;
+      c[t] = cross(ev, d[t]);
+      Lc[t] = lmul(L, c[t]);
+    }
 #pragma unroll
     for (int e = 0; e < Q4; ++e) {
       if (e >= Q) break;
       const int e1 = e + 1 == Q ? 0 : e + 1;
-      double S[10], tv;
-      tet_stiffness(xK, xs, q[e], q[e1], L, S, tv);
+      V3 n[4], Ln[4];
+      n[1] = cross(d[e], d[e1]);
+      Ln[1] = lmul(L, n[1]);
+      n[2] = neg(c[e1]);
+      Ln[2] = neg(Lc[e1]);
+      n[3] = c[e];
+      Ln[3] = Lc[e];
+      n[0] = neg(n[1] + n[2] + n[3]);
+      Ln[0] = neg(Ln[1] + Ln[2] + Ln[3]);
+      const double ad = fabs(dot(ev, n[1]));
+      const double tv = ad * (1.0 / 6.0);
       vol += tv;
       minvol = fmin(minvol, tv);
+      const double inv = 1.0 / (6.0 * ad);
       const int map[4] = {0, 1, 2 + e, 2 + e1};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = i; j < 4; ++j) F[p6(map[i], map[j])] += S[p4(i, j)];
+        for (int j = i; j < 4; ++j) F[p6(map[i], map[j])] = fma(dot(n[i], Ln[j]), inv, F[p6(map[i], map[j])]);
     }
     const bool isff = cell_ff[6 * (size_t)K + lf] >= 0;
     M[topo::pidx(0, 0)] += F[p6(0, 0)];
