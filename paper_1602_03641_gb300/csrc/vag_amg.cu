@@ -583,16 +583,17 @@ __global__ void k_resid_sell(int n, const int *__restrict__ rowptr, const int *_
   r[i] = b[i] - sell_row<T, U>(i, rowptr, slice_ptr, scol, sval, x);
 }
 
-// The last finest-level sweep of the V-cycle inside CG (FP64): z = the sweep,
-// and r.z per system formed on the way (r is the level's right-hand side),
-// exactly as the separate r.z kernel would: one row per thread of a 256-row
-// tile, the tile's block sum, the last tile of a system adding the tile
-// partials in order and setting beta = (r.z)' / (r.z) and rho = (r.z)'.
-template <int U>
+// The last finest-level sweep of the V-cycle inside CG (FP64 CG, or the FP32
+// CG inside refinement): z = the sweep, and r.z per system formed on the way
+// (r is the level's right-hand side), exactly as the separate r.z kernel
+// would: one row per thread of a 256-row tile, the tile's block sum, the last
+// tile of a system adding the tile partials in order and setting
+// beta = (r.z)' / (r.z) and rho = (r.z)'.
+template <class T, int U>
 __global__ void __launch_bounds__(256) k_jac_sell_rz(const int *__restrict__ rowptr, const int *__restrict__ slice_ptr,
-                                                     const int *__restrict__ scol, const double *__restrict__ sval,
-                                                     const double *__restrict__ sinv, const double *__restrict__ r,
-                                                     const double *__restrict__ xin, double *__restrict__ z,
+                                                     const int *__restrict__ scol, const T *__restrict__ sval,
+                                                     const T *__restrict__ sinv, const T *__restrict__ r,
+                                                     const T *__restrict__ xin, T *__restrict__ z,
                                                      const uint8_t *__restrict__ skip, Tiles tl, double *partials,
                                                      unsigned *counter, KrylovScalars *ks, int *n_done) {
   const int t = blockIdx.x;
@@ -603,14 +604,14 @@ __global__ void __launch_bounds__(256) k_jac_sell_rz(const int *__restrict__ row
   pdl_trigger();
   double rz = 0.0;
   if (valid) {
-    double zi;
+    T zi;
     if (skip[i]) {
       zi = z[i];   // solved densely on this level
     } else {
-      zi = jac_row(xin[i], sinv[i], r[i], sell_row<double, U>(i, rowptr, slice_ptr, scol, sval, xin));
+      zi = jac_row(xin[i], sinv[i], r[i], sell_row<T, U>(i, rowptr, slice_ptr, scol, sval, xin));
       z[i] = zi;
     }
-    rz = fma(r[i], zi, 0.0);
+    rz = (double)fma(r[i], zi, (T)0);
   }
   if (ks[sys].done) return;   // uniform in the block: one system per tile
   double v[1] = {rz}, out[1];
@@ -1523,7 +1524,8 @@ static void tail(System *s, int lvl, cudaStream_t st) {
 // D_l1^-1 r was made by the CG update, and its last sweep also forms r.z
 // (returns true when it did)
 template <class T>
-static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool cg = false) {
+static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool cg = false,
+                   KrylovScalars *cg_ks = nullptr, int *cg_done = nullptr) {
   Amg &A = s->amg;
   AmgLevel &L = A.levels[lvl];
   if (lvl > 0 && lvl == A.tail_start) {   // b, x are this level's own b, x
@@ -1620,18 +1622,15 @@ static bool vcycle(System *s, int lvl, const T *b, T *x, cudaStream_t st, bool c
                  v.t);
     else
       launch_pdl(k_prolong<T>, g, TB, 0, st, n, (const int *)L.agg, (const T *)c.x, v.t);
-    if constexpr (sizeof(T) == 8) {
-      if (cg) {
-      auto jr = s->sell_u == 2 ? k_jac_sell_rz<2> : s->sell_u == 8 ? k_jac_sell_rz<8> : k_jac_sell_rz<4>;
+    if (cg) {   // the last sweep forms r.z for the Krylov loop (cg_ks, cg_done)
+      auto jr = s->sell_u == 2 ? k_jac_sell_rz<T, 2> : s->sell_u == 8 ? k_jac_sell_rz<T, 8> : k_jac_sell_rz<T, 4>;
       const Tiles tl{s->seg.tile_sys, s->seg.tile_row0, s->seg.tile_row1, s->seg.sys_tile0, s->seg.sys_grp0,
                      s->seg.n_tiles, s->seg.n_sys};
       launch_pdl(jr, s->seg.n_tiles, 256, 0, st, (const int *)L.rowptr, (const int *)L.slice_ptr,
-                 (const int *)L.scol, (const double *)v.sval, (const double *)v.sinv, (const double *)b,
-                 (const double *)v.t, (double *)x, (const uint8_t *)L.skip, tl, s->partials, s->counter, s->ks,
-                 s->n_done);
+                 (const int *)L.scol, (const T *)v.sval, (const T *)v.sinv, (const T *)b, (const T *)v.t, (T *)x,
+                 (const uint8_t *)L.skip, tl, s->partials, s->counter, cg_ks, cg_done);
       note_launches(2);
       return true;
-      }
     }
     launch_pdl(jac_sell, g, TB, 0, st, n, (const int *)L.rowptr, (const int *)L.slice_ptr, (const int *)L.scol,
                v.sval, v.sinv, b, (const T *)v.t, x, (const uint8_t *)L.skip);
@@ -1692,7 +1691,21 @@ void amg_apply_f32(System *s, const float *r, float *z, cudaStream_t st) {
 
 bool amg_apply_cg(System *s, const double *r, double *z, cudaStream_t st) {
   if (s->amg.f32 || s->amg.levels.empty() || s->amg.levels[0].all_term) return false;
-  return vcycle<double>(s, 0, r, z, st, true);
+  return vcycle<double>(s, 0, r, z, st, true, s->ks, s->n_done);
+}
+
+bool amg_apply_f32_cg(System *s, const float *r, float *z, cudaStream_t st, KrylovScalars *ks, int *n_done) {
+  const Amg &A = s->amg;
+  if (!A.f32 || A.f16 || A.levels.empty() || A.levels[0].all_term) return false;
+  return vcycle<float>(s, 0, r, z, st, true, ks, n_done);
+}
+
+const float *amg_first_sweep_scale_f32(System *s, float *&t0, float &omega) {
+  const Amg &A = s->amg;
+  if (!A.f32 || A.f16 || A.levels.empty() || A.levels[0].all_term) return nullptr;
+  t0 = A.levels[0].t32;
+  omega = (float)kOmega;
+  return A.levels[0].sinv32;
 }
 
 const double *amg_first_sweep_scale(System *s, double *&t0, double &omega) {

@@ -428,6 +428,10 @@ void amg_apply_f32(System *s, const float *r, float *z, cudaStream_t st);
 // the cycle and forms r.z (beta, rho) in its last sweep.
 const double *amg_first_sweep_scale(System *s, double *&t0, double &omega);
 bool amg_apply_cg(System *s, const double *r, double *z, cudaStream_t st);
+// The same for the FP32 V-cycle of the CG inside refinement (inner scalars
+// ks, n_done); unavailable (nullptr / false) with the FP16 finest level.
+const float *amg_first_sweep_scale_f32(System *s, float *&t0, float &omega);
+bool amg_apply_f32_cg(System *s, const float *r, float *z, cudaStream_t st, KrylovScalars *ks, int *n_done);
 void amg_free(System *s);
 // Chebyshev preconditioner (FP64): cheb_setup estimates each system's interval
 // from Jacobi-CG Lanczos coefficients and fills the coefficient table;

@@ -360,7 +360,8 @@ __global__ void __launch_bounds__(NT) k_irm_rz_start(const float *__restrict__ r
 __global__ void __launch_bounds__(NT) k_irm_update(float *__restrict__ x, float *__restrict__ r,
                                                    const float *__restrict__ p, const float *__restrict__ q, Tiles tl,
                                                    double *partials, unsigned *counter, KrylovScalars *ki,
-                                                   int *n_done_in) {
+                                                   int *n_done_in, const float *__restrict__ sinv0,
+                                                   float *__restrict__ t0, float omega) {
   const int t = blockIdx.x;
   const int sys = tl.sys[t];
   pdl_wait();
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(NT) k_irm_update(float *__restrict__ x, float 
     x[i] = fmaf(a, p[i], x[i]);
     const float ri = fmaf(-a, q[i], r[i]);
     r[i] = ri;
+    if (sinv0) t0[i] = omega * sinv0[i] * ri;   // the V-cycle's first sweep from zero
     rr = fmaf(ri, ri, rr);
   }
   double v[1] = {(double)rr}, out[1];
@@ -560,17 +562,26 @@ void mixed_amg_solve(System *s, const vag_solve_opts *o, vag_solve_info *info) {
   const float *a32 = m.dval32;   // FP32 difference-form values of A, sliced ELL
   auto spmv32 = s->sell_u == 2 ? k_spmv32d<2> : s->sell_u == 8 ? k_spmv32d<8> : k_spmv32d<4>;
   // one inner iteration: q = A p (p.q, alpha), x/r update, z = V(r), r.z, p
+  // the V-cycle's first sweep is formed by the update and its last sweep
+  // forms r.z (the same arithmetic as the separate kernels)
+  float *t0 = nullptr;
+  float omega = 0.f;
+  const float *sinv0 = amg_first_sweep_scale_f32(s, t0, omega);
   auto iteration = [&]() {
     launch_pdl(spmv32, nt, NT, 0, st, (const int *)s->rowptr, (const int *)s->slice_ptr, (const int *)s->scol, a32,
                (const float *)m.rowsum32, (const float *)m.p32, m.q32, tl, s->partials, s->counter, m.ks_in,
                m.n_done_in);
     launch_pdl(k_irm_update, nt, NT, 0, st, m.x32, m.r32, (const float *)m.p32, (const float *)m.q32, tl, s->partials,
-               s->counter, m.ks_in, m.n_done_in);
-    amg_apply_f32(s, m.r32, m.z32, st);
-    launch_pdl(k_irm_rz, nt, NT, 0, st, (const float *)m.r32, (const float *)m.z32, tl, s->partials, s->counter,
-               m.ks_in, m.n_done_in);
+               s->counter, m.ks_in, m.n_done_in, sinv0, t0, omega);
+    const bool rz_done = sinv0 ? amg_apply_f32_cg(s, m.r32, m.z32, st, m.ks_in, m.n_done_in)
+                               : (amg_apply_f32(s, m.r32, m.z32, st), false);
+    if (!rz_done) {
+      launch_pdl(k_irm_rz, nt, NT, 0, st, (const float *)m.r32, (const float *)m.z32, tl, s->partials, s->counter,
+                 m.ks_in, m.n_done_in);
+      note_launches(1);
+    }
     launch_pdl(k_irm_pdir, nt, NT, 0, st, m.p32, (const float *)m.z32, tl, (const KrylovScalars *)m.ks_in);
-    note_launches(4);
+    note_launches(3);
   };
   VAG_CUDA(cudaMemsetAsync(s->n_done, 0, sizeof(int), st));
   k_ir_init<<<nt, NT, 0, st>>>(s->rhs, s->kx, s->kr, tl, s->partials, s->counter, s->ks, s->n_done, o->rtol,
