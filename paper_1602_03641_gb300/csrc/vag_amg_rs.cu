@@ -526,17 +526,24 @@ void rs_coarsen(System *s, AmgLevel &L, AmgLevel &C, const std::function<void *(
   int *cidx = static_cast<int *>(tmp(4 * ((size_t)n + 1)));
   k_rs_second_pass<<<g, TB, 0, st>>>(n, L.rowptr, L.col, L.val, maxneg, sa, sb, cflag);
   note_launches(1);
-  const int nc = scan_exclusive(cflag, cidx, n, st);
+  scan_exclusive(cflag, cidx, n, st, false);
   const int8_t *state = sb;
-  // P
+  // P: row counts, then one read-back of the coarse count and of P's
+  // nonzeros (R = P^T has as many)
   int *pcnt = static_cast<int *>(tmp(4 * ((size_t)n + 1)));
   L.prow = static_cast<int *>(alloc(4 * ((size_t)n + 1)));
   k_rs_p_count<<<g, TB, 0, st>>>(n, L.rowptr, L.col, L.val, maxneg, state, pcnt);
   note_launches(1);
-  L.p_nnz = scan_exclusive(pcnt, L.prow, n, st);
+  scan_exclusive(pcnt, L.prow, n, st, false);
+  int *pin = s->amg_pin;   // pinned
+  VAG_CUDA(cudaMemcpyAsync(&pin[0], cidx + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VAG_CUDA(cudaMemcpyAsync(&pin[1], L.prow + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VAG_CUDA(cudaStreamSynchronize(st));
+  const int nc = pin[0];
+  L.p_nnz = pin[1];
   L.pcol = static_cast<int *>(alloc(4 * (size_t)std::max<int64_t>(L.p_nnz, 1)));
   L.pval = static_cast<double *>(alloc(8 * (size_t)std::max<int64_t>(L.p_nnz, 1)));
-  VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
+  VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));   // checked after the Galerkin product
   k_rs_p_fill<<<g, TB, 0, st>>>(n, L.rowptr, L.col, L.val, maxneg, state, cidx, L.prow, L.pcol, L.pval, s->status);
   note_launches(1);
   // R = P^T
@@ -547,18 +554,14 @@ void rs_coarsen(System *s, AmgLevel &L, AmgLevel &C, const std::function<void *(
   VAG_CUDA(cudaMemsetAsync(cursor, 0, 4 * ((size_t)nc + 1), st));
   k_rs_r_count<<<g, TB, 0, st>>>(n, L.prow, L.pcol, rcnt);
   note_launches(1);
-  L.r_nnz = scan_exclusive(rcnt, L.rrow, nc, st);
+  scan_exclusive(rcnt, L.rrow, nc, st, false);
+  L.r_nnz = L.p_nnz;
   L.rcol = static_cast<int *>(alloc(4 * (size_t)std::max<int64_t>(L.r_nnz, 1)));
   L.rval = static_cast<double *>(alloc(8 * (size_t)std::max<int64_t>(L.r_nnz, 1)));
   k_rs_r_fill<<<g, TB, 0, st>>>(n, L.prow, L.pcol, L.pval, L.rrow, cursor, L.rcol, L.rval);
   k_rs_r_sort<<<grid_for(nc, TB), TB, 0, st>>>(nc, L.rrow, L.rcol, L.rval);
   note_launches(2);
   VAG_CHECK_LAUNCH();
-  {
-    const int stv = read_status(s);
-    if (stv & ST_BAD_INDEX) fail(VAG_ECUDA, "AMG: internal interpolation count mismatch");
-    if (stv & ST_NONPOSITIVE) fail(VAG_EINVAL, "AMG: a fine row has no usable coarse couplings");
-  }
   L.nc = nc;
   trace_mark(st, "  classical: second pass, P, R");
   // Galerkin A_c = R A P in one pass into rows padded to kRapHash/2 columns,
@@ -571,15 +574,21 @@ void rs_coarsen(System *s, AmgLevel &L, AmgLevel &C, const std::function<void *(
   int *tcol = static_cast<int *>(tmp(4 * (size_t)std::max(nc, 1) * kRapCap));
   double *tval = static_cast<double *>(tmp(8 * (size_t)std::max(nc, 1) * kRapCap));
   const int gc = rap_blocks(nc, kRapWarps);
-  VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   k_rs_rap<kRapHash, kRapWarps><<<gc, 32 * kRapWarps, 0, st>>>(nc, L.rrow, L.rcol, L.rval, L.rowptr, L.col, L.val,
                                                                L.prow, L.pcol, L.pval, cc, tcol, tval, C.dinv,
                                                                s->status);
   note_launches(1);
-  C.nnz = scan_exclusive(cc, C.rowptr, nc, st);
+  scan_exclusive(cc, C.rowptr, nc, st, false);
+  VAG_CUDA(cudaMemcpyAsync(&pin[0], C.rowptr + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VAG_CUDA(cudaMemcpyAsync(&pin[1], s->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  VAG_CUDA(cudaStreamSynchronize(st));
+  C.nnz = pin[0];
   {
-    const int stv = read_status(s);
+    const int stv = pin[1];
+    if (stv & ST_BAD_INDEX) fail(VAG_ECUDA, "AMG: internal interpolation count mismatch");
     if (stv & ST_ROW_OVERFLOW) fail(VAG_EMESH, "AMG: a coarse row couples too many coarse rows");
+    if (stv & ST_NONPOSITIVE)
+      fail(VAG_EINVAL, "AMG: a fine row has no usable coarse couplings or a coarse diagonal is not positive");
   }
   C.col = static_cast<int *>(alloc(4 * (size_t)std::max<int64_t>(C.nnz, 1)));
   C.val = static_cast<double *>(alloc(8 * (size_t)std::max<int64_t>(C.nnz, 1)));
