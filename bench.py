@@ -525,10 +525,11 @@ def serve_arm(args):
                        "failed": sum(1 for r in res if r.status != 0), "peak_reserved_gb": st.peak_bytes / 2**30}
         srv.close()
     print(json.dumps({"metric": "served Darcy+transport requests: solves/s, p50/p99 latency", "unit": UNIT,
-                      "value": lines["mixed_amg"]["solves_per_s"], "n_gpus": 1, "higher_is_better": True,
+                      "value": lines["mixed_classical_amg"]["solves_per_s"], "n_gpus": 1, "higher_is_better": True,
                       "data": "synthetic",
                       "config": {"workload": f"{len(pbs)} Poisson arrivals at 200/s, n lognormal in [16, 96], "
-                                             "1-50 fractures, 100 transport steps, rtol 1e-8, 60 GB budget, 3 slots"},
+                                             "1-50 fractures, 100 transport steps, rtol 1e-8, 60 GB budget, 3 slots; "
+                                             "value = mixed precision with the classical AMG"},
                       "results": lines}))
 
 
