@@ -49,6 +49,7 @@ enum : int {
   ST_ISOLATED = 512,       // an unknown coupled to nothing (no diagonal)
   ST_NO_SLOT = 1024,       // a contribution without a CSR slot
   ST_TAIL_SMEM = 2048,     // a system's tail levels exceed the shared-memory plan
+  ST_WAIT_TIMEOUT = 4096,  // a bounded barrier wait gave up
 };
 
 constexpr int kMaxRowWidth = 160;   // unique columns of one eliminated row
@@ -292,17 +293,21 @@ struct System {
   double *Fff = nullptr;       // [4 nf]
   bool have_flux = false;
   double *phi = nullptr;       // [n_cv]
-  double *tdiag = nullptr;     // [n_cv + n_perf]
-  int *trowptr = nullptr;      // [n_cv + n_perf + 1]
-  int *tcol = nullptr;         // [nnz_t]
-  double *tval = nullptr;      // [nnz_t]
+  // upwind map in sliced ELL: slot i (rows sorted by inflow count inside
+  // windows) holds control volume tperm[i]; slice s = 32 slots, entry u of
+  // its lane r at tsp[s] + 32 u + r
+  double *tdiag = nullptr;     // [n_cv + n_perf] by slot
+  int *tperm = nullptr;        // [n_cv + n_perf]
+  int *tsp = nullptr;          // [slices + 1]
+  int *tcol = nullptr;         // [t_cap] (padding entries: own row, weight 0)
+  double *tval = nullptr;      // [t_cap]
   int64_t t_cap = 0;
   double *cbuf = nullptr;      // [2 (n_cv + n_perf)]
   double *dts = nullptr;       // [2 n_sys]: per system dt_max, dt
   cudaGraphExec_t step_graph = nullptr;   // kStepChunk transport steps
   int64_t step_graph_cap = -1;
   int step_graph_rows = 0;
-  int t_rows = 0;              // rows allocated for tdiag, trowptr and each half of cbuf
+  int t_rows = 0;              // rows allocated for tdiag, tperm, tsp and each half of cbuf
   std::vector<double> dts_host;
 
   // timing events

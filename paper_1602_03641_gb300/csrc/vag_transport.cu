@@ -12,10 +12,14 @@
 //                because every edge with F != 0 has one upstream end: its
 //                flux enters the downstream control volume with the upstream
 //                concentration and leaves the upstream one with it.  The map
-//                is built once per (fluxes, dt) as a CSR of the inflow edges;
+//                is built once per (fluxes, dt) from the inflow edges;
 //                Dirichlet rows keep c = cbar (d = 1, no inflow).
+//  k_sigma_sort  the map's row order: inside each window of kSigma control
+//                volumes, rows by decreasing inflow count (stable), so that
+//                the 32 rows of a warp have nearly the same number of edges;
+//                the map is stored as sliced ELL over that order.
 //  k_cfl         Eq. (eq_CFL): min over non-Dirichlet CVs of phi / outflow.
-//  k_step        c' = d c + W c (one thread per control volume).
+//  k_step        c' = d c + W c (one thread per row slot, one warp per slice).
 //
 // Wells (Sec. 5.5): perforation p exchanges the rate Fw[p] =
 // WI (u_sigma - p_w) - q between its fracture face and the well.  The well
@@ -305,25 +309,91 @@ __global__ void k_pick_dt(int n_sys, const unsigned long long *__restrict__ dt_b
   dts[2 * g + 1] = h;
 }
 
+// Row mu in slot inv[mu]: inflow entry j at tsp[s] + 32 j + r (slice s, lane
+// r); the slice's remaining entries of the row are padding (column mu,
+// weight 0), which leaves every product chain unchanged.
 __global__ void k_map_fill(TView t, int n, const double *__restrict__ phi, const int *__restrict__ cv_sys,
-                           const int *__restrict__ rowptr, const double *__restrict__ dts, double *__restrict__ diag,
-                           int *__restrict__ col, double *__restrict__ w) {
+                           const int *__restrict__ inv, const int *__restrict__ sp, const double *__restrict__ dts,
+                           double *__restrict__ diag, int *__restrict__ col, double *__restrict__ w) {
   const int mu = blockIdx.x * blockDim.x + threadIdx.x;
   if (mu >= n) return;
-  if (is_dir(t, mu)) { diag[mu] = 1.0; return; }
-  const double h = dts[2 * cv_sys[mu] + 1] / phi[mu];
-  int k = rowptr[mu];
-  double out = 0.0;
-  for_edges(t, mu, [&](double Fin, int nb) {
-    if (Fin > 0.0) {
-      col[k] = nb;
-      w[k] = h * Fin;
-      ++k;
-    } else {
-      out -= Fin;
+  const int slot = inv[mu];
+  const int k0 = sp[slot >> 5] + (slot & 31), width = (sp[(slot >> 5) + 1] - sp[slot >> 5]) >> 5;
+  int j = 0;
+  if (is_dir(t, mu)) {
+    diag[slot] = 1.0;
+  } else {
+    const double h = dts[2 * cv_sys[mu] + 1] / phi[mu];
+    double out = 0.0;
+    for_edges(t, mu, [&](double Fin, int nb) {
+      if (Fin > 0.0) {
+        col[k0 + 32 * j] = nb;
+        w[k0 + 32 * j] = h * Fin;
+        ++j;
+      } else {
+        out -= Fin;
+      }
+    });
+    diag[slot] = 1.0 - h * out;
+  }
+  for (; j < width; ++j) {
+    col[k0 + 32 * j] = mu;
+    w[k0 + 32 * j] = 0.0;
+  }
+}
+
+// One block per window of kSigma rows: perm (slot -> row) and inv (row ->
+// slot) with the rows of the window ordered by decreasing inflow count
+// (counts of 31 and more share the first bucket), equal counts by row index;
+// slice_len[s] = 32 x the widest row of slice s.  Deterministic: ranks come
+// from warp matches and prefix sums, not from atomics.
+constexpr int kSigma = 256;
+__global__ void __launch_bounds__(kSigma) k_sigma_sort(int n, const int *__restrict__ cnt, int *__restrict__ perm,
+                                                       int *__restrict__ inv, int *__restrict__ slice_len) {
+  constexpr int NW = kSigma / 32;
+  __shared__ int wc[NW][32];   // rows per (warp, bucket), then the warp's offset in the bucket
+  __shared__ int start[32];    // first position of each bucket in the window
+  __shared__ int srow[kSigma];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w0 = blockIdx.x * kSigma, i = w0 + threadIdx.x;
+  const bool valid = i < n;
+  const int c = valid ? cnt[i] : 0;
+  const int b = valid ? 31 - min(c, 31) : 32;   // bucket 0 = the longest rows
+  wc[warp][lane] = 0;
+  __syncthreads();
+  const unsigned same = __match_any_sync(0xffffffffu, b);
+  const int rank = __popc(same & ((1u << lane) - 1u));
+  if (valid && rank == 0) wc[warp][b] = __popc(same);
+  __syncthreads();
+  if (warp == 0) {
+    int run = 0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      const int x = wc[q][lane];
+      wc[q][lane] = run;
+      run += x;
     }
-  });
-  diag[mu] = 1.0 - h * out;
+    int incl = run;   // bucket totals -> exclusive scan over buckets
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    start[lane] = incl - run;
+  }
+  __syncthreads();
+  if (valid) {
+    const int pos = start[b] + wc[warp][b] + rank;
+    perm[w0 + pos] = i;
+    inv[i] = w0 + pos;
+    srow[pos] = c;
+  }
+  __syncthreads();
+  const int slot = w0 + threadIdx.x;
+  int m = slot < n ? srow[threadIdx.x] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0 && slot < n) slice_len[slot >> 5] = 32 * m;
 }
 
 // system of every control volume of the union ([nodes | ffaces | cells])
@@ -344,25 +414,32 @@ __global__ void k_cv_sys(int nv, int nf, int nc, int n_sys, const int *__restric
   cv_sys[mu] = lo;
 }
 
-// Launched with programmatic dependent launch: the map (written once per
-// solve) is read before the dependency wait, the previous step's c after it.
-// The map streams through once a step (evict-first loads), so the cache keeps
-// the concentrations that the upwind gathers reuse.  (Two, six or eight
-// prefetched entries a row were measured slower than four.)
+// One thread per row slot, one warp per slice: the slice's entries are read
+// lane-contiguous (coalesced) and every lane walks the slice's width, so a
+// warp's fma instructions are as many as its widest row (rows of a slice
+// have nearly equal counts, see k_sigma_sort).  Launched with programmatic
+// dependent launch: the map (written once per solve) is read before the
+// dependency wait, the previous step's c after it.  The map streams through
+// once a step (evict-first loads), so the cache keeps the concentrations
+// that the gathers reuse.
 constexpr int kStepPF = 4;
-__global__ void __launch_bounds__(TB) k_step(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                                             const double *__restrict__ w, const double *__restrict__ diag,
-                                             const double *__restrict__ c, double *__restrict__ cn) {
-  const int mu = blockIdx.x * TB + threadIdx.x;
-  const bool valid = mu < n;
-  const int b = valid ? __ldcs(rowptr + mu) : 0, e = valid ? __ldcs(rowptr + mu + 1) : 0;
-  const double d = valid ? __ldcs(diag + mu) : 0.0;
+__global__ void __launch_bounds__(TB) k_step(int n, const int *__restrict__ perm, const int *__restrict__ sp,
+                                             const int *__restrict__ col, const double *__restrict__ w,
+                                             const double *__restrict__ diag, const double *__restrict__ c,
+                                             double *__restrict__ cn) {
+  const int i = blockIdx.x * TB + threadIdx.x;
+  if ((i >> 5) >= (n + 31) >> 5) return;   // whole warps
+  const int r = i & 31;
+  const int k0 = __ldcs(sp + (i >> 5)), width = (__ldcs(sp + (i >> 5) + 1) - k0) >> 5;
+  const bool valid = i < n;
+  const int mu = valid ? __ldcs(perm + i) : 0;
+  const double d = valid ? __ldcs(diag + i) : 0.0;
   int pc[kStepPF];
   double pw[kStepPF];
 #pragma unroll
   for (int u = 0; u < kStepPF; ++u) {
-    pc[u] = b + u < e ? __ldcs(col + b + u) : 0;
-    pw[u] = b + u < e ? __ldcs(w + b + u) : 0.0;
+    pc[u] = valid && u < width ? __ldcs(col + k0 + 32 * u + r) : 0;
+    pw[u] = valid && u < width ? __ldcs(w + k0 + 32 * u + r) : 0.0;
   }
   pdl_wait();
   pdl_trigger();
@@ -370,8 +447,8 @@ __global__ void __launch_bounds__(TB) k_step(int n, const int *__restrict__ rowp
   double v = d * c[mu];
 #pragma unroll
   for (int u = 0; u < kStepPF; ++u)
-    if (b + u < e) v = fma(pw[u], c[pc[u]], v);
-  for (int k = b + kStepPF; k < e; ++k) v = fma(__ldcs(w + k), c[__ldcs(col + k)], v);
+    if (u < width) v = fma(pw[u], c[pc[u]], v);
+  for (int u = kStepPF; u < width; ++u) v = fma(__ldcs(w + k0 + 32 * u + r), c[__ldcs(col + k0 + 32 * u + r)], v);
   cn[mu] = v;
 }
 
@@ -384,14 +461,14 @@ __global__ void k_set_dir(int nd, const int *__restrict__ dn, const double *__re
 
 // Mean duration of one explicit step on the current upwind map.
 double time_transport_step(System *s, int reps) {
-  if (!s->trowptr || !s->cbuf || !s->tdiag) fail(VAG_EINVAL, "no upwind map: run vag_transport first");
+  if (!s->tsp || !s->cbuf || !s->tdiag) fail(VAG_EINVAL, "no upwind map: run vag_transport first");
   cudaStream_t st = s->ctx->stream;
   const int n = s->n_cv + s->n_perf;
-  const int gs = grid_for(n, TB);
+  const int gs = grid_for(32 * ((n + 31) / 32), TB);
   double *a = s->cbuf, *b = s->cbuf + n;
   auto step = [&](const double *c, double *cn) {
-    launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
-               (const double *)s->tdiag, c, cn);
+    launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
+               (const double *)s->tval, (const double *)s->tdiag, c, cn);
     note_launches(1);
   };
   step(a, b);   // warm-up
@@ -438,6 +515,22 @@ void recover_cells_and_fluxes(System *s) {
   s->have_flux = true;
 }
 
+// Stream-ordered scratch allocations, released on every exit path.
+struct StreamScratch {
+  cudaStream_t st;
+  std::vector<void *> p;
+  template <class T>
+  T *get(size_t count) {
+    void *q = nullptr;
+    VAG_CUDA(cudaMallocAsync(&q, sizeof(T) * std::max<size_t>(count, 1), st));
+    p.push_back(q);
+    return static_cast<T *>(q);
+  }
+  ~StreamScratch() {
+    for (void *q : p) cudaFreeAsync(q, st);
+  }
+};
+
 // phi_m [nc], phi_f [nf], cbar [nd] already on the device.
 void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_transport_info *info,
                    const double *phi_m, const double *phi_f, const double *cbar) {
@@ -453,9 +546,11 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
                                              s->seg.d_cell_start, s->seg.cv_sys);
     note_launches(1);
   }
+  const int n_slices = (nt + 31) / 32;
   if (nt > s->t_rows) {
     s->tdiag = sys_alloc<double>(s, nt);
-    s->trowptr = sys_alloc<int>(s, (size_t)nt + 1);
+    s->tperm = sys_alloc<int>(s, nt);
+    s->tsp = sys_alloc<int>(s, (size_t)n_slices + 1);
     s->cbuf = sys_alloc<double>(s, 2 * (size_t)nt);
     s->t_rows = nt;
   }
@@ -465,28 +560,32 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
   VAG_CUDA(cudaMemsetAsync(s->status, 0, sizeof(int), st));
   k_porous<<<grid_for(n, TB), TB, 0, st>>>(t, s->phi, s->status);
   note_launches(1);
-  int *cnt;
-  unsigned long long *dt_bits;
-  VAG_CUDA(cudaMallocAsync(&cnt, sizeof(int) * ((size_t)nt + 1), st));
-  VAG_CUDA(cudaMallocAsync(&dt_bits, sizeof(unsigned long long) * ns, st));
+  StreamScratch scratch{st, {}};
+  int *cnt = scratch.get<int>((size_t)nt + 1);
+  int *inv = scratch.get<int>((size_t)nt + 1);
+  int *slice_len = scratch.get<int>((size_t)n_slices + 1);
+  unsigned long long *dt_bits = scratch.get<unsigned long long>(ns);
   VAG_CUDA(cudaMemsetAsync(dt_bits, 0x7f, sizeof(unsigned long long) * ns, st));   // > every finite ratio
   k_map_count<<<grid_for(nt, TB), TB, 0, st>>>(t, nt, s->phi, s->seg.cv_sys, cnt, dt_bits);
   note_launches(1);
   k_pick_dt<<<grid_for(ns, TB), TB, 0, st>>>(ns, dt_bits, s->dts, o->cfl, o->dt);
   note_launches(1);
   VAG_CHECK_LAUNCH();
-  const int64_t nnz_t = scan_exclusive(cnt, s->trowptr, nt, st);
-  VAG_CUDA(cudaFreeAsync(cnt, st));
-  VAG_CUDA(cudaFreeAsync(dt_bits, st));
+  const int64_t nnz_t = scan_exclusive(cnt, inv, nt, st);   // inflow entries (inv as scratch)
   if (read_status(s) & ST_NONPOSITIVE) fail(VAG_EINVAL, "a control volume has a non-positive porous volume");
-  if (nnz_t > s->t_cap) {
-    // grow the inflow-edge arrays (kept across calls)
-    s->tcol = sys_alloc<int>(s, (size_t)nnz_t);
-    s->tval = sys_alloc<double>(s, (size_t)nnz_t);
-    s->t_cap = nnz_t;
+  k_sigma_sort<<<(nt + kSigma - 1) / kSigma, kSigma, 0, st>>>(nt, cnt, s->tperm, inv, slice_len);
+  note_launches(1);
+  VAG_CHECK_LAUNCH();
+  const int64_t n_stored = scan_exclusive(slice_len, s->tsp, n_slices, st);
+  if (n_stored < nnz_t) fail(VAG_EINVAL, "the transport map exceeds 2^31 stored entries");
+  if (n_stored > s->t_cap) {
+    // grow the entry arrays (kept across calls)
+    s->tcol = sys_alloc<int>(s, (size_t)std::max<int64_t>(n_stored, 1));
+    s->tval = sys_alloc<double>(s, (size_t)std::max<int64_t>(n_stored, 1));
+    s->t_cap = n_stored;
   }
   s->nnz_t = nnz_t;
-  k_map_fill<<<grid_for(nt, TB), TB, 0, st>>>(t, nt, s->phi, s->seg.cv_sys, s->trowptr, s->dts, s->tdiag, s->tcol,
+  k_map_fill<<<grid_for(nt, TB), TB, 0, st>>>(t, nt, s->phi, s->seg.cv_sys, inv, s->tsp, s->dts, s->tdiag, s->tcol,
                                               s->tval);
   note_launches(1);
   // c^0 with the Dirichlet values and the injected concentrations
@@ -499,7 +598,7 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
   VAG_CHECK_LAUNCH();
   trace_mark(st, "porous volumes + CFL + upwind map");
   VAG_CUDA(cudaEventRecord(s->ev0, st));
-  const int gs = grid_for(nt, TB);
+  const int gs = grid_for(32 * n_slices, TB);
   // steps in CUDA graphs of kStepChunk launches (an even count: the chunk
   // starts and ends in the same buffer), the remainder launched directly
   constexpr int kStepChunk = 20;
@@ -513,8 +612,8 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
       set_capturing(true);
       double *a = s->cbuf, *b = s->cbuf + nt;
       for (int k = 0; k < kStepChunk; ++k) {
-        launch_pdl(k_step, gs, TB, 0, st, nt, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
-                   (const double *)s->tdiag, (const double *)a, b);
+        launch_pdl(k_step, gs, TB, 0, st, nt, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
+                   (const double *)s->tval, (const double *)s->tdiag, (const double *)a, b);
         std::swap(a, b);
       }
       set_capturing(false);
@@ -530,8 +629,8 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     }
   }
   for (int k = chunks * kStepChunk; k < o->n_steps; ++k) {
-    launch_pdl(k_step, gs, TB, 0, st, nt, (const int *)s->trowptr, (const int *)s->tcol, (const double *)s->tval,
-               (const double *)s->tdiag, (const double *)c0, c1);
+    launch_pdl(k_step, gs, TB, 0, st, nt, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
+               (const double *)s->tval, (const double *)s->tdiag, (const double *)c0, c1);
     note_launches(1);
     std::swap(c0, c1);
   }
