@@ -470,10 +470,12 @@ __device__ __forceinline__ T row_csr(int i, bool valid, int lane, const int *__r
 // The same row product split in two for programmatic dependent launch: the
 // first pf<T>() entries of each lane (matrix data, written by no kernel of the
 // cycle) are loaded before pdl_wait(), the x gathers after it.  Entries are
-// multiplied in the same order as row_csr, so the sum is identical.  (Eight
-// entries a lane for FP32 was measured slower on the classical levels.)
+// multiplied in the same order as row_csr, so the sum is identical.  FP32
+// rows take six entries a lane (48 of the classical coarse levels' 40-46
+// entries a row in flight at once; four and eight were measured slower),
+// FP64 rows four.
 template <class T>
-__host__ __device__ constexpr int pf() { return 4; }
+__host__ __device__ constexpr int pf() { return sizeof(T) == 4 ? 6 : 4; }
 template <class T>
 struct RowPF {
   int k, ke;
