@@ -59,7 +59,10 @@ __device__ __forceinline__ V3 neg(V3 a) { return {-a.x, -a.y, -a.z}; }
 // Here e1 = x_sigma - x_K for the whole face and, with d_t = q_t - x_K,
 // n1 = d_e x d_e+1, n2 = -(e1 x d_e+1), n3 = e1 x d_e: the corner vectors
 // c_t = e1 x d_t and L c_t are formed once and shared by the two tetrahedra
-// at corner t.
+// at corner t.  The gradients of a tetrahedron's barycentric coordinates sum
+// to zero, so every row of S, and of the face's sum F, sums to zero: only the
+// entries among (sigma, q0..q3) are integrated, and the x_K row follows as
+// F_K,j = -sum_i F_i,j, F_K,K = -sum_j F_K,j.
 template <int SH>
 __device__ __forceinline__ void cell_local(int K, int nc, const int *__restrict__ cn, const double *__restrict__ xyz,
                                            const double (&L)[6], const int *__restrict__ cell_ff, int fi, int n_fc,
@@ -107,25 +110,40 @@ __device__ __forceinline__ void cell_local(int K, int nc, const int *__restrict_
     for (int e = 0; e < Q4; ++e) {
       if (e >= Q) break;
       const int e1 = e + 1 == Q ? 0 : e + 1;
-      V3 n[4], Ln[4];
-      n[1] = cross(d[e], d[e1]);
-      Ln[1] = lmul(L, n[1]);
-      n[2] = neg(c[e1]);
-      Ln[2] = neg(Lc[e1]);
-      n[3] = c[e];
-      Ln[3] = Lc[e];
-      n[0] = neg(n[1] + n[2] + n[3]);
-      Ln[0] = neg(Ln[1] + Ln[2] + Ln[3]);
-      const double ad = fabs(dot(ev, n[1]));
+      V3 n[3], Ln[3];   // area vectors of (sigma, q_e, q_e+1)
+      n[0] = cross(d[e], d[e1]);
+      Ln[0] = lmul(L, n[0]);
+      n[1] = neg(c[e1]);
+      Ln[1] = neg(Lc[e1]);
+      n[2] = c[e];
+      Ln[2] = Lc[e];
+      const double ad = fabs(dot(ev, n[0]));
       const double tv = ad * (1.0 / 6.0);
       vol += tv;
       minvol = fmin(minvol, tv);
       const double inv = 1.0 / (6.0 * ad);
-      const int map[4] = {0, 1, 2 + e, 2 + e1};
+      const int map[3] = {1, 2 + e, 2 + e1};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = i; j < 4; ++j) F[p6(map[i], map[j])] = fma(dot(n[i], Ln[j]), inv, F[p6(map[i], map[j])]);
+        for (int j = i; j < 3; ++j) F[p6(map[i], map[j])] = fma(dot(n[i], Ln[j]), inv, F[p6(map[i], map[j])]);
+    }
+    // the x_K row from the zero row sums
+#pragma unroll
+    for (int j = 1; j < 2 + Q4; ++j) {
+      if (j >= 2 + Q) break;
+      double sj = 0.0;
+#pragma unroll
+      for (int i = 1; i < 2 + Q4; ++i)
+        if (i < 2 + Q) sj += F[p6(i, j)];
+      F[p6(0, j)] = -sj;
+    }
+    {
+      double sk = 0.0;
+#pragma unroll
+      for (int j = 1; j < 2 + Q4; ++j)
+        if (j < 2 + Q) sk += F[p6(0, j)];
+      F[p6(0, 0)] = -sk;
     }
     const bool isff = cell_ff[6 * (size_t)K + lf] >= 0;
     M[topo::pidx(0, 0)] += F[p6(0, 0)];
