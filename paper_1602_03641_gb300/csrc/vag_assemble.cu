@@ -106,6 +106,33 @@ __device__ __forceinline__ void cell_local(int K, int nc, const int *__restrict_
       c[t] = cross(ev, d[t]);
       Lc[t] = lmul(L, c[t]);
     }
+    // 6 |T| = |e1 . (d_e x d_e+1)| = |c_e . d_e+1| for each tetrahedron of the
+    // face, and all their reciprocals from one division (prefix products)
+    double a6[Q4], rinv[Q4];
+#pragma unroll
+    for (int e = 0; e < Q4; ++e) {
+      if (e >= Q) break;
+      const double ad = fabs(dot(c[e], d[e + 1 == Q ? 0 : e + 1]));
+      const double tv = ad * (1.0 / 6.0);
+      vol += tv;
+      minvol = fmin(minvol, tv);
+      a6[e] = 6.0 * ad;
+    }
+    {
+      double pre[Q4];
+      pre[0] = a6[0];
+#pragma unroll
+      for (int e = 1; e < Q4; ++e)
+        if (e < Q) pre[e] = pre[e - 1] * a6[e];
+      double r = 1.0 / pre[Q - 1];
+#pragma unroll
+      for (int e = Q4 - 1; e >= 1; --e) {
+        if (e >= Q) continue;
+        rinv[e] = r * pre[e - 1];
+        r *= a6[e];
+      }
+      rinv[0] = r;
+    }
 #pragma unroll
     for (int e = 0; e < Q4; ++e) {
       if (e >= Q) break;
@@ -117,11 +144,7 @@ __device__ __forceinline__ void cell_local(int K, int nc, const int *__restrict_
       Ln[1] = neg(Lc[e1]);
       n[2] = c[e];
       Ln[2] = Lc[e];
-      const double ad = fabs(dot(ev, n[0]));
-      const double tv = ad * (1.0 / 6.0);
-      vol += tv;
-      minvol = fmin(minvol, tv);
-      const double inv = 1.0 / (6.0 * ad);
+      const double inv = rinv[e];
       const int map[3] = {1, 2 + e, 2 + e1};
 #pragma unroll
       for (int i = 0; i < 3; ++i)
