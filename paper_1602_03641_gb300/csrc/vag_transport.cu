@@ -423,11 +423,12 @@ __global__ void k_cv_sys(int nv, int nf, int nc, int n_sys, const int *__restric
 // once a step (evict-first loads), so the cache keeps the concentrations
 // that the gathers reuse.
 constexpr int kStepPF = 4;
-__global__ void __launch_bounds__(TB) k_step(int n, const int *__restrict__ perm, const int *__restrict__ sp,
+constexpr int kStepTB = 128;   // 128 / 256 / 512 threads: 54.8 / 55.3 / 58.7 us at 128^3
+__global__ void __launch_bounds__(kStepTB) k_step(int n, const int *__restrict__ perm, const int *__restrict__ sp,
                                              const int *__restrict__ col, const double *__restrict__ w,
                                              const double *__restrict__ diag, const double *__restrict__ c,
                                              double *__restrict__ cn) {
-  const int i = blockIdx.x * TB + threadIdx.x;
+  const int i = blockIdx.x * kStepTB + threadIdx.x;
   if ((i >> 5) >= (n + 31) >> 5) return;   // whole warps
   const int r = i & 31;
   const int k0 = __ldcs(sp + (i >> 5)), width = (__ldcs(sp + (i >> 5) + 1) - k0) >> 5;
@@ -464,10 +465,10 @@ double time_transport_step(System *s, int reps) {
   if (!s->tsp || !s->cbuf || !s->tdiag) fail(VAG_EINVAL, "no upwind map: run vag_transport first");
   cudaStream_t st = s->ctx->stream;
   const int n = s->n_cv + s->n_perf;
-  const int gs = grid_for(32 * ((n + 31) / 32), TB);
+  const int gs = grid_for(32 * ((n + 31) / 32), kStepTB);
   double *a = s->cbuf, *b = s->cbuf + n;
   auto step = [&](const double *c, double *cn) {
-    launch_pdl(k_step, gs, TB, 0, st, n, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
+    launch_pdl(k_step, gs, kStepTB, 0, st, n, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
                (const double *)s->tval, (const double *)s->tdiag, c, cn);
     note_launches(1);
   };
@@ -598,7 +599,7 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
   VAG_CHECK_LAUNCH();
   trace_mark(st, "porous volumes + CFL + upwind map");
   VAG_CUDA(cudaEventRecord(s->ev0, st));
-  const int gs = grid_for(32 * n_slices, TB);
+  const int gs = grid_for(32 * n_slices, kStepTB);
   // steps in CUDA graphs of kStepChunk launches (an even count: the chunk
   // starts and ends in the same buffer), the remainder launched directly
   constexpr int kStepChunk = 20;
@@ -612,7 +613,7 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
       set_capturing(true);
       double *a = s->cbuf, *b = s->cbuf + nt;
       for (int k = 0; k < kStepChunk; ++k) {
-        launch_pdl(k_step, gs, TB, 0, st, nt, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
+        launch_pdl(k_step, gs, kStepTB, 0, st, nt, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
                    (const double *)s->tval, (const double *)s->tdiag, (const double *)a, b);
         std::swap(a, b);
       }
@@ -629,7 +630,7 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     }
   }
   for (int k = chunks * kStepChunk; k < o->n_steps; ++k) {
-    launch_pdl(k_step, gs, TB, 0, st, nt, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
+    launch_pdl(k_step, gs, kStepTB, 0, st, nt, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
                (const double *)s->tval, (const double *)s->tdiag, (const double *)c0, c1);
     note_launches(1);
     std::swap(c0, c1);
