@@ -415,17 +415,25 @@ __global__ void k_dense_inverse(const int *__restrict__ sys_start, const int *__
       return;   // uniform across the block: every thread read the same pivot
     }
     __syncthreads();
+    // Before pivot p, row p of A is zero left of p and column j > p of B is
+    // still e_j, so only A's columns > p and B's columns <= p change: m
+    // entries a row instead of 2m - 1 (the skipped updates subtract zeros)
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
-      A[p * m + j] /= piv;
-      B[p * m + j] /= piv;
+      if (j > p) A[p * m + j] /= piv;
+      else B[p * m + j] /= piv;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = e / m, j = e % m;
-      if (i == p) continue;
+    for (int e = threadIdx.x; e < (m - 1) * m; e += blockDim.x) {
+      const int ii = e / m, jj = e % m;
+      const int i = ii < p ? ii : ii + 1;
       const double f = A[i * m + p];
-      if (j != p) A[i * m + j] -= f * A[p * m + j];
-      B[i * m + j] -= f * B[p * m + j];
+      if (jj < m - 1 - p) {
+        const int j = p + 1 + jj;
+        A[i * m + j] -= f * A[p * m + j];
+      } else {
+        const int j = jj - (m - 1 - p);
+        B[i * m + j] -= f * B[p * m + j];
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x)

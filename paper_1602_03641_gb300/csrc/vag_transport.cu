@@ -310,8 +310,9 @@ __global__ void k_pick_dt(int n_sys, const unsigned long long *__restrict__ dt_b
 }
 
 // Row mu in slot inv[mu]: inflow entry j at tsp[s] + 32 j + r (slice s, lane
-// r); the slice's remaining entries of the row are padding (column mu,
-// weight 0), which leaves every product chain unchanged.
+// r), its column the upstream volume's slot (the steps run on the state in
+// slot order); the slice's remaining entries of the row are padding (the
+// row's own slot, weight 0), which leaves every product chain unchanged.
 __global__ void k_map_fill(TView t, int n, const double *__restrict__ phi, const int *__restrict__ cv_sys,
                            const int *__restrict__ inv, const int *__restrict__ sp, const double *__restrict__ dts,
                            double *__restrict__ diag, int *__restrict__ col, double *__restrict__ w) {
@@ -327,7 +328,7 @@ __global__ void k_map_fill(TView t, int n, const double *__restrict__ phi, const
     double out = 0.0;
     for_edges(t, mu, [&](double Fin, int nb) {
       if (Fin > 0.0) {
-        col[k0 + 32 * j] = nb;
+        col[k0 + 32 * j] = inv[nb];
         w[k0 + 32 * j] = h * Fin;
         ++j;
       } else {
@@ -337,7 +338,7 @@ __global__ void k_map_fill(TView t, int n, const double *__restrict__ phi, const
     diag[slot] = 1.0 - h * out;
   }
   for (; j < width; ++j) {
-    col[k0 + 32 * j] = mu;
+    col[k0 + 32 * j] = slot;
     w[k0 + 32 * j] = 0.0;
   }
 }
@@ -414,26 +415,25 @@ __global__ void k_cv_sys(int nv, int nf, int nc, int n_sys, const int *__restric
   cv_sys[mu] = lo;
 }
 
-// One thread per row slot, one warp per slice: the slice's entries are read
-// lane-contiguous (coalesced) and every lane walks the slice's width, so a
-// warp's fma instructions are as many as its widest row (rows of a slice
-// have nearly equal counts, see k_sigma_sort).  Launched with programmatic
-// dependent launch: the map (written once per solve) is read before the
-// dependency wait, the previous step's c after it.  The map streams through
-// once a step (evict-first loads), so the cache keeps the concentrations
-// that the gathers reuse.
+// One thread per row slot, one warp per slice, on the state in slot order
+// (c[i] is the concentration of volume tperm[i]): the slice's entries and
+// the rows' own values are read lane-contiguous (coalesced), and every lane
+// walks the slice's width, so a warp's fma instructions are as many as its
+// widest row (rows of a slice have nearly equal counts, see k_sigma_sort).
+// Launched with programmatic dependent launch: the map (written once per
+// solve) is read before the dependency wait, the previous step's c after it.
+// The map streams through once a step (evict-first loads), so the cache keeps
+// the concentrations that the gathers reuse.
 constexpr int kStepPF = 4;
 constexpr int kStepTB = 128;   // 128 / 256 / 512 threads: 54.8 / 55.3 / 58.7 us at 128^3
-__global__ void __launch_bounds__(kStepTB) k_step(int n, const int *__restrict__ perm, const int *__restrict__ sp,
-                                             const int *__restrict__ col, const double *__restrict__ w,
-                                             const double *__restrict__ diag, const double *__restrict__ c,
-                                             double *__restrict__ cn) {
+__global__ void __launch_bounds__(kStepTB) k_step(int n, const int *__restrict__ sp, const int *__restrict__ col,
+                                                  const double *__restrict__ w, const double *__restrict__ diag,
+                                                  const double *__restrict__ c, double *__restrict__ cn) {
   const int i = blockIdx.x * kStepTB + threadIdx.x;
   if ((i >> 5) >= (n + 31) >> 5) return;   // whole warps
   const int r = i & 31;
   const int k0 = __ldcs(sp + (i >> 5)), width = (__ldcs(sp + (i >> 5) + 1) - k0) >> 5;
   const bool valid = i < n;
-  const int mu = valid ? __ldcs(perm + i) : 0;
   const double d = valid ? __ldcs(diag + i) : 0.0;
   int pc[kStepPF];
   double pw[kStepPF];
@@ -445,12 +445,26 @@ __global__ void __launch_bounds__(kStepTB) k_step(int n, const int *__restrict__
   pdl_wait();
   pdl_trigger();
   if (!valid) return;
-  double v = d * c[mu];
+  double v = d * c[i];
 #pragma unroll
   for (int u = 0; u < kStepPF; ++u)
     if (u < width) v = fma(pw[u], c[pc[u]], v);
   for (int u = kStepPF; u < width; ++u) v = fma(__ldcs(w + k0 + 32 * u + r), c[__ldcs(col + k0 + 32 * u + r)], v);
-  cn[mu] = v;
+  cn[i] = v;
+}
+
+// state in control-volume order <-> slot order
+__global__ void k_to_slots(int n, const int *__restrict__ perm, const double *__restrict__ c_cv,
+                           double *__restrict__ c_slot) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c_slot[i] = c_cv[perm[i]];
+}
+__global__ void k_from_slots(int n, const int *__restrict__ perm, const double *__restrict__ c_slot,
+                             double *__restrict__ c_cv, int n_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int mu = perm[i];
+  if (mu < n_out) c_cv[mu] = c_slot[i];
 }
 
 __global__ void k_set_dir(int nd, const int *__restrict__ dn, const double *__restrict__ cbar, double *__restrict__ c) {
@@ -468,8 +482,8 @@ double time_transport_step(System *s, int reps) {
   const int gs = grid_for(32 * ((n + 31) / 32), kStepTB);
   double *a = s->cbuf, *b = s->cbuf + n;
   auto step = [&](const double *c, double *cn) {
-    launch_pdl(k_step, gs, kStepTB, 0, st, n, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
-               (const double *)s->tval, (const double *)s->tdiag, c, cn);
+    launch_pdl(k_step, gs, kStepTB, 0, st, n, (const int *)s->tsp, (const int *)s->tcol, (const double *)s->tval,
+               (const double *)s->tdiag, c, cn);
     note_launches(1);
   };
   step(a, b);   // warm-up
@@ -590,12 +604,15 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
                                               s->tval);
   note_launches(1);
   // c^0 with the Dirichlet values and the injected concentrations
+  // (assembled in control-volume order in the second half of cbuf, then
+  // gathered into slot order in the first)
   double *c0 = s->cbuf, *c1 = s->cbuf + nt;
-  VAG_CUDA(cudaMemcpyAsync(c0, c_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  VAG_CUDA(cudaMemcpyAsync(c1, c_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   if (s->n_perf)
-    VAG_CUDA(cudaMemcpyAsync(c0 + n, s->well_cin, sizeof(double) * s->n_perf, cudaMemcpyDeviceToDevice, st));
-  k_set_dir<<<grid_for(s->nd, TB), TB, 0, st>>>(s->nd, s->dir_nodes, cbar, c0);
-  note_launches(1);
+    VAG_CUDA(cudaMemcpyAsync(c1 + n, s->well_cin, sizeof(double) * s->n_perf, cudaMemcpyDeviceToDevice, st));
+  k_set_dir<<<grid_for(s->nd, TB), TB, 0, st>>>(s->nd, s->dir_nodes, cbar, c1);
+  k_to_slots<<<grid_for(nt, TB), TB, 0, st>>>(nt, s->tperm, c1, c0);
+  note_launches(2);
   VAG_CHECK_LAUNCH();
   trace_mark(st, "porous volumes + CFL + upwind map");
   VAG_CUDA(cudaEventRecord(s->ev0, st));
@@ -613,8 +630,8 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
       set_capturing(true);
       double *a = s->cbuf, *b = s->cbuf + nt;
       for (int k = 0; k < kStepChunk; ++k) {
-        launch_pdl(k_step, gs, kStepTB, 0, st, nt, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
-                   (const double *)s->tval, (const double *)s->tdiag, (const double *)a, b);
+        launch_pdl(k_step, gs, kStepTB, 0, st, nt, (const int *)s->tsp, (const int *)s->tcol, (const double *)s->tval,
+                   (const double *)s->tdiag, (const double *)a, b);
         std::swap(a, b);
       }
       set_capturing(false);
@@ -630,15 +647,16 @@ void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_tr
     }
   }
   for (int k = chunks * kStepChunk; k < o->n_steps; ++k) {
-    launch_pdl(k_step, gs, kStepTB, 0, st, nt, (const int *)s->tperm, (const int *)s->tsp, (const int *)s->tcol,
-               (const double *)s->tval, (const double *)s->tdiag, (const double *)c0, c1);
+    launch_pdl(k_step, gs, kStepTB, 0, st, nt, (const int *)s->tsp, (const int *)s->tcol, (const double *)s->tval,
+               (const double *)s->tdiag, (const double *)c0, c1);
     note_launches(1);
     std::swap(c0, c1);
   }
   VAG_CHECK_LAUNCH();
   trace_mark(st, "explicit steps");
   VAG_CUDA(cudaEventRecord(s->ev1, st));
-  VAG_CUDA(cudaMemcpyAsync(c_dev, c0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  k_from_slots<<<grid_for(nt, TB), TB, 0, st>>>(nt, s->tperm, c0, c_dev, n);
+  note_launches(1);
   s->dts_host.resize(2 * (size_t)ns);
   VAG_CUDA(cudaMemcpyAsync(s->dts_host.data(), s->dts, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, st));
   VAG_CUDA(cudaStreamSynchronize(st));
