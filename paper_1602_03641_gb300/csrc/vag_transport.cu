@@ -530,6 +530,7 @@ void recover_cells_and_fluxes(System *s) {
   s->have_flux = true;
 }
 
+namespace {
 // Stream-ordered scratch allocations, released on every exit path.
 struct StreamScratch {
   cudaStream_t st;
@@ -545,6 +546,7 @@ struct StreamScratch {
     for (void *q : p) cudaFreeAsync(q, st);
   }
 };
+}  // namespace
 
 // phi_m [nc], phi_f [nf], cbar [nd] already on the device.
 void transport_run(System *s, const vag_transport_opts *o, double *c_dev, vag_transport_info *info,
