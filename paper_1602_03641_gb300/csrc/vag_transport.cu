@@ -348,7 +348,7 @@ __global__ void k_map_fill(TView t, int n, const double *__restrict__ phi, const
 // (counts of 31 and more share the first bucket), equal counts by row index;
 // slice_len[s] = 32 x the widest row of slice s.  Deterministic: ranks come
 // from warp matches and prefix sums, not from atomics.
-constexpr int kSigma = 512;
+constexpr int kSigma = 1024;
 __global__ void __launch_bounds__(kSigma) k_sigma_sort(int n, const int *__restrict__ cnt, int *__restrict__ perm,
                                                        int *__restrict__ inv, int *__restrict__ slice_len) {
   constexpr int NW = kSigma / 32;
