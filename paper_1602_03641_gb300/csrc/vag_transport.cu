@@ -18,7 +18,10 @@
 //                volumes, rows by decreasing inflow count (stable), so that
 //                the 32 rows of a warp have nearly the same number of edges;
 //                the map is stored as sliced ELL over that order.
-//  k_cfl         Eq. (eq_CFL): min over non-Dirichlet CVs of phi / outflow.
+//  k_map_count / k_pick_dt
+//                Eq. (eq_CFL): per system the min over non-Dirichlet CVs of
+//                phi / outflow (taken while counting the inflow edges), and
+//                the step cfl x that bound.
 //  k_step        c' = d c + W c (one thread per row slot, one warp per slice).
 //
 // Wells (Sec. 5.5): perforation p exchanges the rate Fw[p] =
