@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "vag_internal.cuh"
+#include "vag_sizes.h"
 #include "vag_topo.h"
 
 namespace vag {
@@ -464,6 +465,16 @@ void symbolic_phase(System *s) {
   VAG_CUDA(cudaMallocAsync(&cnt, sizeof(int) * ((size_t)s->n_rows + 1), st));
   k_row_count<<<grid_for(s->n_rows, 128), 128, 0, st>>>(pv, s->n_rows, s->dof_of_row, cnt, s->status); note_launches(1);
   VAG_CHECK_LAUNCH();
+  if ((int64_t)s->n_rows * kMaxRowWidth > INT32_MAX) {
+    // Row pointers, sliced-ELL offsets and column indices are int32: a system
+    // this large may hold more stored entries than they address, so count
+    // them exactly (64-bit, on the host) before the 32-bit scan.
+    std::vector<int> h((size_t)s->n_rows);
+    VAG_CUDA(cudaMemcpyAsync(h.data(), cnt, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, st));
+    VAG_CUDA(cudaStreamSynchronize(st));
+    if (!fits_int32_indices(h.data(), h.size()))
+      fail(VAG_EINVAL, "the eliminated system holds more than 2^31 - 1 stored entries (int32 indices)");
+  }
   s->nnz = scan_exclusive(cnt, s->rowptr, s->n_rows, st);
   const int st2 = read_status(s);
   if (st2 & ST_ROW_OVERFLOW) fail(VAG_EMESH, "an eliminated row couples too many unknowns");
