@@ -231,9 +231,10 @@ unsigned long long vag_launch_count(void);
  * Krylov rows are the non-Dirichlet nodes in increasing node id followed by
  * the fracture faces in input order.  All arithmetic is FP64.
  * mem: location of every pointer in mesh, props and bc.
- * Size limits (int32 indices): n_nodes + n_ff + n_cells < 2^31, and the
- * eliminated system's stored entries, including the sliced-ELL padding of
- * 32-row slices, < 2^31; larger inputs are VAG_EINVAL.
+ * Size limits (int32 indices): n_nodes + n_ff + n_cells < 2^31, 8 n_cells
+ * and 4 n_ff < 2^31, and the eliminated system's stored entries, including
+ * the sliced-ELL padding of 32-row slices, < 2^31; larger inputs are
+ * VAG_EINVAL (the same limits hold for a batch's union).
  */
 vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *props,
                         const vag_dirichlet *bc, int mem, vag_system **out);

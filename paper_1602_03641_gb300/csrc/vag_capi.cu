@@ -283,7 +283,11 @@ vag_status vag_assemble(vag_ctx *ctx, const vag_mesh *mesh, const vag_props *pro
     if (mesh->n_nodes <= 0 || mesh->n_cells <= 0 || mesh->n_ff < 0) fail(VAG_EINVAL, "bad mesh sizes");
     if (bc->n_dir < 0) fail(VAG_EINVAL, "n_dir < 0");
     if (!(props->mu > 0.0)) fail(VAG_EINVAL, "mu must be positive");
-    if ((int64_t)mesh->n_nodes + mesh->n_ff + mesh->n_cells > 0x7fffffffLL) fail(VAG_EINVAL, "mesh too large");
+    // int32 indices: every control volume, and every cell's 8 node slots and
+    // fracture face's 4 node slots, must be addressable
+    if ((int64_t)mesh->n_nodes + mesh->n_ff + mesh->n_cells > 0x7fffffffLL || 8LL * mesh->n_cells > 0x7fffffffLL ||
+        4LL * mesh->n_ff > 0x7fffffffLL)
+      fail(VAG_EINVAL, "mesh too large");
     use_device(&ctx->c);
     sys.reset(new vag_system());
     System *s = &sys->s;
@@ -368,7 +372,7 @@ vag_status vag_assemble_batch(vag_ctx *ctx, int32_t n_sys, const vag_mesh *meshe
       if (props[i].mu != props[0].mu) fail(VAG_EINVAL, "all systems of a batch must share mu");
       nv += m.n_nodes; nc += m.n_cells; nf += m.n_ff; nd += bcs[i].n_dir;
     }
-    if (nv + nf + nc > 0x7fffffffLL || 8 * nc > 0x7fffffffLL) fail(VAG_EINVAL, "batch too large");
+    if (nv + nf + nc > 0x7fffffffLL || 8 * nc > 0x7fffffffLL || 4 * nf > 0x7fffffffLL) fail(VAG_EINVAL, "batch too large");
     use_device(&ctx->c);
     sys.reset(new vag_system());
     System *s = &sys->s;
