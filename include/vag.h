@@ -72,7 +72,7 @@ enum { VAG_FP64 = 0, VAG_MIXED = 1, VAG_MIXED_F16 = 2, VAG_FP64_PC32 = 3 };
  * second pass, direct interpolation from at most four coarse neighbours,
  * Galerkin R A P with R = P^T, the same l1-Jacobi sweeps; FP64, FP32 under
  * VAG_MIXED or VAG_FP64_PC32 (not VAG_MIXED_F16).  Wherever VAG_PC_AMG is
- * accepted, VAG_PC_AMG_RS is too. */
+ * accepted, VAG_PC_AMG_RS is too, except under VAG_MIXED_F16 (VAG_EINVAL). */
 enum { VAG_PC_JACOBI = 0, VAG_PC_CHEBYSHEV = 1, VAG_PC_AMG = 2, VAG_PC_AMG_RS = 3 };
 /* Krylov method: CG (the system is SPD), or one of the methods of the
  * paper's solver experiments (§5.3), both right-preconditioned: BiCGStab, or
