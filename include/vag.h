@@ -281,19 +281,20 @@ vag_status vag_system_get_info(const vag_system *sys, vag_system_info *info);
 typedef struct {
   int precision;     /* VAG_FP64, VAG_MIXED, VAG_MIXED_F16, VAG_FP64_PC32   */
   int precond;       /* VAG_PC_JACOBI, VAG_PC_CHEBYSHEV (VAG_FP64 only;
-                        VAG_EINVAL otherwise), VAG_PC_AMG                     */
+                        VAG_EINVAL otherwise), VAG_PC_AMG, VAG_PC_AMG_RS     */
   double rtol;       /* stop at ||b - A x||_2 <= rtol ||b||_2 (> 0)           */
   int32_t maxit;     /* Krylov iteration cap (total over refinements)          */
   int mem;           /* location of u_out                                     */
   int32_t krylov;    /* VAG_KRYLOV_CG (0, the default), VAG_KRYLOV_BICGSTAB
                         or VAG_KRYLOV_GMRES (FP64 iterations; with VAG_MIXED
-                        only for VAG_PC_AMG, whose V-cycle then runs on the
-                        FP32 hierarchy); iterations counts Arnoldi steps for
-                        GMRES                                              */
-  double inner_rtol; /* VAG_MIXED(_F16) with VAG_PC_AMG and CG: smallest
-                        relative tolerance of an inner FP32 solve (each
-                        refinement step solves to max(inner_rtol, 0.3 x the
-                        reduction still needed), at most 0.1); 0 = 1e-6    */
+                        only for an AMG preconditioner, whose V-cycle then
+                        runs on the FP32 hierarchy); iterations counts
+                        Arnoldi steps for GMRES                            */
+  double inner_rtol; /* VAG_MIXED(_F16) with an AMG preconditioner and CG:
+                        smallest relative tolerance of an inner FP32 solve
+                        (each refinement step solves to max(inner_rtol,
+                        0.3 x the reduction still needed), at most 0.1);
+                        0 = 1e-6                                           */
 } vag_solve_opts;
 
 typedef struct {
@@ -351,8 +352,11 @@ typedef struct {
 /*
  * Explicit first-order upwind transport (Sec. 3.2, Eq. darcyfluxH) driven by
  * the fluxes of the last vag_solve (or of vag_set_fluxes).  Porous volumes
- * follow Sec. 3.2.1 with alpha_{K,s} = omega/8 on nodes of K outside
- * V_D u V_Gamma and alpha_{sigma,s} = omega/4 on nodes of sigma outside V_D.
+ * follow Sec. 3.2.1 with alpha_{K,s} = omega/|V_K| on nodes of K outside
+ * V_D u V_Gamma (omega/8 on a hexahedron) and alpha_{sigma,s} =
+ * omega/|V_sigma| on nodes of sigma outside V_D.  Well perforations (Sec.
+ * 5.5) add their rates: a producer's outflow leaves its fracture face with
+ * the face's concentration, an injector's inflow enters at its well_cin.
  * c_inout: [n_nodes + n_ff + n_cells]; on entry c^0, on exit c^{n_steps}.  The
  * Dirichlet entries are set to cbar before the first step (c^0_s = cbar_s).
  */
