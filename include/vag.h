@@ -438,9 +438,9 @@ enum {
  * launches of one hot kernel on this system's own data with CUDA events on the
  * context's stream and return the mean duration of a launch in *ms_per_launch.
  * VAG_KERNEL_SMOOTH needs the AMG hierarchy of a previous vag_solve with
- * VAG_PC_AMG (VAG_MIXED_F16's FP16 finest level excepted);
+ * VAG_PC_AMG or VAG_PC_AMG_RS (VAG_MIXED_F16's FP16 finest level excepted);
  * VAG_KERNEL_SPMV32 needs a previous VAG_MIXED or VAG_MIXED_F16 solve with
- * VAG_PC_AMG and CG; VAG_KERNEL_CELL_LOCAL rewrites the system's local
+ * an AMG preconditioner and CG; VAG_KERNEL_CELL_LOCAL rewrites the system's local
  * matrices with the same values; VAG_KERNEL_TRANSPORT_STEP needs the upwind map of a
  * previous vag_transport; VAG_EINVAL otherwise, or for reps < 1.  The kernels
  * run on the system's Krylov and transport work vectors, whose contents are
