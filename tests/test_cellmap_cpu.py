@@ -172,6 +172,15 @@ def test_bad_cells_and_bad_ids_are_rejected(run):
     assert res[0][0] == BAD_INDEX
     res, _ = run(pb.n_nodes - 1, faces, [cf])
     assert res[0][0] == BAD_INDEX
+    # three faces folded onto a repeated node ((0,1,0,2) for the bottom face,
+    # and two more that restore every node's count): eight nodes, each in
+    # three faces, and the cube's twelve edges, but not the cube's faces
+    cube = [[0, 2, 6, 4], [1, 3, 7, 5], [0, 1, 5, 4], [2, 3, 7, 6], [0, 1, 3, 2], [4, 5, 7, 6]]
+    res, _ = run(8, cube, [[0, 1, 2, 3, 4, 5]])
+    assert res[0][0] == OK
+    folded = [[6, 2, 6, 4], [1, 3, 7, 5], [0, 1, 5, 4], [3, 2, 3, 7], [0, 1, 0, 2], [4, 5, 7, 6]]
+    res, _ = run(8, folded, [[0, 1, 2, 3, 4, 5]])
+    assert res[0][0] == UNSUPPORTED
     # a prism with a lateral face whose nodes do not join its triangles
     prism_faces = [[0, 1, 2], [3, 4, 5], [0, 1, 4, 3], [1, 2, 5, 4], [2, 0, 3, 5]]
     twisted = [list(f) for f in prism_faces]
