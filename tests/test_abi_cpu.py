@@ -115,3 +115,24 @@ def test_binding_constants_match_the_header(vag):
         assert hasattr(vag, n) or hasattr(pkg, n), n
         got = getattr(vag, n, getattr(pkg, n, None))
         assert got == int(v), (n, got, v)
+
+
+def test_binding_fails_loudly_without_the_library(vag, monkeypatch):
+    """No fallback: without libvag.so the binding raises instead of computing
+    anything another way."""
+    monkeypatch.setattr(vag, "_LIB", None)
+    monkeypatch.setattr(vag, "LIB_PATH", os.path.join(tempfile.mkdtemp(), "libvag.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        vag.lib()
+
+
+def test_product_never_imports_the_oracle():
+    """The package and its kernels share nothing with the oracle: no import of
+    it anywhere in the package's sources."""
+    pkg = os.path.join(ROOT, "paper_1602_03641_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", txt, flags=re.M), f
+                assert "vag_oracle" not in txt, f
